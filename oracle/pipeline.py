@@ -1,0 +1,60 @@
+"""Oracle: the whole path for one request, step by step (Sec. 2).
+
+Test infrastructure only (see the package docstring).
+
+G (Eq. green_mat) -> chi0(R, tau) (Algorithm 1, or the plain definition)
+-> chi0(R, i omega) (cosine transform) -> chi0(q, i omega) (Fourier
+transform) -> E_c (ln det by LU, quadrature over omega, mean over q).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import energy, freq, green
+from .chi0_alg1 import chi0_alg1
+from .chi0_definition import chi0_definition
+
+
+def spin_factor(nspins: int) -> float:
+    """Spin factor s of chi0: 2 for a spin-unpolarised calculation."""
+    if nspins != 1:
+        raise ValueError("only nspins = 1 is covered")
+    return 2.0
+
+
+def chi0_tau(inp, grid, route="alg1", go=None, gv=None):
+    """chi0(R, tau) as [ntau][nR][N][N]."""
+    st = inp.st
+    if go is None:
+        go, gv = green.green(st.kmesh, inp.kfrac, inp.eig, inp.occ, inp.wfc, inp.efermi, grid["tau"])
+    ntau = len(grid["tau"])
+    pts = [(iR, it) for it in range(ntau) for iR in range(st.nk)]
+    s = spin_factor(st.nspins)
+    if route == "alg1":
+        c = chi0_alg1(st, inp.lri, go, gv, pts, spin=s)
+    elif route == "definition":
+        c = chi0_definition(st, inp.lri, go, gv, pts, spin=s)
+    else:
+        raise ValueError(route)
+    return c.reshape(ntau, st.nk, st.naux, st.naux)
+
+
+def chi0_q_omega(inp, grid, chi_tau):
+    """chi0(q, i omega) as [nq][nomega][N][N] complex."""
+    st = inp.st
+    chi_w = freq.tau_to_omega(chi_tau, grid["gamma"])            # [nw][nR][N][N]
+    out = np.empty((st.nk, chi_w.shape[0], st.naux, st.naux), dtype=np.complex128)
+    for k in range(chi_w.shape[0]):
+        out[:, k] = freq.r_to_q(chi_w[k], st.kmesh, inp.kfrac)
+    return out
+
+
+def rpa_energy(inp, grid, route="alg1", vq=None):
+    """Dict with G, chi0 in every representation and E_c (Ha per cell)."""
+    st = inp.st
+    go, gv = green.green(st.kmesh, inp.kfrac, inp.eig, inp.occ, inp.wfc, inp.efermi, grid["tau"])
+    ct = chi0_tau(inp, grid, route=route, go=go, gv=gv)
+    cq = chi0_q_omega(inp, grid, ct)
+    v = inp.vq if vq is None else vq
+    ec, ec_q, ec_w, f = energy.correlation_energy(cq, v, grid["w_omega"])
+    return dict(go=go, gv=gv, chi_tau=ct, chi_qw=cq, ec=ec, ec_q=ec_q, ec_w=ec_w, integrand=f)

@@ -1,0 +1,324 @@
+"""Pins of the CPU oracle against mathematics (no GPU).
+
+Each test ties the oracle to something other than itself: an independent
+route to the same number, a closed form, an invariant or a textbook special
+case.  Together they catch a dropped term, a wrong sign, phase or index,
+a transposed operand or a wrong normalisation anywhere in the oracle.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_2407_19930_gb300 import synthetic as syn
+from oracle import energy, freq, green, grid as ogrid, pipeline
+from oracle.chi0_alg1 import chi0_alg1
+from oracle.chi0_definition import chi0_definition
+from oracle.chi0_sos import chi0_sos
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return syn.config_tiny()
+
+
+@pytest.fixture(scope="module")
+def cubic():
+    return syn.config_cubic()
+
+
+def _green(inp, tau):
+    st = inp.st
+    return green.green(st.kmesh, inp.kfrac, inp.eig, inp.occ, inp.wfc, inp.efermi, tau)
+
+
+# ---------------------------------------------------------------- P0: G
+
+
+def test_green_completeness_and_trace(cubic):
+    """sum over all bands at tau = 0: G^occ(R,0) + G^vir(R,0) = delta_R0 I (S = I);
+    Tr G^occ(0, 0) = number of occupied bands."""
+    st = cubic.st
+    go, gv, im = green.green(st.kmesh, cubic.kfrac, cubic.eig, cubic.occ, cubic.wfc,
+                             cubic.efermi, [0.0], return_imag=True)
+    assert im < 1e-13
+    tot = go[0] + gv[0]
+    for iR in range(st.nk):
+        ref = np.eye(st.nao) if iR == 0 else np.zeros((st.nao, st.nao))
+        assert np.abs(tot[iR] - ref).max() < 1e-12
+    assert abs(np.trace(go[0, 0]) - st.nocc) < 1e-12
+
+
+def test_green_matches_bvk_supercell(cubic):
+    """G(R, tau) equals the block of the Green's function of the BvK supercell
+    Hamiltonian diagonalised at Gamma: pins exp(-i k.R) and 1/N_k."""
+    st = cubic.st
+    n1, n2, n3 = st.kmesh
+    cells = [(a, b, c) for a in range(n1) for b in range(n2) for c in range(n3)]
+    nao, nR = st.nao, len(cells)
+    hs = np.zeros((nR * nao, nR * nao))
+    for ia, Ra in enumerate(cells):
+        for ib, Rb in enumerate(cells):
+            for R, h in cubic.hr.items():
+                d = np.array(R) - (np.array(Rb) - np.array(Ra))
+                if d[0] % n1 == 0 and d[1] % n2 == 0 and d[2] % n3 == 0:
+                    hs[ia * nao:(ia + 1) * nao, ib * nao:(ib + 1) * nao] += h
+    e, v = np.linalg.eigh(0.5 * (hs + hs.T))
+    nocc = st.nocc * nR
+    tau = np.array([0.0, 0.7, 2.5])
+    go, gv = _green(cubic, tau)
+    mu = cubic.efermi
+    for it, t in enumerate(tau):
+        wo = np.where(np.arange(len(e)) < nocc, np.exp(-(mu - e) * t), 0.0)
+        wv = np.where(np.arange(len(e)) >= nocc, np.exp(-(e - mu) * t), 0.0)
+        gso = (v * wo) @ v.T
+        gsv = (v * wv) @ v.T
+        for iR in range(nR):
+            blk_o = gso[0:nao, iR * nao:(iR + 1) * nao]
+            blk_v = gsv[0:nao, iR * nao:(iR + 1) * nao]
+            assert np.abs(blk_o - go[it, iR]).max() < 1e-12
+            assert np.abs(blk_v - gv[it, iR]).max() < 1e-12
+
+
+# ---------------------------------------------------------------- P1: exact in tau
+
+
+@pytest.mark.parametrize("name", ["tiny", "cubic"])
+def test_three_routes_agree_in_tau(name, request):
+    """Algorithm 1 == plain definition (R space) and == sum over states (q space),
+    an algebraic identity with no grid error."""
+    inp = request.getfixturevalue(name)
+    st = inp.st
+    tau = np.array([0.25, 1.3])
+    go, gv = _green(inp, tau)
+    pts = [(iR, it) for it in range(len(tau)) for iR in range(st.nk)]
+    ca = chi0_alg1(st, inp.lri, go, gv, pts)
+    cd = chi0_definition(st, inp.lri, go, gv, pts)
+    scale = np.abs(ca).max()
+    assert scale > 1.0
+    assert np.abs(ca - cd).max() < 1e-13 * scale
+    ca = ca.reshape(len(tau), st.nk, st.naux, st.naux)
+    for iq in range(st.nk):
+        s = chi0_sos(st, inp.lri, inp.kfrac, inp.eig, inp.occ, inp.wfc, iq, tau=tau)
+        for it in range(len(tau)):
+            q = freq.r_to_q(ca[it], st.kmesh, inp.kfrac, [iq])[0]
+            assert np.abs(q - s[it]).max() < 1e-13 * scale
+
+
+# ---------------------------------------------------------------- P2..P5: frequency domain
+
+
+@pytest.fixture(scope="module")
+def cubic_run(cubic):
+    dmin, dmax = cubic.delta_range
+    g = ogrid.make_grid(8, dmin, dmax)
+    out = pipeline.rpa_energy(cubic, g)
+    return g, out
+
+
+def test_frequency_form_within_grid_error(cubic, cubic_run):
+    """Space-time chi0(q, i omega_k) vs the exact sum over states with the
+    Lorentzian kernel: |diff_{mu nu}| <= (s/N_k) sum f(1-f) |rho^mu||rho^nu| eps_k."""
+    g, out = cubic_run
+    st = cubic.st
+    dmin, dmax = cubic.delta_range
+    eps = ogrid.transform_error(g, dmin, dmax)
+    # |rho| bound: recompute the diagonal of the tau = 0 response (kernel 1)
+    for iq in (0, 3):
+        exact = chi0_sos(st, cubic.lri, cubic.kfrac, cubic.eig, cubic.occ, cubic.wfc, iq,
+                         omega=g["omega"])
+        bound0 = -chi0_sos(st, cubic.lri, cubic.kfrac, cubic.eig, cubic.occ, cubic.wfc, iq,
+                           tau=[0.0])[0]
+        dia = np.sqrt(np.abs(np.diag(bound0)).real)
+        for k in range(len(g["omega"])):
+            diff = np.abs(out["chi_qw"][iq, k] - exact[k])
+            bound = eps[k] * np.outer(dia, dia) * 1.0000001 + 1e-12
+            assert np.all(diff <= bound)
+    # and the grid is good enough for the bound to mean something
+    assert eps.max() < 1e-5
+
+
+def test_hermitian_and_time_reversal(cubic, cubic_run):
+    g, out = cubic_run
+    st = cubic.st
+    mi = syn.minus_index(st.kmesh)
+    cq = out["chi_qw"]
+    scale = np.abs(cq).max()
+    for iq in range(st.nk):
+        for k in range(cq.shape[1]):
+            assert np.abs(cq[iq, k] - cq[iq, k].conj().T).max() < 1e-13 * scale
+            assert np.abs(cq[mi[iq], k] - cq[iq, k].conj()).max() < 1e-13 * scale
+
+
+def test_negative_semidefinite_and_energy_sign(cubic, cubic_run):
+    """chi0(q, i omega) <= 0 when the grid kernel sum_j Gamma_kj e^{-D tau_j}
+    is >= 0 on every transition energy; every integrand and E_c are <= 0."""
+    g, out = cubic_run
+    st = cubic.st
+    nocc = st.nocc
+    d = (cubic.eig[:, None, nocc:][..., None] - cubic.eig[None, :, :nocc][..., None, :]).ravel()
+    ker = np.exp(-np.outer(d, g["tau"])) @ g["gamma"].T
+    assert ker.min() >= 0
+    for iq in range(st.nk):
+        for k in range(len(g["omega"])):
+            ev = np.linalg.eigvalsh(out["chi_qw"][iq, k])
+            assert ev.max() <= 1e-12 * np.abs(ev).max()
+    assert np.all(out["integrand"] <= 0)
+    assert out["ec"] < 0
+
+
+def test_lu_equals_eigenvalues(cubic, cubic_run):
+    """ln det(1 - Pi) + Tr Pi by LU == sum ln(1 - lambda) + lambda over eigenvalues of Pi."""
+    g, out = cubic_run
+    for iq in (0, 5):
+        for k in (0, 4):
+            a, phase, _ = energy.integrand_lu(out["chi_qw"][iq, k], cubic.vq[iq])
+            b = energy.integrand_eig(out["chi_qw"][iq, k], cubic.vq[iq])
+            assert abs(phase) < 1e-10
+            assert abs(a - b) < 1e-10 * max(1.0, abs(a))
+
+
+def test_quadratic_limit(cubic, cubic_run):
+    """E_c(lambda V) / lambda^2 -> -(1/4 pi) sum_q w_q sum_k W_k Tr[(chi0 V)^2]."""
+    g, out = cubic_run
+    cq = out["chi_qw"]
+    nq = cq.shape[0]
+    lim = 0.0
+    for iq in range(nq):
+        for k in range(cq.shape[1]):
+            p = cq[iq, k] @ cubic.vq[iq]
+            lim += g["w_omega"][k] * np.trace(p @ p).real / nq
+    lim *= -1.0 / (4 * math.pi)
+    vals = []
+    for lam in (1e-2, 1e-3):
+        ec = energy.correlation_energy(cq, cubic.vq * lam, g["w_omega"])[0]
+        vals.append(ec / lam ** 2)
+    # O(lambda) correction: Richardson-extrapolate the two values to lambda -> 0
+    rich = (vals[1] * 1e-2 - vals[0] * 1e-3) / (1e-2 - 1e-3)
+    assert abs(vals[1] - lim) < 2e-2 * abs(lim)
+    assert abs(rich - lim) < 1e-5 * abs(lim)
+
+
+# ---------------------------------------------------------------- P8: two-level closed form
+
+
+def _two_level(delta, c01, v, n_tau=16):
+    """One atom, one k point, two NAOs (one occupied, one virtual), one ABF."""
+    st = syn.Structure(lat=np.eye(3) * 50.0, pos=np.zeros((1, 3)), n_ao=np.array([2]),
+                       n_aux=np.array([1]), n_low=np.array([1]), kmesh=(1, 1, 1))
+    eig = np.array([[-delta / 2, delta / 2]])
+    occ = np.array([[1.0, 0.0]])
+    wfc = np.eye(2, dtype=np.complex128)[None]
+    C = np.array([[[0.0, c01], [c01, 0.0]]])
+    inp = syn.Inputs(st=st, kfrac=np.zeros((1, 3)), eig=eig, occ=occ, wfc=wfc, efermi=0.0,
+                     lri=[(0, 0, (0, 0, 0), C)], vq=np.array([[[v + 0j]]]))
+    g = ogrid.make_grid(n_tau, delta, delta)
+    return inp, g
+
+
+@pytest.mark.parametrize("delta,c01,v", [(0.6, 0.7, 1.3), (1.1, 0.2, 0.5), (0.3, 1.5, 2.0)])
+def test_two_level_closed_form(delta, c01, v):
+    """E_c = (1/2)(sqrt(D^2 + 2aD) - D - a), a = s rho^2 V, rho = 2 c01 (both
+    on-site terms of Eq. LRI), from int_0^inf ln(1 + c/(D^2+w^2)) dw = pi(sqrt(D^2+c) - D)."""
+    inp, g = _two_level(delta, c01, v)
+    out = pipeline.rpa_energy(inp, g)
+    a = 2.0 * (2 * c01) ** 2 * v
+    exact = 0.5 * (math.sqrt(delta ** 2 + 2 * a * delta) - delta - a)
+    assert out["ec"] < 0
+    assert abs(out["ec"] - exact) < 1e-6 * abs(exact)
+
+
+# ---------------------------------------------------------------- P9: grid
+
+
+def test_grid_rules():
+    """The Gauss-Legendre rule integrates Legendre polynomials exactly; the
+    mapped omega rule reproduces int_0^inf 4D^2/(D^2+w^2)^2 dw = pi/D; the
+    fitted transform reproduces the exact cosine transform of e^{-D tau}."""
+    t, w = ogrid.gauss_legendre(12)
+    for deg in range(0, 23):
+        exact = 0.0 if deg % 2 else 2.0 / (deg + 1)
+        assert abs(np.sum(w * t ** deg) - exact) < 1e-14
+    for n, dmin, dmax, tol_q, tol_t in ((8, 0.7, 1.3, 1e-4, 1e-6), (16, 0.7, 1.3, 1e-9, 1e-8),
+                                        (16, 0.5, 5.0, 1e-7, 1e-5)):
+        g = ogrid.make_grid(n, dmin, dmax)
+        assert ogrid.quadrature_error(g, dmin, dmax) < tol_q
+        eps = ogrid.transform_error(g, dmin, dmax)
+        scale = 2.0 / dmin
+        assert eps.max() < tol_t * scale
+        assert np.all(g["w_omega"] > 0) and np.all(np.diff(g["tau"]) > 0)
+
+
+# ---------------------------------------------------------------- P10: invariances
+
+
+def _permute(inp, perm):
+    """Relabel atoms: new atom a is old atom perm[a]."""
+    st = inp.st
+    inv = np.argsort(perm)
+    ao_off = np.concatenate([[0], np.cumsum(st.n_ao)])
+    aux_off = np.concatenate([[0], np.cumsum(st.n_aux)])
+    st2 = syn.Structure(lat=st.lat, pos=st.pos[perm], n_ao=st.n_ao[perm], n_aux=st.n_aux[perm],
+                        n_low=st.n_low[perm], kmesh=st.kmesh)
+    orb = np.concatenate([np.arange(ao_off[p], ao_off[p + 1]) for p in perm])
+    aux = np.concatenate([np.arange(aux_off[p], aux_off[p + 1]) for p in perm])
+    lri = [(int(inv[I]), int(inv[K]), R, C) for I, K, R, C in inp.lri]
+    vq = inp.vq[:, aux][:, :, aux]
+    return syn.Inputs(st=st2, kfrac=inp.kfrac, eig=inp.eig, occ=inp.occ, wfc=inp.wfc[:, :, orb],
+                      efermi=inp.efermi, lri=lri, vq=vq), aux
+
+
+def test_atom_permutation_invariance(cubic, cubic_run):
+    g, out = cubic_run
+    inp2, aux = _permute(cubic, [1, 0])
+    out2 = pipeline.rpa_energy(inp2, g)
+    assert abs(out2["ec"] - out["ec"]) < 1e-12 * abs(out["ec"])
+    assert np.abs(out2["chi_tau"] - out["chi_tau"][:, :, aux][:, :, :, aux]).max() < 1e-12 * np.abs(
+        out["chi_tau"]).max()
+
+
+def test_lattice_shift_invariance(cubic, cubic_run):
+    """Moving atom 1 by a lattice vector L relabels its cells: C[I,1,R] -> C[I,1,R-L],
+    C[1,K,R] -> C[1,K,R+L], c_i(k) of atom 1 picks up e^{+i k.L}."""
+    g, out = cubic_run
+    st = cubic.st
+    L = np.array([1, 0, -1])
+    lri = []
+    for I, K, R, C in cubic.lri:
+        R = np.array(R)
+        if K == 1:
+            R = R - L
+        if I == 1:
+            R = R + L
+        lri.append((I, K, tuple(int(x) for x in R), C))
+    wfc = cubic.wfc.copy()
+    orb1 = slice(int(st.n_ao[0]), st.nao)
+    ph = np.exp(2j * np.pi * (cubic.kfrac @ L))
+    wfc[:, :, orb1] *= ph[:, None, None]
+    st2 = syn.Structure(lat=st.lat, pos=st.pos + np.array([[0, 0, 0], L @ st.lat]), n_ao=st.n_ao,
+                        n_aux=st.n_aux, n_low=st.n_low, kmesh=st.kmesh)
+    inp2 = syn.Inputs(st=st2, kfrac=cubic.kfrac, eig=cubic.eig, occ=cubic.occ, wfc=wfc,
+                      efermi=cubic.efermi, lri=lri, vq=cubic.vq)
+    # V(q) in the relabelled ABF cells: V_{mu nu} -> e^{+i q.L_mu} V_{mu nu} e^{-i q.L_nu}
+    aux1 = slice(int(st.n_aux[0]), st.naux)
+    vq = cubic.vq.copy()
+    phq = np.exp(2j * np.pi * (cubic.kfrac @ L))
+    for iq in range(st.nk):
+        vq[iq][aux1, :] *= phq[iq]
+        vq[iq][:, aux1] *= phq[iq].conj()
+    inp2.vq = vq
+    out2 = pipeline.rpa_energy(inp2, g)
+    assert abs(out2["ec"] - out["ec"]) < 1e-12 * abs(out["ec"])
+
+
+def test_pair_transpose_symmetry(cubic, cubic_run):
+    """chi0_{VU}(-R) = chi0_{UV}(R)^T (the U <-> V symmetry of the pair set)."""
+    g, out = cubic_run
+    st = cubic.st
+    ct = out["chi_tau"]
+    mi = syn.minus_index(st.kmesh)
+    scale = np.abs(ct).max()
+    for it in range(ct.shape[0]):
+        for iR in range(st.nk):
+            assert np.abs(ct[it, mi[iR]] - ct[it, iR].T).max() < 1e-13 * scale
