@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the LRI space-time RPA path on GB300.
+
+One step = one RPA correlation energy of the graphene-slab workload (35 atoms:
+a 4x4 graphene supercell plus a water-shaped molecule, N_aux = 2010, 4x4x1
+k-mesh, 16 tau/omega points, FP64): G(R, tau) -> chi0(R, tau) -> chi0(q, i omega)
+-> ln det -> E_c, every step through the library's C ABI.
+
+Prints one JSON line.  ``value`` = RPA energies/s of the whole job with inputs
+resident in HBM; ``e2e`` = the same with the inputs pushed from host buffers
+through the C ABI and E_c read back inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gpu,reference}]
+
+Under torchrun (N > 1) every rank computes its own energy (independent
+requests, no collective on the data path): weak scaling, value = all ranks'
+energies / the slowest rank's time.  ``--impl reference`` times the CPU oracle
+(the paper's Algorithm 1 in plain C, OpenMP) on a bounded sample of the same
+workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RPA energies/s"
+UNIT = "energies/s"
+WORKLOAD = ("graphene 4x4 supercell + H2O-shaped molecule: 35 atoms, n_ao 431, N_aux 2010, "
+            "4x4x1 k-mesh, 16 tau/omega points, FP64")
+
+# FP64 tensor-core peak: measured BF16 dense peak x the nominal FP64/BF16 ratio of GB300
+# (1.25 TFLOP/s / 2250 TFLOP/s); no FP64 figure is in the measured-peaks file.
+NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
+
+# DRAM traffic per launch of the dominant kernels from one ncu capture (see profiles/),
+# valid only while the kernel source is unchanged (sha256 of the file at capture time).
+TRAFFIC = {}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _src_sha(path):
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                if self.uuid and parts[0] != self.uuid:
+                    continue
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+
+
+def cpu_sample(inp, grid, budget_s=25.0):
+    """Time the oracle (Algorithm 1 in plain C with OpenMP, numpy LU) on a bounded
+    sample of the workload and extrapolate to one RPA energy."""
+    import numpy as np
+    from oracle import energy, green
+    from oracle.chi0_alg1 import chi0_alg1
+    st = inp.st
+    ntau = len(grid["tau"])
+    t0 = time.perf_counter()
+    go, gv = green.green(st.kmesh, inp.kfrac, inp.eig, inp.occ, inp.wfc, inp.efermi, grid["tau"][:1])
+    t_green = (time.perf_counter() - t0) * ntau
+    pts = []
+    t_pt = []
+    deadline = time.perf_counter() + budget_s
+    for p in [(0, 0), (5, 0), (10, 0)]:
+        t0 = time.perf_counter()
+        chi0_alg1(st, inp.lri, go, gv, [p])
+        t_pt.append(time.perf_counter() - t0)
+        pts.append(p)
+        if time.perf_counter() > deadline:
+            break
+    n = st.naux
+    rng = np.random.default_rng(0)
+    x = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * 1e-3
+    chi = -(x @ x.conj().T)
+    t0 = time.perf_counter()
+    energy.integrand_lu(chi, inp.vq[0])
+    t_lu = time.perf_counter() - t0
+    tp = statistics.median(t_pt)
+    npts = ntau * st.nk
+    t_energy = npts * tp + st.nk * ntau * t_lu + t_green
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"t_energy_s": t_energy, "t_point_s": tp, "t_lu_s": t_lu, "t_green_s": t_green, "cores": cores,
+            "sample": "chi0(R,tau) by Algorithm 1 on %d of %d (R,tau) points, ln det by LU on 1 of %d (q,omega), "
+                      "G on 1 of %d tau; extrapolated to one energy" % (len(pts), npts, st.nk * ntau, ntau)}
+
+
+# ------------------------------------------------------------------ arms
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, local = dist_init()
+    if rank != 0:
+        return 0
+    from paper_2407_19930_gb300 import synthetic as syn
+    from oracle import build as obuild, grid as ogrid
+    obuild.build()
+    inp = syn.config_graphene()
+    grid = ogrid.make_grid(16, *inp.delta_range)
+    per = []
+    for i in range(args.warmup + args.steps):
+        s = cpu_sample(inp, grid, budget_s=max(5.0, 60.0 / max(1, args.warmup + args.steps)))
+        if i >= args.warmup:
+            per.append(s)
+    t = statistics.median([s["t_energy_s"] for s in per])
+    v = 1.0 / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": per[0]["cores"], "kind": "oracle",
+                             "sample": per[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_init()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(local)
+    from paper_2407_19930_gb300 import build as lbuild
+    from paper_2407_19930_gb300 import librpa_gpu as L
+    from paper_2407_19930_gb300 import synthetic as syn
+    if rank == 0:
+        lbuild.build()
+    if dist:
+        dist.barrier()
+    L.load(build_if_missing=False)
+    inp = syn.config_graphene()
+    st = inp.st
+    stream = torch.cuda.Stream(device=local)
+    o = L.librpa_gpu_default_opts()
+    o.device = local
+    o.n_tau = 16
+    h = L.librpa_gpu_create(o, torch_stream=stream, torch_alloc=True)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    try:
+        L.set_inputs(h, inp)
+        for _ in range(args.warmup):
+            L.librpa_gpu_chi0(h)
+            L.librpa_gpu_ec(h)
+        # ---------------- device-resident timing
+        uuid = None
+        try:
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+        except Exception:
+            pass
+        clocks = ClockSampler(uuid)
+        launches = 0
+        stats = []
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        clocks.start()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            L.librpa_gpu_chi0(h)
+            s1 = L.librpa_gpu_get_stats(h)
+            ec, _, _ = L.librpa_gpu_ec(h)
+            s2 = L.librpa_gpu_get_stats(h)
+            launches += s2["launches"]
+            stats.append(s2)
+        ev1.record(stream)
+        barrier()
+        clk = clocks.stop()
+        t = ev0.elapsed_time(ev1) / 1e3
+        if dist:
+            tt = torch.tensor([t], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        value = args.steps * ws / t
+        # ---------------- end to end through host buffers
+        h2d = sum(C.nbytes for *_, C in inp.lri) + st.nk * (inp.wfc[0].real.nbytes * 2 + inp.eig[0].nbytes * 2) \
+            + st.nk * inp.vq[0].real.nbytes * 2
+        d2h = 8
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for I, K, R, C in inp.lri:
+                L.librpa_gpu_set_lri_coeffs(h, I, K, R, C)
+            for ik in range(st.nk):
+                L.librpa_gpu_set_green(h, 0, ik, inp.eig[ik], inp.occ[ik], inp.wfc[ik], inp.efermi)
+            for iq in range(st.nk):
+                L.librpa_gpu_set_coulomb(h, iq, inp.vq[iq])
+            L.librpa_gpu_chi0(h)
+            ec_e2e, _, _ = L.librpa_gpu_ec(h)
+        barrier()
+        te = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([te], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = args.e2e_steps * ws / te
+    finally:
+        L.librpa_gpu_destroy(h)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    s = stats[-1]
+    peaks, src = _peaks()
+    fp64_peak = peaks["bf16_tflops"] * NOMINAL_FP64_OVER_BF16 if src == "measured" else 1.9e3 * NOMINAL_FP64_OVER_BF16
+    fp64_peak_sus = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * NOMINAL_FP64_OVER_BF16
+    # dominant kernel by device time within the step
+    kern = {"k_dgemm_nt": (s["ms_gemm_chi0"], s["flop_gemm_chi0"], s["n_gemm_chi0"], "paper_2407_19930_gb300/csrc/k_chi0.cu"),
+            "k_zgemm": (s["ms_gemm_ec"], s["flop_gemm_ec"], s["n_gemm_ec"], "paper_2407_19930_gb300/csrc/k_zgemm.cu")}
+    name = max(kern, key=lambda k: kern[k][0])
+    ms, fl, nl, srcf = kern[name]
+    achieved = fl / (ms * 1e-3) / 1e12 if ms > 0 else None
+    tr = TRAFFIC.get(name)
+    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _src_sha(srcf) else None
+    step_ms = t / args.steps * 1e3 * ws / ws
+    chi0_tflops = s["flop_chi0"] / (s["ms_chi0"] * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded tight-binding KS data, LRI coefficients and Coulomb matrices "
+                                "of the paper's graphene/H2O workload shape)",
+        "config": {"workload": WORKLOAD, "atoms": st.natoms, "n_ao": st.nao, "n_aux": st.naux,
+                   "kmesh": "x".join(map(str, st.kmesh)), "n_tau": 16, "precision": "fp64",
+                   "l2": "inputs larger than L2: chi0(R,tau) %.1f GB and G %.2f GB are streamed every step"
+                         % (16 * st.nk * st.naux ** 2 * 8 / 1e9, 2 * 16 * st.nk * st.nao ** 2 * 8 / 1e9)},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "chi0_tflops": chi0_tflops,
+        "stage_ms": {"green": s["ms_green"], "chi0": s["ms_chi0"], "freq": s["ms_freq"], "ec": s["ms_ec"]},
+        "ec_ha": ec,
+        "roofline": {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak if achieved else None, "traffic": traffic,
+                     "peak_note": "FP64 MMA: %s BF16 dense burst peak x nominal FP64/BF16 (1.25/2250); "
+                                  "sustained-based peak %.3f" % (src, fp64_peak_sus),
+                     "launches": nl, "flop": fl},
+        "clocks": clk,
+    }
+    if ws == 1:
+        from oracle import build as obuild, grid as ogrid
+        obuild.build()
+        cb = cpu_sample(inp, ogrid.make_grid(16, *inp.delta_range))
+        line["cpu_baseline"] = {"value": 1.0 / cb["t_energy_s"], "unit": UNIT, "cores": cb["cores"],
+                                "kind": "oracle", "sample": cb["sample"],
+                                "chi0_tflops": s["flop_chi0"] / (16 * st.nk) / cb["t_point_s"] / 1e12}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * librpa_gpu -- C ABI of a GB300 (sm_103a) implementation of the low-scaling
+ * localized-RI (LRI) space-time RPA correlation energy path of
+ * "LibRPA: A Software Package for Low-scaling First-principles Calculations of
+ * Random Phase Approximation Electron Correlation Energy Based on Numerical Atomic
+ * Orbitals" (arXiv:2407.19930).
+ *
+ * The calls follow the paper's API groups (Appendix B, "API functions of LibRPA":
+ * environment setup, input parsing, computation), adapted to one GPU and no MPI:
+ *
+ *   paper                                              here
+ *   initialize_librpa_environment                      librpa_gpu_create
+ *   set_dimension + set_latvec_and_G + set_kgrids_*    librpa_gpu_set_structure
+ *   set_ao_basis_aux                                   librpa_gpu_set_lri_coeffs
+ *   set_wg_ekb_efermi + set_ao_basis_wfc               librpa_gpu_set_green
+ *   set_aux_bare_coulomb_k_*                           librpa_gpu_set_coulomb
+ *   (GreenX grids)                                     librpa_gpu_set_grid / librpa_gpu_build_grid
+ *   get_rpa_correlation_energy                         librpa_gpu_chi0 + librpa_gpu_ec
+ *   finalize_librpa_environment                        librpa_gpu_destroy
+ *
+ * Conventions used by every call:
+ *  - Energies in Hartree, lengths in bohr.  All floating-point arguments are FP64.
+ *  - Matrices are dense, row-major, C order; complex data is passed as separate
+ *    real and imaginary arrays of the same shape.
+ *  - The k-mesh is Gamma-centred: point (i1,i2,i3) has fractional coordinates
+ *    (i1/nk1, i2/nk2, i3/nk3) and flat index (i1*nk2 + i2)*nk3 + i3.  The same flat
+ *    order enumerates the Born-von Karman (BvK) cells R and the q-mesh.
+ *  - Bloch sums carry exp(+i k.R): H(k) = sum_R e^{ik.R} H(R), so the real-space
+ *    Green's function carries exp(-i k.R) (Sec. 2, Eq. green_mat) and
+ *    chi0(q) = sum_R e^{iq.R} chi0(R) (Sec. 2, R -> q transform).
+ *  - NAOs are ordered atom by atom (all NAOs of atom 0, then atom 1, ...); ABFs
+ *    likewise.  The NAO basis is orthonormal (S = I) and nbands = total NAOs.
+ *  - Host buffers are owned by the caller.  Every call that takes host input copies
+ *    it (to host staging or to the device) before returning; the caller may reuse
+ *    or free its buffers afterwards.  Output buffers are caller-allocated.
+ *  - Every call returns LIBRPA_OK (0) or a negative LIBRPA_E_* code and never exits
+ *    or throws; librpa_gpu_last_error() gives a one-line description.
+ *  - A handle is not thread-safe; use one handle per host thread.  All device work
+ *    of a handle is ordered on the handle's stream.
+ */
+#ifndef LIBRPA_GPU_H
+#define LIBRPA_GPU_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define LIBRPA_OK 0
+#define LIBRPA_E_ARG (-1)     /* an argument is out of range, NULL or inconsistent */
+#define LIBRPA_E_STATE (-2)   /* call order violated or a required input is missing */
+#define LIBRPA_E_NOMEM (-3)   /* device memory beyond the handle's HBM budget, or allocation failed */
+#define LIBRPA_E_CUDA (-4)    /* a CUDA runtime error (message in last_error) */
+#define LIBRPA_E_NOT_PD (-5)  /* a Cholesky pivot <= 0: V(q) or 1 - V^1/2 chi0 V^1/2 not positive definite */
+#define LIBRPA_E_TIMEOUT (-6) /* a bounded device wait ran out */
+#define LIBRPA_E_NUMERIC (-7) /* a non-finite or inconsistent intermediate (e.g. complex G for real input) */
+
+/* ---------------------------------------------------------------- precision modes */
+#define LIBRPA_FP64 0 /* every step in FP64 (FP64 tensor-core MMA for the contractions) */
+
+typedef struct librpa_gpu *librpa_gpu_t;
+
+/* Device allocator hooks.  alloc returns a device pointer aligned to >= 256 bytes,
+ * or NULL on failure; free releases it.  Both are called on the host thread that
+ * drives the handle.  NULL hooks select cudaMalloc / cudaFree. */
+typedef void *(*librpa_gpu_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*librpa_gpu_free_fn)(void *ptr, void *ctx);
+
+typedef struct {
+  int device;                    /* CUDA device ordinal */
+  void *stream;                  /* cudaStream_t to run on; NULL = a stream owned by the handle */
+  librpa_gpu_alloc_fn dev_alloc; /* NULL = cudaMalloc */
+  librpa_gpu_free_fn dev_free;   /* NULL = cudaFree */
+  void *alloc_ctx;               /* passed to dev_alloc / dev_free */
+  int n_tau;                     /* grid size (tau = omega points) when the library builds the grid */
+  int precision;                 /* LIBRPA_FP64 */
+  size_t hbm_budget;             /* bytes the handle may allocate; 0 = no limit */
+  int check_level;               /* 0 = none; 1 = check G is real and the pivots finite */
+} librpa_gpu_opts;
+
+/* Per-stage device times (ms, CUDA events on the handle's stream) and work counts of
+ * the most recent librpa_gpu_chi0 / librpa_gpu_ec call. */
+typedef struct {
+  double ms_green;         /* K1: G^occ / G^vir (R, tau) */
+  double ms_chi0;          /* K2: chi0(R, tau) contraction (Algorithm 1) */
+  double ms_freq;          /* K3 + K4: tau -> i omega and R -> q */
+  double ms_ec;            /* K5 + K6: Cholesky, ln det, E_c */
+  double flop_chi0;        /* algorithmic FP64 flops of K2 (no padding), see the design notes */
+  double flop_ec;          /* algorithmic FP64 flops of K5 */
+  double ms_gemm_chi0;     /* device time of the FP64 MMA GEMM launches of K2 (sum of per-launch events) */
+  double flop_gemm_chi0;   /* algorithmic flops of those launches (2 M N K, no padding) */
+  long long n_gemm_chi0;   /* number of those launches */
+  double ms_gemm_ec;       /* device time of the complex GEMM launches of K5 */
+  double flop_gemm_ec;     /* algorithmic flops of those launches (8 per complex MAC on the triangle) */
+  long long n_gemm_ec;     /* number of those launches */
+  long long launches;      /* kernels launched by the call */
+  size_t bytes_device;     /* device bytes held by the handle */
+} librpa_gpu_stats;
+
+/* Fill *o with defaults: device 0, own stream, cudaMalloc, n_tau = 16, FP64,
+ * no budget, check_level 1. */
+void librpa_gpu_default_opts(librpa_gpu_opts *o);
+
+/* Environment setup (paper: initialize_librpa_environment).  Creates a handle
+ * bound to o->device.  *h is set to NULL on failure.
+ * Errors: E_ARG (h or o NULL, bad device or n_tau < 1 or > 64, unknown precision),
+ *         E_CUDA. */
+int librpa_gpu_create(librpa_gpu_t *h, const librpa_gpu_opts *o);
+
+/* Structure and k-mesh (paper: set_dimension, set_latvec_and_G, set_kgrids_kvec_tot).
+ *   lat[9]   lattice vectors as rows a1, a2, a3 (bohr);
+ *   pos      [natoms][3] Cartesian positions (bohr);
+ *   n_ao     [natoms] NAOs per atom (1..64); n_aux [natoms] ABFs per atom (1..256);
+ *   nk1..nk3 Gamma-centred k-mesh (each >= 1); nspins must be 1 (spin factor s = 2);
+ *   r_cut    LRI cutoff (bohr): set_lri_coeffs rejects blocks whose atoms are farther apart.
+ * Resets every other input of the handle.
+ * Errors: E_ARG. */
+int librpa_gpu_set_structure(librpa_gpu_t h, int natoms, const double lat[9], const double *pos,
+                             const int *n_ao, const int *n_aux, int nk1, int nk2, int nk3,
+                             int nspins, double r_cut);
+
+/* LRI expansion coefficients (paper: set_ao_basis_aux; Sec. 2, Eq. LRI).
+ *   C [n_aux(I)][n_ao(I)][n_ao(K)] row-major = C^{mu(0)}_{i(0), k(R)}: mu and i on atom I
+ *   in the home cell, k on atom K in cell R.  R is a true lattice vector (not folded
+ *   into the BvK cell).  The neighbour set N[I] of Algorithm 1 is the set of (K, R)
+ *   given here.  Setting the same (I, K, R) again replaces the block.
+ * Errors: E_STATE (no structure), E_ARG (indices, |tau_K + R - tau_I| > r_cut, C NULL). */
+int librpa_gpu_set_lri_coeffs(librpa_gpu_t h, int I, int K, const int R[3], const double *C);
+
+/* KS eigen-data of one k point (paper: set_wg_ekb_efermi + set_ao_basis_wfc;
+ * Sec. 2, Eq. green_mat).
+ *   eig [nbands] (Ha), occ [nbands] occupation per spin-orbital in [0, 1];
+ *   wfc_re, wfc_im [nbands][n_ao_total]: wfc[n][i] = c_{i,n}(k);
+ *   efermi: the chemical potential mu (Ha).
+ * nbands must equal the total number of NAOs.  The path assumes time-reversal
+ * symmetry (real H(R)), which makes G(R, tau) real; with check_level >= 1 librpa_gpu_chi0
+ * returns E_NUMERIC if G has an imaginary part above 1e-10 relative.
+ * Errors: E_STATE (no structure), E_ARG. */
+int librpa_gpu_set_green(librpa_gpu_t h, int ispin, int ik, int nbands, const double *eig,
+                         const double *occ, const double *wfc_re, const double *wfc_im,
+                         double efermi);
+
+/* Coulomb matrix of one q point in the ABF basis (paper: set_aux_bare_coulomb_k_*;
+ * Sec. 2, Eq. Coulomb_matr_kspace): V_re, V_im [N_aux][N_aux], Hermitian positive
+ * definite.  Copied to the device during the call.
+ * Errors: E_STATE (no structure), E_ARG, E_NOMEM, E_CUDA. */
+int librpa_gpu_set_coulomb(librpa_gpu_t h, int iq, const double *V_re, const double *V_im);
+
+/* Optional grid override (Sec. 2, cosine transform):
+ *   tau [ntau] (1/Ha), omega [nomega] (Ha), w_omega [nomega] quadrature weights of
+ *   int_0^inf d omega, gamma [nomega][ntau] = the real transform matrix Gamma_kj with
+ *   chi0(R, i omega_k) = sum_j Gamma_kj chi0(R, tau_j)  (the paper's
+ *   -i gamma_jk cos(omega_k tau_j) with the -i factors of G taken out).
+ * ntau == nomega required (1..64).  Without this call librpa_gpu_chi0 builds the grid
+ * with librpa_gpu_build_grid(opts.n_tau, Delta_min, Delta_max) from the KS spectrum.
+ * Errors: E_STATE (no structure), E_ARG. */
+int librpa_gpu_set_grid(librpa_gpu_t h, int ntau, const double *tau, int nomega,
+                        const double *omega, const double *w_omega, const double *gamma);
+
+/* Stateless grid construction (host; Sec. 2: non-uniform tau/omega grids and gamma
+ * from an L2 minimisation).  For n points and transition energies in [dmin, dmax]:
+ *   omega_k, w_omega: n-point Gauss-Legendre rule mapped to (0, inf) by
+ *     omega = w0 (1 + t) / (1 - t), w0 = sqrt(dmin dmax);
+ *   tau_j: the same rule mapped with 1 / w0;
+ *   gamma[k][j]: least-squares fit, in relative error over 1000 log-spaced D in
+ *     [dmin, dmax], of 2D / (D^2 + omega_k^2) by sum_j gamma[k][j] exp(-D tau_j),
+ *     by SVD with singular values below 1e-12 s_max dropped.
+ * Outputs are caller-allocated: tau[n], omega[n], w_omega[n], gamma[n][n].
+ * Errors: E_ARG (n < 1 or > 64, dmin <= 0, dmax < dmin, NULL outputs). */
+int librpa_gpu_build_grid(int n, double dmin, double dmax, double *tau, double *omega,
+                          double *w_omega, double *gamma);
+
+/* Grid in use by the handle (after set_grid or after librpa_gpu_chi0 built it).
+ * Outputs as in librpa_gpu_build_grid; *n receives the grid size.
+ * Errors: E_STATE (no grid yet), E_ARG. */
+int librpa_gpu_get_grid(librpa_gpu_t h, int *n, double *tau, double *omega, double *w_omega,
+                        double *gamma);
+
+/* Response function (Sec. 2: Eq. green_mat, Algorithm 1, cosine and Fourier transforms):
+ *   G^occ, G^vir(R, tau_j)  ->  chi0_{mu nu}(R, tau_j)  ->  chi0(R, i omega_k)  ->  chi0(q, i omega_k).
+ * Requires set_structure, set_green for every k and set_lri_coeffs for at least one
+ * block per atom.  out_re / out_im may be NULL; otherwise each receives
+ * [nq][nomega][N_aux][N_aux] (N_aux^2 * nq * nomega doubles).  The device copies of
+ * G, chi0(R, tau) and chi0(q, i omega) stay on the device for librpa_gpu_ec and the
+ * librpa_gpu_get_* calls until the next librpa_gpu_chi0 or set_structure.
+ * Errors: E_STATE, E_NOMEM, E_CUDA, E_NUMERIC. */
+int librpa_gpu_chi0(librpa_gpu_t h, double *out_re, double *out_im);
+
+/* RPA correlation energy (Sec. 2, Eq. for E_c with Pi = chi0 V and Tr ln = ln det):
+ *   E_c = (1/2 pi) sum_q w_q sum_k W_k [ln det(1 - Pi(q, i omega_k)) + Tr Pi(q, i omega_k)]
+ * with w_q = 1/N_q.  ln det(1 - chi0 V) is computed as ln det(I - L^H chi0 L) with the
+ * Cholesky factor V = L L^H and a blocked Cholesky of I - L^H chi0 L (FP64).
+ *   ec    -> E_c in Ha per cell;
+ *   ec_q  -> [nq] per-q contributions (nullable);  ec_w -> [nomega] per-frequency (nullable).
+ * Requires librpa_gpu_chi0 and set_coulomb for every q.
+ * Errors: E_STATE, E_NOT_PD, E_NOMEM, E_CUDA. */
+int librpa_gpu_ec(librpa_gpu_t h, double *ec, double *ec_q, double *ec_w);
+
+/* Inspection of intermediates kept on the device (host copies of one slice):
+ *   get_green:      go, gv  [n_ao_total][n_ao_total] at (itau, iR);
+ *   get_chi0_tau:   out     [N_aux][N_aux] = chi0(R, tau) at (itau, iR);
+ *   get_chi0_freq:  re, im  [N_aux][N_aux] = chi0(q, i omega) at (iq, iomega).
+ * Errors: E_STATE (not computed yet), E_ARG, E_CUDA. */
+int librpa_gpu_get_green(librpa_gpu_t h, int itau, int iR, double *go, double *gv);
+int librpa_gpu_get_chi0_tau(librpa_gpu_t h, int itau, int iR, double *out);
+int librpa_gpu_get_chi0_freq(librpa_gpu_t h, int iq, int iomega, double *re, double *im);
+
+/* Stage timings and counters of the last chi0 / ec calls. Errors: E_ARG. */
+int librpa_gpu_get_stats(librpa_gpu_t h, librpa_gpu_stats *s);
+
+/* One-line description of the last error on h (never NULL; "" after success). */
+const char *librpa_gpu_last_error(librpa_gpu_t h);
+
+/* Environment teardown (paper: finalize_librpa_environment): frees every device and
+ * host resource of h.  NULL is ignored. */
+void librpa_gpu_destroy(librpa_gpu_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBRPA_GPU_H */

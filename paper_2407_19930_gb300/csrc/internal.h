@@ -1,0 +1,184 @@
+// Internal declarations of librpa_gpu (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/librpa_gpu.h"
+
+namespace librpa {
+
+// ----------------------------------------------------------------- error plumbing
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define LR_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      throw ::librpa::Error{LIBRPA_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+// ----------------------------------------------------------------- BvK helpers
+struct Mesh {
+  int n1 = 1, n2 = 1, n3 = 1;
+  int size() const { return n1 * n2 * n3; }
+  static int fold(int x, int n) { int r = x % n; return r < 0 ? r + n : r; }
+  int index(int a, int b, int c) const { return (fold(a, n1) * n2 + fold(b, n2)) * n3 + fold(c, n3); }
+  void split(int i, int &a, int &b, int &c) const { a = i / (n2 * n3); b = (i / n3) % n2; c = i % n3; }
+};
+
+// ----------------------------------------------------------------- device buffers
+struct Handle;
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+// ----------------------------------------------------------------- chi0 plan (Algorithm 1 data layout)
+// Neighbour entry of atom U: block C[U, K, R1] (K an atom, R1 a lattice vector).
+struct NbEntry {
+  int K;
+  int R[3];
+  int col;        // first column of this block inside the packed matrix of U (0 .. m_U)
+  int ucol;       // first column of (K, R1) inside the union list (0 .. M_all)
+};
+
+struct Chi0Plan {
+  int natoms = 0, nao = 0, naux = 0;
+  std::vector<int> n_ao, n_aux, ao_off, aux_off;
+  std::vector<std::vector<NbEntry>> nb;   // per atom U: N[U] sorted by (K, R)
+  std::vector<int> m;                     // m_U = sum over N[U] of n_ao(K)
+  std::vector<long long> cp_off;          // offset of packed C_U [n_aux_U][n_U][m_U] in the C arena
+  long long cp_total = 0;
+  // union of all (K, R1) over N[U], U in the home cell
+  std::vector<std::tuple<int, int, int, int>> uni;  // (K, R0, R1, R2)
+  std::vector<int> uni_col;               // first column of each union block
+  int m_all = 0;
+  // device index tables (int arrays; see k_chi0.cu for their meaning)
+  DevBuf d_lam;      // per-V columns of the packed C: {L, R0, R1, R2, l, ao(L)+l} x sum m_V
+  DevBuf d_uni;      // union columns: {K, R0, R1, R2, k, ao(K)+k} x M_all
+  DevBuf d_kap;      // per-U columns: {K, R0, R1, R2, ao(K)+k, ucol} x sum m_U
+  std::vector<long long> lam_off, kap_off;   // element offsets of each atom's part
+  // workspace element offsets (per (R, tau) point)
+  std::vector<long long> bg_off, ag_off, n_off, x_off, o_off;
+  long long bg_sz = 0, ag_sz = 0, n_sz = 0, x_sz = 0, o_sz = 0;
+  double flop_per_point = 0;  // algorithmic FP64 flops per (R, tau) point
+  // device copies of the per-atom tables, point list, workspace and GEMM descriptors
+  DevBuf t_n_ao, t_n_aux, t_ao_off, t_aux_off, t_m, t_lam_off, t_kap_off, t_bg_off, t_ag_off, t_n_off, t_x_off,
+      t_o_off, t_pts, ws, gargs1, gargs2;
+  std::vector<DevBuf *> all() {
+    return {&d_lam, &d_uni, &d_kap, &t_n_ao, &t_n_aux, &t_ao_off, &t_aux_off, &t_m, &t_lam_off, &t_kap_off,
+            &t_bg_off, &t_ag_off, &t_n_off, &t_x_off, &t_o_off, &t_pts, &ws, &gargs1, &gargs2};
+  }
+};
+
+// ----------------------------------------------------------------- handle
+struct Handle {
+  librpa_gpu_opts opts{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error;
+  size_t bytes_held = 0;
+  std::map<void *, size_t> allocs;
+
+  // structure
+  bool have_structure = false;
+  int natoms = 0, nao = 0, naux = 0, nspins = 1;
+  double lat[9]{};
+  std::vector<double> pos;
+  std::vector<int> n_ao, n_aux, ao_off, aux_off;
+  Mesh mesh;
+  double r_cut = 0;
+
+  // inputs (host staging)
+  std::map<std::tuple<int, int, int, int, int>, std::vector<double>> lri;  // (I,K,R0,R1,R2) -> C
+  std::vector<double> eig, occ;            // [nk][nb] host copies (grid range, band ranges)
+  std::vector<char> have_k;
+  std::vector<double> efermi_k;
+  std::vector<char> have_q;
+
+  // grid
+  bool have_grid = false, grid_user = false;
+  int ntau = 0;
+  std::vector<double> tau, omega, w_omega, gamma;
+
+  // device state
+  DevBuf d_vq;        // [nq][naux][naux] complex interleaved
+  DevBuf d_wfc;       // [nk][nb][nao] complex interleaved: wfc[k][n][i] = c_in(k)
+  DevBuf d_eig, d_occ;  // [nk][nb]
+  DevBuf d_g;         // G: [2][ntau][nR][nao][nao]  (0 = occ, 1 = vir)
+  DevBuf d_chi_tau;   // [ntau][nR][naux][naux]
+  DevBuf d_chi_qw;    // [nq][nomega][naux][naux] complex interleaved
+  DevBuf d_cpack;     // packed LRI coefficients
+  DevBuf zgemm_args;  // descriptors and tile lists of batched GEMM launches
+  DevBuf gemm_args;
+  DevBuf work;        // per-call workspace
+  bool chi0_done = false, lri_dirty = true;
+  Chi0Plan plan;
+
+  librpa_gpu_stats stats{};
+
+  // event-timed launches of the dense GEMM kernels, resolved after a stream synchronisation
+  struct Timed {
+    cudaEvent_t a, b;
+    double flops;
+    int kind;  // 0 = FP64 DMMA GEMM of the chi0 contraction, 1 = complex GEMM of the energy stage
+  };
+  std::vector<Timed> timed;
+  void resolve_timers();
+
+  void *dalloc(size_t bytes);
+  void dfree(void *p);
+  void ensure(DevBuf &b, size_t bytes);
+  void release(DevBuf &b);
+};
+
+// ----------------------------------------------------------------- grid (host, grid.cpp)
+int build_grid(int n, double dmin, double dmax, double *tau, double *omega, double *w_omega,
+               double *gamma);
+
+// ----------------------------------------------------------------- kernels
+// K1 (k_green.cu): G^occ and G^vir for all (tau, R).  Returns max |Im G| / max |G|.
+double green_build(Handle &h);
+// K2 (k_chi0.cu)
+void chi0_plan(Handle &h);
+void chi0_run(Handle &h, double *ms_gemm);
+// K3 + K4 (k_freq.cu)
+void freq_transform(Handle &h);
+// K5 + K6 (k_ec.cu); returns LIBRPA_OK or LIBRPA_E_NOT_PD
+int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w);
+
+// generic batched complex FP64 GEMM (k_zgemm.cu), used by K1 and K5
+struct ZGemm {
+  const double2 *A;   // row-major, lda
+  const double2 *B;   // row-major, ldb
+  double2 *C;         // row-major, ldc
+  const double *kscale;  // optional per-k real scale of the product (length K), or nullptr
+  int M, N, K, lda, ldb, ldc;
+  double2 alpha, beta;
+};
+// op(A): transA (A stored [K][M]) / conjA; op(B): transB (B stored [N][K]) / conjB.
+// kfrom: 0 = full K range, 1 = start at the tile's first row (A upper-zero rows),
+// 2 = start at the tile's first column (B lower-triangular, zero above the diagonal).
+// lower_only: skip output tiles strictly above the diagonal.
+struct ZGemmFlags {
+  bool transA = false, conjA = false, transB = false, conjB = false;
+  int kfrom = 0;
+  bool lower_only = false;
+};
+// timed_kind >= 0 records the launch with CUDA events as Handle::Timed{kind, algorithmic flops}.
+void zgemm_batched(const std::vector<ZGemm> &batch, const ZGemmFlags &f, cudaStream_t s,
+                   Handle &h, int timed_kind = -1, double flops = 0.0);
+
+long long &launch_counter();
+
+}  // namespace librpa

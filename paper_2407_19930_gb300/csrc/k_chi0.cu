@@ -1,0 +1,548 @@
+// K2: chi0_{mu nu}(R, tau) by the atom-pair contraction of Algorithm 1 (Sec. 2).
+//
+// Per (R, tau) point, with A = G^vir (the paper's G(i tau)) and B = G^occ (G(-i tau)):
+//
+//   N^{B,nu}_{jk}(K R1) = sum_{(L,R2') in N[V]} sum_l C[V,L,R2']_{nu j l} B_{lk}(R1 - R - R2')
+//   X^{A,nu}_{ij}       = sum_{(L,R2') in N[V]} sum_l C[V,L,R2']_{nu j l} A_{il}(R + R2')
+//   O^nu_{ik}(K R1)     = sum_{j in V} A_ij(R) N^{B,nu}_jk + B_ij(R) N^{A,nu}_jk
+//                                  + B_jk(R1 - R) X^{A,nu}_ij + A_jk(R1 - R) X^{B,nu}_ij
+//   chi0_{mu nu}(R, tau) = -s sum_{(K,R1) in N[U]} sum_{ik} C[U,K,R1]_{mu i k} O^nu_{ik}(K R1)
+//
+// i.e. Algorithm 1's M + M*(-i tau) + Z + Z*(-i tau) with the paper's -i factors taken out
+// (real convention: G(i tau) = +i G^vir, G(-i tau) = -i G^occ).  Two exact restructurings
+// of the loop nest: N depends on (V, R, K R1) but not on U, so it is computed once per V for
+// every (K, R1) in the union of all N[U]; X depends on (V, R) only, so it is computed once
+// per V for every NAO i of the home cell.  All contractions are then dense GEMMs:
+//
+//   N-step  (per V, per G):  N_V = Cpack_V [n_aux_V n_V x m_V]  .  Bg_V^T  [m_V x M_all]
+//   X-step  (per V, per G):  X_V = Ag_V [n_ao x m_V]            .  Cpack_V^T [m_V x n_aux_V n_V]
+//   final   (per U):         chi0[U rows] = -s Cpack_U [n_aux_U x n_U m_U] . O_U^T [n_U m_U x N_aux]
+//
+// where Cpack_U[mu][i][(K,R1,k)] packs the blocks C[U,K,R1] side by side, Bg_V and Ag_V are
+// G blocks gathered at the lattice vectors above, and O_U[nu][(i,(K,R1,k))] is assembled by a
+// dedicated kernel.  The GEMMs run on the FP64 tensor cores (mma.sync m8n8k4 .f64).
+#include <algorithm>
+#include <cstring>
+#include <set>
+#include <vector>
+
+#include "internal.h"
+
+namespace librpa {
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// batched FP64 "NT" GEMM on the tensor cores: C[m][n] = alpha sum_k A[m][k] B[n][k] + beta C
+struct DGemm {
+  const double *A, *B;
+  double *C;
+  int M, N, K, lda, ldb, ldc;
+  double alpha, beta;
+};
+struct DTile {
+  int e, m0, n0;
+};
+
+constexpr int GM = 64, GN = 64, GK = 16, GT = 128, GPAD = GK + 1;
+
+__device__ __forceinline__ void dmma_m8n8k4(double &c0, double &c1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(c0), "+d"(c1)
+               : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(GT) k_dgemm_nt(const DGemm *__restrict__ gs, const DTile *__restrict__ tiles) {
+  const DTile t = tiles[blockIdx.x];
+  const DGemm g = gs[t.e];
+  __shared__ double As[GM][GPAD];
+  __shared__ double Bs[GN][GPAD];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int gid = lane >> 2, tig = lane & 3;
+  double acc[4][4][2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c][0] = acc[r][c][1] = 0.0;
+  for (int k0 = 0; k0 < g.K; k0 += GK) {
+#pragma unroll
+    for (int s = 0; s < (GM * GK) / GT; ++s) {
+      const int e = tid + GT * s, row = e / GK, k = e % GK;
+      const int gm = t.m0 + row, gn = t.n0 + row, gk = k0 + k;
+      As[row][k] = (gm < g.M && gk < g.K) ? g.A[(size_t)gm * g.lda + gk] : 0.0;
+      Bs[row][k] = (gn < g.N && gk < g.K) ? g.B[(size_t)gn * g.ldb + gk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; kk += 4) {
+      double a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[wm * 32 + r * 8 + gid][kk + tig];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[wn * 32 + c * 8 + gid][kk + tig];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dmma_m8n8k4(acc[r][c][0], acc[r][c][1], a[r], b[c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int gm = t.m0 + wm * 32 + r * 8 + gid;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gn = t.n0 + wn * 32 + c * 8 + tig * 2 + h;
+        if (gn >= g.N) continue;
+        double *p = g.C + (size_t)gm * g.ldc + gn;
+        const double v = g.alpha * acc[r][c][h];
+        *p = g.beta == 0.0 ? v : v + g.beta * *p;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// gathers.  Column tables hold 6 ints per column: {atom, R0, R1, R2, orbital, ao(atom)+orbital}.
+struct Point {
+  int iR, itau;
+  int R[3];
+};
+
+// Bg[p][g][V][kappa][lambda] = G^g(tau_p)[bvk(R1_kappa - R_p - R2'_lambda)][ao_lambda][ao_kappa]
+__global__ void k_gather_bg(const double *__restrict__ G, size_t g_gstride, const Point *__restrict__ pts,
+                            const int *__restrict__ uni, const int *__restrict__ lam, const long long *lam_off,
+                            const int *m, const long long *bg_off, int natoms, int m_all, int nR_stride,
+                            int nao, int n1, int n2, int n3, long long bg_sz_g, long long bg_sz_p, double *Bg) {
+  const int V = blockIdx.y % natoms;
+  const int g = (blockIdx.y / natoms) % 2;
+  const int p = blockIdx.y / (2 * natoms);
+  const int mV = m[V];
+  const long long n = (long long)m_all * mV;
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  const int kap = (int)(x / mV), l = (int)(x % mV);
+  const int *u = uni + 6 * kap;
+  const int *c = lam + 6 * (lam_off[V] + l);
+  const Point pt = pts[p];
+  auto fold = [](int a, int nn) { int r = a % nn; return r < 0 ? r + nn : r; };
+  const int iR = (fold(u[1] - pt.R[0] - c[1], n1) * n2 + fold(u[2] - pt.R[1] - c[2], n2)) * n3 +
+                 fold(u[3] - pt.R[2] - c[3], n3);
+  const double *Gp = G + g * g_gstride + ((size_t)pt.itau * nR_stride + iR) * nao * nao;
+  Bg[p * bg_sz_p + g * bg_sz_g + bg_off[V] + x] = Gp[(size_t)c[5] * nao + u[5]];
+}
+
+// Ag[p][g][V][i][lambda] = G^g(tau_p)[bvk(R_p + R2'_lambda)][i][ao_lambda]
+__global__ void k_gather_ag(const double *__restrict__ G, size_t g_gstride, const Point *__restrict__ pts,
+                            const int *__restrict__ lam, const long long *lam_off, const int *m,
+                            const long long *ag_off, int natoms, int nR_stride, int nao, int n1, int n2, int n3,
+                            long long ag_sz_g, long long ag_sz_p, double *Ag) {
+  const int V = blockIdx.y % natoms;
+  const int g = (blockIdx.y / natoms) % 2;
+  const int p = blockIdx.y / (2 * natoms);
+  const int mV = m[V];
+  const long long n = (long long)nao * mV;
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  const int i = (int)(x / mV), l = (int)(x % mV);
+  const int *c = lam + 6 * (lam_off[V] + l);
+  const Point pt = pts[p];
+  auto fold = [](int a, int nn) { int r = a % nn; return r < 0 ? r + nn : r; };
+  const int iR = (fold(pt.R[0] + c[1], n1) * n2 + fold(pt.R[1] + c[2], n2)) * n3 + fold(pt.R[2] + c[3], n3);
+  const double *Gp = G + g * g_gstride + ((size_t)pt.itau * nR_stride + iR) * nao * nao;
+  Ag[p * ag_sz_p + g * ag_sz_g + ag_off[V] + x] = Gp[(size_t)i * nao + c[5]];
+}
+
+// ---------------------------------------------------------------------------------------
+// O assembly.  One CTA per (point, U, V, 64-column chunk of U's packed columns); 256
+// threads = 64 columns x 4 row groups.  Shared memory: Lm[n_U][2 n_V] = [A_UV(R) | B_UV(R)],
+// LX[n_U][2 n_V] = [X^A_nu | X^B_nu] rows of U, RG[2 n_V][64] = [B_{V,kap}(R1-R); A_{V,kap}(R1-R)].
+struct OArgs {
+  const double *G;       // [2][ntau][nR][nao][nao]
+  size_t g_gstride;
+  int nR_stride, nao, natoms, naux, n1, n2, n3;
+  const Point *pts;
+  const int *n_ao, *n_aux, *ao_off, *aux_off, *m;
+  const int *kap;            // per-U column table {K, R0, R1, R2, ao(K)+k, union column}
+  const long long *kap_off;
+  const double *N;           // [P][2][sum_V n_aux_V n_V M_all]
+  const long long *n_off;
+  long long n_sz_g, n_sz_p;
+  int m_all;
+  const double *X;           // [P][2][sum_V nao n_aux_V n_V]
+  const long long *x_off;
+  long long x_sz_g, x_sz_p;
+  double *O;                 // [P][sum_U naux n_U m_U]
+  const long long *o_off;
+  long long o_sz_p;
+};
+
+__global__ void __launch_bounds__(256) k_oassemble(OArgs a) {
+  extern __shared__ double sm[];
+  const int V = blockIdx.y % a.natoms;
+  const int U = (blockIdx.y / a.natoms) % a.natoms;
+  const int p = blockIdx.y / (a.natoms * a.natoms);
+  const int mU = a.m[U];
+  const int c0 = blockIdx.x * 64;
+  if (c0 >= mU) return;
+  const int nU = a.n_ao[U], nV = a.n_ao[V], two = 2 * nV;
+  double *Lm = sm;                 // [nU][two]
+  double *LX = Lm + nU * two;      // [nU][two]
+  double *RG = LX + nU * two;      // [two][64]
+  const Point pt = a.pts[p];
+  const int tid = threadIdx.x, col = tid & 63, rg = tid >> 6;
+  const size_t n2 = (size_t)a.nao * a.nao;
+  const double *GB = a.G + ((size_t)pt.itau * a.nR_stride) * n2;                 // G^occ(tau)
+  const double *GA = a.G + a.g_gstride + ((size_t)pt.itau * a.nR_stride) * n2;   // G^vir(tau)
+  const int aoU = a.ao_off[U], aoV = a.ao_off[V];
+  // Lm: [A_UV(R) | B_UV(R)]
+  for (int e = tid; e < nU * two; e += 256) {
+    const int i = e / two, t = e % two;
+    const double *Gs = t < nV ? GA : GB;
+    Lm[e] = Gs[((size_t)pt.iR) * n2 + (size_t)(aoU + i) * a.nao + aoV + (t % nV)];
+  }
+  // RG for this thread's column
+  const int kc = c0 + col;
+  const bool live = kc < mU;
+  int ucol = 0;
+  if (live) {
+    const int *kp = a.kap + 6 * (a.kap_off[U] + kc);
+    auto fold = [](int x, int nn) { int r = x % nn; return r < 0 ? r + nn : r; };
+    const int iR = (fold(kp[1] - pt.R[0], a.n1) * a.n2 + fold(kp[2] - pt.R[1], a.n2)) * a.n3 +
+                   fold(kp[3] - pt.R[2], a.n3);
+    ucol = kp[5];
+    for (int t = rg; t < two; t += 4) {
+      const double *Gs = t < nV ? GB : GA;
+      RG[t * 64 + col] = Gs[(size_t)iR * n2 + (size_t)(aoV + (t % nV)) * a.nao + kp[4]];
+    }
+  }
+  const int nauxV = a.n_aux[V];
+  const double *NB = a.N + p * a.n_sz_p + a.n_off[V];                 // N[G^occ]: g = 0
+  const double *NA = a.N + p * a.n_sz_p + a.n_sz_g + a.n_off[V];      // N[G^vir]: g = 1
+  const double *XB = a.X + p * a.x_sz_p + a.x_off[V];                 // X[G^occ]
+  const double *XA = a.X + p * a.x_sz_p + a.x_sz_g + a.x_off[V];      // X[G^vir]
+  const int ldx = nauxV * nV;
+  double *Ob = a.O + p * a.o_sz_p + a.o_off[U];
+  const int ldo = nU * mU;
+  for (int nu = 0; nu < nauxV; ++nu) {
+    __syncthreads();   // previous LX consumed; Lm and RG written
+    for (int e = tid; e < nU * two; e += 256) {
+      const int i = e / two, t = e % two;
+      const double *Xs = t < nV ? XA : XB;
+      LX[e] = Xs[(size_t)(aoU + i) * ldx + nu * nV + (t % nV)];
+    }
+    __syncthreads();
+    if (!live) continue;
+    double acc[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc[r] = 0.0;
+    for (int t = 0; t < two; ++t) {
+      const double *Ns = t < nV ? NB : NA;
+      const double rn = Ns[(size_t)(nu * nV + (t % nV)) * a.m_all + ucol];
+      const double rgv = RG[t * 64 + col];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int i = rg + 4 * r;
+        if (i < nU) acc[r] = fma(Lm[i * two + t], rn, fma(LX[i * two + t], rgv, acc[r]));
+      }
+    }
+    double *orow = Ob + (size_t)(a.aux_off[V] + nu) * ldo;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = rg + 4 * r;
+      if (i < nU) orow[(size_t)i * mU + kc] = acc[r];
+    }
+  }
+}
+
+template <class T>
+T *upload(Handle &h, DevBuf &b, const std::vector<T> &v) {
+  h.ensure(b, std::max<size_t>(1, v.size()) * sizeof(T));
+  if (!v.empty()) LR_CUDA(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return (T *)b.p;
+}
+
+void dgemm_batched(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, DevBuf &args) {
+  std::vector<DTile> tiles;
+  for (int e = 0; e < (int)batch.size(); ++e)
+    for (int m0 = 0; m0 < batch[e].M; m0 += GM)
+      for (int n0 = 0; n0 < batch[e].N; n0 += GN) tiles.push_back({e, m0, n0});
+  if (tiles.empty()) return;
+  const size_t b1 = batch.size() * sizeof(DGemm), off2 = (b1 + 255) / 256 * 256, b2 = tiles.size() * sizeof(DTile);
+  std::vector<char> host(off2 + b2);
+  std::memcpy(host.data(), batch.data(), b1);
+  std::memcpy(host.data() + off2, tiles.data(), b2);
+  h.ensure(args, off2 + b2);
+  LR_CUDA(cudaMemcpyAsync(args.p, host.data(), off2 + b2, cudaMemcpyHostToDevice, s));
+  double flops = 0;
+  for (const DGemm &g : batch) flops += 2.0 * g.M * g.N * g.K;
+  Handle::Timed t{nullptr, nullptr, flops, 0};
+  LR_CUDA(cudaEventCreate(&t.a));
+  LR_CUDA(cudaEventCreate(&t.b));
+  LR_CUDA(cudaEventRecord(t.a, s));
+  k_dgemm_nt<<<(unsigned)tiles.size(), GT, 0, s>>>((const DGemm *)args.p,
+                                                   (const DTile *)((const char *)args.p + off2));
+  LR_CUDA(cudaEventRecord(t.b, s));
+  h.timed.push_back(t);
+  ++launch_counter();
+  LR_CUDA(cudaGetLastError());
+}
+
+
+}  // namespace
+
+void chi0_plan(Handle &h) {
+  Chi0Plan &P = h.plan;
+  const int nat = h.natoms;
+  P.natoms = nat;
+  P.nao = h.nao;
+  P.naux = h.naux;
+  P.n_ao = h.n_ao;
+  P.n_aux = h.n_aux;
+  P.ao_off = h.ao_off;
+  P.aux_off = h.aux_off;
+  P.nb.assign(nat, {});
+  for (auto &kv : h.lri) {
+    int I, K, r0, r1, r2;
+    std::tie(I, K, r0, r1, r2) = kv.first;
+    NbEntry e{K, {r0, r1, r2}, 0, 0};
+    P.nb[I].push_back(e);
+  }
+  std::set<std::tuple<int, int, int, int>> uni;
+  P.m.assign(nat, 0);
+  for (int U = 0; U < nat; ++U) {
+    // std::map iteration already orders by (K, R)
+    int col = 0;
+    for (auto &e : P.nb[U]) {
+      e.col = col;
+      col += h.n_ao[e.K];
+      uni.insert(std::make_tuple(e.K, e.R[0], e.R[1], e.R[2]));
+    }
+    P.m[U] = col;
+  }
+  P.uni.assign(uni.begin(), uni.end());
+  P.uni_col.resize(P.uni.size());
+  int mc = 0;
+  std::map<std::tuple<int, int, int, int>, int> ucol;
+  for (size_t b = 0; b < P.uni.size(); ++b) {
+    P.uni_col[b] = mc;
+    ucol[P.uni[b]] = mc;
+    mc += h.n_ao[std::get<0>(P.uni[b])];
+  }
+  P.m_all = mc;
+  for (int U = 0; U < nat; ++U)
+    for (auto &e : P.nb[U]) e.ucol = ucol[std::make_tuple(e.K, e.R[0], e.R[1], e.R[2])];
+  // packed coefficients
+  P.cp_off.assign(nat + 1, 0);
+  for (int U = 0; U < nat; ++U) P.cp_off[U + 1] = P.cp_off[U] + (long long)h.n_aux[U] * h.n_ao[U] * P.m[U];
+  P.cp_total = P.cp_off[nat];
+  std::vector<double> cp(P.cp_total, 0.0);
+  for (int U = 0; U < nat; ++U) {
+    const int nU = h.n_ao[U], mU = P.m[U];
+    for (auto &e : P.nb[U]) {
+      const std::vector<double> &C = h.lri.at(std::make_tuple(U, e.K, e.R[0], e.R[1], e.R[2]));
+      const int nK = h.n_ao[e.K];
+      for (int mu = 0; mu < h.n_aux[U]; ++mu)
+        for (int i = 0; i < nU; ++i)
+          for (int k = 0; k < nK; ++k)
+            cp[P.cp_off[U] + ((size_t)mu * nU + i) * mU + e.col + k] = C[((size_t)mu * nU + i) * nK + k];
+    }
+  }
+  upload(h, h.d_cpack, cp);
+  // column tables
+  std::vector<int> lam, kap, un;
+  P.lam_off.assign(nat + 1, 0);
+  P.kap_off.assign(nat + 1, 0);
+  for (int U = 0; U < nat; ++U) {
+    P.lam_off[U] = (long long)lam.size() / 6;
+    P.kap_off[U] = (long long)kap.size() / 6;
+    for (auto &e : P.nb[U])
+      for (int k = 0; k < h.n_ao[e.K]; ++k) {
+        const int row[6] = {e.K, e.R[0], e.R[1], e.R[2], k, h.ao_off[e.K] + k};
+        lam.insert(lam.end(), row, row + 6);
+        const int krow[6] = {e.K, e.R[0], e.R[1], e.R[2], h.ao_off[e.K] + k, e.ucol + k};
+        kap.insert(kap.end(), krow, krow + 6);
+      }
+  }
+  P.lam_off[nat] = (long long)lam.size() / 6;
+  P.kap_off[nat] = (long long)kap.size() / 6;
+  for (size_t b = 0; b < P.uni.size(); ++b) {
+    const int K = std::get<0>(P.uni[b]);
+    for (int k = 0; k < h.n_ao[K]; ++k) {
+      const int row[6] = {K, std::get<1>(P.uni[b]), std::get<2>(P.uni[b]), std::get<3>(P.uni[b]), k,
+                          h.ao_off[K] + k};
+      un.insert(un.end(), row, row + 6);
+    }
+  }
+  upload(h, P.d_lam, lam);
+  upload(h, P.d_kap, kap);
+  upload(h, P.d_uni, un);
+  // workspace offsets (elements, per point and per Green's function)
+  P.bg_off.assign(nat + 1, 0);
+  P.ag_off.assign(nat + 1, 0);
+  P.n_off.assign(nat + 1, 0);
+  P.x_off.assign(nat + 1, 0);
+  P.o_off.assign(nat + 1, 0);
+  double fl = 0;
+  for (int V = 0; V < nat; ++V) {
+    const long long rowsV = (long long)h.n_aux[V] * h.n_ao[V];
+    P.bg_off[V + 1] = P.bg_off[V] + (long long)P.m_all * P.m[V];
+    P.ag_off[V + 1] = P.ag_off[V] + (long long)h.nao * P.m[V];
+    P.n_off[V + 1] = P.n_off[V] + rowsV * P.m_all;
+    P.x_off[V + 1] = P.x_off[V] + (long long)h.nao * rowsV;
+    P.o_off[V + 1] = P.o_off[V] + (long long)h.naux * h.n_ao[V] * P.m[V];
+    fl += 2.0 * 2.0 * rowsV * P.m[V] * P.m_all;    // N-step, both G
+    fl += 2.0 * 2.0 * h.nao * P.m[V] * rowsV;      // X-step, both G
+  }
+  for (int U = 0; U < nat; ++U) {
+    const double cols = (double)h.n_ao[U] * P.m[U];
+    for (int V = 0; V < nat; ++V) fl += 2.0 * h.n_aux[V] * cols * 4.0 * h.n_ao[V];   // O assembly
+    fl += 2.0 * h.n_aux[U] * cols * h.naux;                                        // final
+  }
+  P.flop_per_point = fl;
+  P.bg_sz = P.bg_off[nat];
+  P.ag_sz = P.ag_off[nat];
+  P.n_sz = P.n_off[nat];
+  P.x_sz = P.x_off[nat];
+  P.o_sz = P.o_off[nat];
+  upload(h, P.t_n_ao, h.n_ao);
+  upload(h, P.t_n_aux, h.n_aux);
+  upload(h, P.t_ao_off, h.ao_off);
+  upload(h, P.t_aux_off, h.aux_off);
+  upload(h, P.t_m, P.m);
+  upload(h, P.t_lam_off, P.lam_off);
+  upload(h, P.t_kap_off, P.kap_off);
+  upload(h, P.t_bg_off, P.bg_off);
+  upload(h, P.t_ag_off, P.ag_off);
+  upload(h, P.t_n_off, P.n_off);
+  upload(h, P.t_x_off, P.x_off);
+  upload(h, P.t_o_off, P.o_off);
+}
+
+void chi0_run(Handle &h, double *ms_gemm) {
+  Chi0Plan &P = h.plan;
+  const int nat = h.natoms, nR = h.mesh.size(), ntau = h.ntau, naux = h.naux, nao = h.nao;
+  cudaStream_t s = h.stream;
+  const size_t n2 = (size_t)nao * nao;
+  const size_t g_gstride = (size_t)ntau * nR * n2;
+  h.ensure(h.d_chi_tau, (size_t)ntau * nR * naux * naux * sizeof(double));
+  // points per batch: bounded workspace (1 GiB, at least one point)
+  const long long per_point = 2 * (P.bg_sz + P.ag_sz + P.n_sz + P.x_sz) + P.o_sz;
+  const long long total_pts = (long long)ntau * nR;
+  long long npb = std::max<long long>(1, (1LL << 27) / std::max<long long>(1, per_point));
+  npb = std::min(npb, total_pts);
+  DevBuf &ws = P.ws;
+  h.ensure(ws, (size_t)npb * per_point * sizeof(double));
+  double *Bg = (double *)ws.p;
+  double *Ag = Bg + npb * 2 * P.bg_sz;
+  double *Nw = Ag + npb * 2 * P.ag_sz;
+  double *Xw = Nw + npb * 2 * P.n_sz;
+  double *Ow = Xw + npb * 2 * P.x_sz;
+  const double *Cp = (const double *)h.d_cpack.p;
+  const double spin = 2.0;
+  // O-assembly shared memory: Lm + LX + RG
+  int maxn = 0;
+  for (int a = 0; a < nat; ++a) maxn = std::max(maxn, h.n_ao[a]);
+  const size_t osmem = (size_t)(2 * maxn * 2 * maxn + 2 * maxn * 64) * sizeof(double);
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
+  int max_chunks = 0, max_m = 0;
+  for (int a = 0; a < nat; ++a) {
+    max_chunks = std::max(max_chunks, (P.m[a] + 63) / 64);
+    max_m = std::max(max_m, P.m[a]);
+  }
+  for (long long p0 = 0; p0 < total_pts; p0 += npb) {
+    const int np = (int)std::min(npb, total_pts - p0);
+    std::vector<Point> pts(np);
+    for (int q = 0; q < np; ++q) {
+      const long long idx = p0 + q;
+      pts[q].itau = (int)(idx / nR);
+      pts[q].iR = (int)(idx % nR);
+      h.mesh.split(pts[q].iR, pts[q].R[0], pts[q].R[1], pts[q].R[2]);
+    }
+    h.ensure(P.t_pts, np * sizeof(Point));
+    LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
+    const Point *dpts = (const Point *)P.t_pts.p;
+    {
+      dim3 grid((unsigned)(((long long)P.m_all * max_m + 255) / 256), (unsigned)(np * 2 * nat));
+      k_gather_bg<<<grid, 256, 0, s>>>((const double *)h.d_g.p, g_gstride, dpts, (const int *)P.d_uni.p,
+                                       (const int *)P.d_lam.p, (const long long *)P.t_lam_off.p, (const int *)P.t_m.p,
+                                       (const long long *)P.t_bg_off.p, nat, P.m_all, nR, nao, h.mesh.n1, h.mesh.n2,
+                                       h.mesh.n3, P.bg_sz, 2 * P.bg_sz, Bg);
+      dim3 grid2((unsigned)(((long long)nao * max_m + 255) / 256), (unsigned)(np * 2 * nat));
+      k_gather_ag<<<grid2, 256, 0, s>>>((const double *)h.d_g.p, g_gstride, dpts, (const int *)P.d_lam.p,
+                                        (const long long *)P.t_lam_off.p, (const int *)P.t_m.p,
+                                        (const long long *)P.t_ag_off.p, nat, nR, nao, h.mesh.n1, h.mesh.n2,
+                                        h.mesh.n3, P.ag_sz, 2 * P.ag_sz, Ag);
+      launch_counter() += 2;
+      LR_CUDA(cudaGetLastError());
+    }
+    // N- and X-steps
+    std::vector<DGemm> b1;
+    for (int q = 0; q < np; ++q)
+      for (int g = 0; g < 2; ++g)
+        for (int V = 0; V < nat; ++V) {
+          const int rowsV = h.n_aux[V] * h.n_ao[V], mV = P.m[V];
+          DGemm dn{Cp + P.cp_off[V], Bg + (size_t)q * 2 * P.bg_sz + g * P.bg_sz + P.bg_off[V],
+                   Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V], rowsV, P.m_all, mV, mV, mV, P.m_all,
+                   1.0, 0.0};
+          b1.push_back(dn);
+          DGemm dx{Ag + (size_t)q * 2 * P.ag_sz + g * P.ag_sz + P.ag_off[V], Cp + P.cp_off[V],
+                   Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V], nao, rowsV, mV, mV, mV, rowsV, 1.0, 0.0};
+          b1.push_back(dx);
+        }
+    dgemm_batched(h, b1, s, P.gargs1);
+    // O assembly
+    OArgs oa;
+    oa.G = (const double *)h.d_g.p;
+    oa.g_gstride = g_gstride;
+    oa.nR_stride = nR;
+    oa.nao = nao;
+    oa.natoms = nat;
+    oa.naux = naux;
+    oa.n1 = h.mesh.n1;
+    oa.n2 = h.mesh.n2;
+    oa.n3 = h.mesh.n3;
+    oa.pts = dpts;
+    oa.n_ao = (const int *)P.t_n_ao.p;
+    oa.n_aux = (const int *)P.t_n_aux.p;
+    oa.ao_off = (const int *)P.t_ao_off.p;
+    oa.aux_off = (const int *)P.t_aux_off.p;
+    oa.m = (const int *)P.t_m.p;
+    oa.kap = (const int *)P.d_kap.p;
+    oa.kap_off = (const long long *)P.t_kap_off.p;
+    oa.N = Nw;
+    oa.n_off = (const long long *)P.t_n_off.p;
+    oa.n_sz_g = P.n_sz;
+    oa.n_sz_p = 2 * P.n_sz;
+    oa.m_all = P.m_all;
+    oa.X = Xw;
+    oa.x_off = (const long long *)P.t_x_off.p;
+    oa.x_sz_g = P.x_sz;
+    oa.x_sz_p = 2 * P.x_sz;
+    oa.O = Ow;
+    oa.o_off = (const long long *)P.t_o_off.p;
+    oa.o_sz_p = P.o_sz;
+    dim3 og((unsigned)max_chunks, (unsigned)(np * nat * nat));
+    k_oassemble<<<og, 256, osmem, s>>>(oa);
+    ++launch_counter();
+    LR_CUDA(cudaGetLastError());
+    // final contraction into chi0(R, tau)
+    std::vector<DGemm> b2;
+    for (int q = 0; q < np; ++q) {
+      double *chi = (double *)h.d_chi_tau.p + ((size_t)pts[q].itau * nR + pts[q].iR) * naux * naux;
+      for (int U = 0; U < nat; ++U) {
+        const int K = h.n_ao[U] * P.m[U];
+        DGemm df{Cp + P.cp_off[U], Ow + (size_t)q * P.o_sz + P.o_off[U], chi + (size_t)h.aux_off[U] * naux,
+                 h.n_aux[U], naux, K, K, K, naux, -spin, 0.0};
+        b2.push_back(df);
+      }
+    }
+    dgemm_batched(h, b2, s, P.gargs2);
+  }
+  LR_CUDA(cudaStreamSynchronize(s));
+  if (ms_gemm) *ms_gemm = 0;
+}
+
+}  // namespace librpa

@@ -1,0 +1,320 @@
+// K5 + K6: RPA correlation energy (Sec. 2):
+//
+//   E_c = (1/2 pi) sum_q w_q sum_k W_k { ln det[1 - Pi(q, i omega_k)] + Tr Pi(q, i omega_k) },  Pi = chi0 V.
+//
+// With the Cholesky factor V(q) = L L^H, det(1 - chi0 V) = det(I - L^H chi0 L) (Sylvester) and
+// A = I - L^H chi0 L is Hermitian positive definite (chi0 <= 0), so ln det A = 2 sum_i ln (L_A)_ii
+// from a Cholesky factorisation A = L_A L_A^H, and Tr Pi = Tr(L^H chi0 L).  Per q: factor V;
+// per (q, omega): W = chi0 L, A = I - L^H W (lower triangle), factor A.  The factorisations are
+// right-looking and blocked (panel width NB): the diagonal block is factored in shared memory by
+// one CTA per matrix, the panel below it by a triangular solve, and the trailing matrix is
+// updated by the batched complex GEMM; every matrix of a batch advances panel by panel in step,
+// so each launch has work from all of them.  Everything is FP64.
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace librpa {
+namespace {
+
+constexpr int NB = 64;
+
+// Factor the NB x NB diagonal block at p0 of every matrix in place (lower triangle).  One CTA per
+// matrix.  Adds 2 sum ln d_jj to lndet[b]; sets info[b] = 1 on a non-positive pivot.
+__global__ void __launch_bounds__(256) k_potrf_diag(double2 *const *mats, int n, int ld, int p0, double *lndet,
+                                                    int *info) {
+  extern __shared__ double2 a[];   // [NB][NB + 1]
+  const int b = blockIdx.x;
+  double2 *M = mats[b];
+  const int nb = min(NB, n - p0);
+  const int lda = NB + 1;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    a[i * lda + j] = j <= i ? M[(size_t)(p0 + i) * ld + p0 + j] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  __shared__ double dsh;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  double lsum = 0.0;
+  for (int j = 0; j < nb; ++j) {
+    if (threadIdx.x == 0) {
+      double d = a[j * lda + j].x;
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        d = 1.0;
+      }
+      d = sqrt(d);
+      a[j * lda + j] = make_double2(d, 0.0);
+      lsum += 2.0 * log(d);
+      dsh = d;
+    }
+    __syncthreads();
+    const double inv = 1.0 / dsh;
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) {
+      a[i * lda + j].x *= inv;
+      a[i * lda + j].y *= inv;
+    }
+    __syncthreads();
+    // trailing update of the block: a_ik -= a_ij conj(a_kj), j < k <= i
+    const int m = nb - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k > i) continue;
+      const double2 x = a[i * lda + j], y = a[k * lda + j];
+      a[i * lda + k].x -= x.x * y.x + x.y * y.y;
+      a[i * lda + k].y -= x.y * y.x - x.x * y.y;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    if (j <= i) M[(size_t)(p0 + i) * ld + p0 + j] = a[i * lda + j];
+  }
+  if (threadIdx.x == 0) {
+    lndet[b] += lsum;
+    if (bad) info[b] = 1;
+  }
+}
+
+// Panel solve: rows i >= p0 + NB, X L_pp^H = B  =>  x_j = (b_j - sum_{k<j} x_k conj(L_jk)) / L_jj.
+// One CTA per (matrix, 64-row chunk); one thread per row.
+__global__ void __launch_bounds__(64) k_trsm_panel(double2 *const *mats, int n, int ld, int p0) {
+  extern __shared__ double2 tsm[];
+  double2(*L)[NB + 1] = reinterpret_cast<double2(*)[NB + 1]>(tsm);
+  double2(*X)[NB + 1] = reinterpret_cast<double2(*)[NB + 1]>(tsm + NB * (NB + 1));
+  const int b = blockIdx.y;
+  double2 *M = mats[b];
+  const int nb = min(NB, n - p0);
+  const int r0 = p0 + nb + blockIdx.x * 64;
+  if (r0 >= n) return;
+  for (int e = threadIdx.x; e < nb * nb; e += 64) {
+    const int i = e / nb, j = e % nb;
+    L[i][j] = M[(size_t)(p0 + i) * ld + p0 + j];
+  }
+  const int rows = min(64, n - r0);
+  for (int e = threadIdx.x; e < rows * nb; e += 64) {
+    const int i = e / nb, j = e % nb;
+    X[i][j] = M[(size_t)(r0 + i) * ld + p0 + j];
+  }
+  __syncthreads();
+  const int i = threadIdx.x;
+  if (i < rows) {
+    for (int j = 0; j < nb; ++j) {
+      double2 s = X[i][j];
+      for (int k = 0; k < j; ++k) {
+        const double2 x = X[i][k], l = L[j][k];
+        // s -= x * conj(l)
+        s.x -= x.x * l.x + x.y * l.y;
+        s.y -= x.y * l.x - x.x * l.y;
+      }
+      const double inv = 1.0 / L[j][j].x;
+      X[i][j] = make_double2(s.x * inv, s.y * inv);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * nb; e += 64) {
+    const int r = e / nb, j = e % nb;
+    M[(size_t)(r0 + r) * ld + p0 + j] = X[r][j];
+  }
+}
+
+// Zero the strict upper triangle (so a Cholesky factor can be used as a triangular operand).
+__global__ void k_zero_upper(double2 *const *mats, int n, int ld) {
+  double2 *M = mats[blockIdx.y];
+  const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (size_t)n * n) return;
+  const int i = (int)(x / n), j = (int)(x % n);
+  if (j > i) M[(size_t)i * ld + j] = make_double2(0.0, 0.0);
+}
+
+// A = -L^H chi0 L on entry (lower triangle).  trace[b] = Re Tr(L^H chi0 L) = -sum Re A_ii;
+// then A_ii += 1 (A = I - L^H chi0 L).  One CTA per matrix.
+__global__ void k_diag_shift(double2 *const *mats, int n, int ld, double *trace) {
+  double2 *M = mats[blockIdx.x];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double2 *p = M + (size_t)i * ld + i;
+    s -= p->x;
+    p->x += 1.0;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) trace[blockIdx.x] = red[0];
+}
+
+// K6: E_c, per-q and per-omega parts from the per-(q, omega) ln det and trace.
+__global__ void k_energy(const double *lndet, const double *trace, const double *w_omega, int nq, int nw,
+                         double *out /* [1 + nq + nw] */) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double pref = 1.0 / (2.0 * M_PI * nq);
+  double tot = 0.0;
+  for (int k = 0; k < nw; ++k) out[1 + nq + k] = 0.0;
+  for (int q = 0; q < nq; ++q) {
+    double sq = 0.0;
+    for (int k = 0; k < nw; ++k) {
+      const double f = pref * w_omega[k] * (lndet[q * nw + k] + trace[q * nw + k]);
+      sq += f;
+      out[1 + nq + k] += f;
+    }
+    out[1 + q] = sq;
+    tot += sq;
+  }
+  out[0] = tot;
+}
+
+// Blocked Cholesky of a batch of n x n matrices (lower triangle, in place), all in step.
+void potrf_batched(Handle &h, double2 *const *d_mats, const std::vector<double2 *> &mats, int n, int ld,
+                   double *lndet, int *info) {
+  cudaStream_t s = h.stream;
+  const int B = (int)mats.size();
+  const size_t smem = (size_t)NB * (NB + 1) * sizeof(double2);
+  LR_CUDA(cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LR_CUDA(cudaFuncSetAttribute(k_trsm_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smem)));
+  for (int p0 = 0; p0 < n; p0 += NB) {
+    k_potrf_diag<<<B, 256, smem, s>>>(d_mats, n, ld, p0, lndet, info);
+    ++launch_counter();
+    const int nb = std::min(NB, n - p0), rest = n - p0 - nb;
+    if (rest <= 0) break;
+    dim3 g((unsigned)((rest + 63) / 64), (unsigned)B);
+    k_trsm_panel<<<g, 64, 2 * smem, s>>>(d_mats, n, ld, p0);
+    ++launch_counter();
+    std::vector<ZGemm> batch;
+    for (int b = 0; b < B; ++b) {
+      ZGemm z{};
+      double2 *M = mats[b];
+      z.A = M + (size_t)(p0 + nb) * ld + p0;
+      z.B = z.A;
+      z.C = M + (size_t)(p0 + nb) * ld + p0 + nb;
+      z.M = rest;
+      z.N = rest;
+      z.K = nb;
+      z.lda = ld;
+      z.ldb = ld;
+      z.ldc = ld;
+      z.alpha = make_double2(-1.0, 0.0);
+      z.beta = make_double2(1.0, 0.0);
+      batch.push_back(z);
+    }
+    ZGemmFlags f;
+    f.transB = true;
+    f.conjB = true;
+    f.lower_only = true;
+    // algorithmic work: the lower triangle (with diagonal) of a rest x rest update of rank nb
+    zgemm_batched(batch, f, s, h, 1, 8.0 * B * (0.5 * rest * (rest + 1.0)) * nb);
+  }
+  LR_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
+  const int n = h.naux, nq = h.mesh.size(), nw = h.ntau;
+  const size_t n2 = (size_t)n * n;
+  cudaStream_t s = h.stream;
+  // workspace: L[nq], W[nw], A[nw] (complex n x n), pointer tables, lndet/trace/info, output
+  const size_t mat = n2 * sizeof(double2);
+  const size_t o_L = 0, o_W = o_L + nq * mat, o_A = o_W + nw * mat, o_ptr = o_A + nw * mat;
+  const size_t n_ptr = (size_t)nq + nw + 8;
+  const size_t o_ld = o_ptr + ((n_ptr * 8 + 255) / 256) * 256;
+  const size_t o_tr = o_ld + ((size_t)nq * nw * 8 + 8 * 1024 + 255) / 256 * 256;
+  const size_t o_inf = o_tr + ((size_t)nq * nw * 8 + 255) / 256 * 256;
+  const size_t o_out = o_inf + ((size_t)(nq + nq * nw) * 4 + 255) / 256 * 256;
+  const size_t o_wo = o_out + ((size_t)(1 + nq + nw) * 8 + 255) / 256 * 256;
+  const size_t total = o_wo + (size_t)nw * 8 + 256;
+  h.ensure(h.work, total);
+  char *w = (char *)h.work.p;
+  double2 *Lq = (double2 *)(w + o_L), *Wm = (double2 *)(w + o_W), *Am = (double2 *)(w + o_A);
+  double2 **ptrs = (double2 **)(w + o_ptr);
+  double *lndet = (double *)(w + o_ld), *trace = (double *)(w + o_tr), *out = (double *)(w + o_out);
+  double *wo = (double *)(w + o_wo);
+  int *info = (int *)(w + o_inf);
+  double *lndet_v = lndet + (size_t)nq * nw;   // scratch for the V(q) factorisations
+  LR_CUDA(cudaMemsetAsync(lndet, 0, ((size_t)nq * nw + nq) * 8, s));
+  LR_CUDA(cudaMemsetAsync(info, 0, (size_t)(nq + nq * nw) * 4, s));
+  LR_CUDA(cudaMemcpyAsync(wo, h.w_omega.data(), (size_t)nw * 8, cudaMemcpyHostToDevice, s));
+  // Cholesky of every V(q)
+  LR_CUDA(cudaMemcpyAsync(Lq, h.d_vq.p, nq * mat, cudaMemcpyDeviceToDevice, s));
+  std::vector<double2 *> lp(nq);
+  for (int q = 0; q < nq; ++q) lp[q] = Lq + q * n2;
+  LR_CUDA(cudaMemcpyAsync(ptrs, lp.data(), nq * 8, cudaMemcpyHostToDevice, s));
+  potrf_batched(h, ptrs, lp, n, n, lndet_v, info);
+  {
+    dim3 g((unsigned)((n2 + 255) / 256), (unsigned)nq);
+    k_zero_upper<<<g, 256, 0, s>>>(ptrs, n, n);
+    ++launch_counter();
+  }
+  const double2 *chi = (const double2 *)h.d_chi_qw.p;
+  double2 **aptr = ptrs + nq;
+  std::vector<double2 *> ap(nw);
+  for (int k = 0; k < nw; ++k) ap[k] = Am + k * n2;
+  LR_CUDA(cudaMemcpyAsync(aptr, ap.data(), nw * 8, cudaMemcpyHostToDevice, s));
+  for (int q = 0; q < nq; ++q) {
+    // W = chi0(q, omega) L_q  (L lower triangular: k >= j)
+    std::vector<ZGemm> b1, b2;
+    for (int k = 0; k < nw; ++k) {
+      ZGemm z{};
+      z.A = chi + ((size_t)q * nw + k) * n2;
+      z.B = Lq + q * n2;
+      z.C = Wm + k * n2;
+      z.M = z.N = z.K = n;
+      z.lda = z.ldb = z.ldc = n;
+      z.alpha = make_double2(1.0, 0.0);
+      z.beta = make_double2(0.0, 0.0);
+      b1.push_back(z);
+      ZGemm y{};
+      y.A = Lq + q * n2;     // op(A) = L^H: stored [K][M], conjugated
+      y.B = Wm + k * n2;
+      y.C = Am + k * n2;
+      y.M = y.N = y.K = n;
+      y.lda = y.ldb = y.ldc = n;
+      y.alpha = make_double2(-1.0, 0.0);
+      y.beta = make_double2(0.0, 0.0);
+      b2.push_back(y);
+    }
+    // algorithmic work (8 flops per complex MAC): W = chi0 L with L lower triangular,
+    // sum_j (n - j) = n (n + 1) / 2 MACs per row; A = -L^H W on the lower triangle,
+    // sum_{i >= j} (n - i) MACs per matrix
+    const double dn = n;
+    ZGemmFlags f1;
+    f1.kfrom = 2;
+    zgemm_batched(b1, f1, s, h, 1, 8.0 * nw * dn * (dn * (dn + 1) / 2));
+    ZGemmFlags f2;
+    f2.transA = true;
+    f2.conjA = true;
+    f2.kfrom = 1;
+    f2.lower_only = true;
+    zgemm_batched(b2, f2, s, h, 1, 8.0 * nw * (dn * (dn + 1) * (dn + 2) / 6));
+    k_diag_shift<<<nw, 256, 0, s>>>(aptr, n, n, trace + (size_t)q * nw);
+    ++launch_counter();
+    potrf_batched(h, aptr, ap, n, n, lndet + (size_t)q * nw, info + nq + (size_t)q * nw);
+  }
+  k_energy<<<1, 1, 0, s>>>(lndet, trace, wo, nq, nw, out);
+  ++launch_counter();
+  LR_CUDA(cudaGetLastError());
+  std::vector<double> res(1 + nq + nw);
+  std::vector<int> inf(nq + (size_t)nq * nw);
+  LR_CUDA(cudaMemcpyAsync(res.data(), out, res.size() * 8, cudaMemcpyDeviceToHost, s));
+  LR_CUDA(cudaMemcpyAsync(inf.data(), info, inf.size() * 4, cudaMemcpyDeviceToHost, s));
+  LR_CUDA(cudaStreamSynchronize(s));
+  for (int v : inf)
+    if (v) return LIBRPA_E_NOT_PD;
+  *ec = res[0];
+  if (ec_q)
+    for (int q = 0; q < nq; ++q) ec_q[q] = res[1 + q];
+  if (ec_w)
+    for (int k = 0; k < nw; ++k) ec_w[k] = res[1 + nq + k];
+  // flop count of this stage (complex MAC = 8 real flops): per q (4/3 n^3 real for the Cholesky of
+  // V), per (q, omega): W = chi0 L (n^3/2 MAC), L^H W lower (n^3/6 MAC), Cholesky (n^3/6 MAC)
+  const double n3 = (double)n * n * n;
+  h.stats.flop_ec = nq * (8.0 * n3 / 6.0) + (double)nq * nw * 8.0 * (n3 / 2 + n3 / 6 + n3 / 6);
+  return LIBRPA_OK;
+}
+
+}  // namespace librpa

@@ -1,0 +1,127 @@
+// K3 + K4: chi0(R, tau) -> chi0(R, i omega) -> chi0(q, i omega) (Sec. 2):
+//
+//   chi0(R, i omega_k) = sum_j Gamma_kj chi0(R, tau_j)        (cosine transform; Gamma real)
+//   chi0(q, i omega)   = sum_{R in BvK} e^{+i q.R} chi0(R, i omega)
+//
+// Both are per-element linear maps over whole N_aux^2 matrices: one thread per matrix element
+// keeps its tau (or R) vector in registers, the small transform matrices sit in shared memory,
+// and consecutive threads touch consecutive elements, so every load and store is coalesced.
+#include <vector>
+
+#include "internal.h"
+
+namespace librpa {
+namespace {
+
+template <int NT>
+__global__ void __launch_bounds__(256) k_tau_to_omega(const double *__restrict__ in, double *__restrict__ out,
+                                                      const double *__restrict__ gamma, int ntau, int nR,
+                                                      size_t n2) {
+  __shared__ double gs[NT * NT];
+  for (int e = threadIdx.x; e < ntau * ntau; e += blockDim.x) gs[e] = gamma[e];
+  __syncthreads();
+  const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int R = blockIdx.y;
+  if (x >= n2) return;
+  double v[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) v[j] = j < ntau ? in[((size_t)j * nR + R) * n2 + x] : 0.0;
+#pragma unroll 1
+  for (int k = 0; k < ntau; ++k) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+      if (j < ntau) acc = fma(gs[k * ntau + j], v[j], acc);
+    out[((size_t)k * nR + R) * n2 + x] = acc;
+  }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) k_r_to_q(const double *__restrict__ in, double2 *__restrict__ out,
+                                                const double2 *__restrict__ ph, int nR, int nq, int nw,
+                                                size_t n2) {
+  __shared__ double2 ps[NR * NR];
+  for (int e = threadIdx.x; e < nq * nR; e += blockDim.x) ps[e] = ph[e];
+  __syncthreads();
+  const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (x >= n2) return;
+  double y[NR];
+#pragma unroll
+  for (int R = 0; R < NR; ++R) y[R] = R < nR ? in[((size_t)k * nR + R) * n2 + x] : 0.0;
+#pragma unroll 1
+  for (int q = 0; q < nq; ++q) {
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int R = 0; R < NR; ++R)
+      if (R < nR) {
+        const double2 p = ps[q * nR + R];
+        re = fma(p.x, y[R], re);
+        im = fma(p.y, y[R], im);
+      }
+    out[((size_t)q * nw + k) * n2 + x] = make_double2(re, im);
+  }
+}
+
+template <int NT>
+void launch_tw(const double *in, double *out, const double *gamma, int ntau, int nR, size_t n2, cudaStream_t s) {
+  dim3 g((unsigned)((n2 + 255) / 256), (unsigned)nR);
+  k_tau_to_omega<NT><<<g, 256, 0, s>>>(in, out, gamma, ntau, nR, n2);
+}
+
+template <int NR>
+void launch_rq(const double *in, double2 *out, const double2 *ph, int nR, int nq, int nw, size_t n2,
+               cudaStream_t s) {
+  dim3 g((unsigned)((n2 + 255) / 256), (unsigned)nw);
+  k_r_to_q<NR><<<g, 256, 0, s>>>(in, out, ph, nR, nq, nw, n2);
+}
+
+}  // namespace
+
+void freq_transform(Handle &h) {
+  const int ntau = h.ntau, nR = h.mesh.size(), nq = nR;
+  const size_t n2 = (size_t)h.naux * h.naux;
+  cudaStream_t s = h.stream;
+  if (nR > 64) throw Error{LIBRPA_E_ARG, "k-mesh with more than 64 points is not supported"};
+  h.ensure(h.d_chi_qw, (size_t)nq * ntau * n2 * 16);
+  // workspace: chi0(R, i omega) plus the two small matrices
+  const size_t b_rw = (size_t)ntau * nR * n2 * 8, b_g = (size_t)ntau * ntau * 8, b_p = (size_t)nq * nR * 16;
+  h.ensure(h.work, b_rw + 256 + b_g + 256 + b_p);
+  char *w = (char *)h.work.p;
+  double *rw = (double *)w;
+  double *dg = (double *)(w + (b_rw + 255) / 256 * 256);
+  double2 *dp = (double2 *)((char *)dg + (b_g + 255) / 256 * 256);
+  std::vector<double2> ph((size_t)nq * nR);
+  for (int q = 0; q < nq; ++q) {
+    int a, b, c;
+    h.mesh.split(q, a, b, c);
+    for (int R = 0; R < nR; ++R) {
+      int x, y, z;
+      h.mesh.split(R, x, y, z);
+      const long long den = (long long)h.mesh.n1 * h.mesh.n2 * h.mesh.n3;
+      const long long num = (long long)a * x * h.mesh.n2 * h.mesh.n3 + (long long)b * y * h.mesh.n1 * h.mesh.n3 +
+                            (long long)c * z * h.mesh.n1 * h.mesh.n2;
+      const double th = 2.0 * M_PI * (double)(num % den) / (double)den;
+      ph[(size_t)q * nR + R] = make_double2(std::cos(th), std::sin(th));
+    }
+  }
+  LR_CUDA(cudaMemcpyAsync(dg, h.gamma.data(), b_g, cudaMemcpyHostToDevice, s));
+  LR_CUDA(cudaMemcpyAsync(dp, ph.data(), b_p, cudaMemcpyHostToDevice, s));
+  const double *in = (const double *)h.d_chi_tau.p;
+  if (ntau <= 16)
+    launch_tw<16>(in, rw, dg, ntau, nR, n2, s);
+  else if (ntau <= 32)
+    launch_tw<32>(in, rw, dg, ntau, nR, n2, s);
+  else
+    launch_tw<64>(in, rw, dg, ntau, nR, n2, s);
+  if (nR <= 16)
+    launch_rq<16>(rw, (double2 *)h.d_chi_qw.p, dp, nR, nq, ntau, n2, s);
+  else if (nR <= 32)
+    launch_rq<32>(rw, (double2 *)h.d_chi_qw.p, dp, nR, nq, ntau, n2, s);
+  else
+    launch_rq<64>(rw, (double2 *)h.d_chi_qw.p, dp, nR, nq, ntau, n2, s);
+  launch_counter() += 2;
+  LR_CUDA(cudaGetLastError());
+}
+
+}  // namespace librpa

@@ -1,0 +1,158 @@
+// K1: real-space imaginary-time Green's functions (Sec. 2, Eq. green_mat):
+//
+//   G^occ_ij(R, tau) = (1/N_k) sum_{k,n} f_nk       c_in(k) c*_jn(k) e^{-ik.R} e^{-(mu - e_nk) tau}
+//   G^vir_ij(R, tau) = (1/N_k) sum_{k,n} (1 - f_nk) c_in(k) c*_jn(k) e^{-ik.R} e^{-(e_nk - mu) tau}
+//
+// (the paper's two branches with the factors -i, +i taken out; tau >= 0 in both).  For each
+// tau: P^g_k = C_k diag(w^g(tau)) C_k^H as one batched complex GEMM over (g, k) restricted to
+// the bands with non-zero weight, then G^g(R) = (1/N_k) Re sum_k e^{-ik.R} P^g_k.  The
+// exponentials are evaluated in FP64 on the device.  For time-reversal-symmetric input
+// G is real; the largest |Im| relative to the largest |Re| is returned as a check.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace librpa {
+namespace {
+
+// w[g][k][n] for one tau: g = 0 occupied weight f e^{-(mu - e) tau}, g = 1 virtual weight
+// (1 - f) e^{-(e - mu) tau}
+__global__ void k_weights(const double *eig, const double *occ, double mu, double tau, int nkb, double *w) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nkb) return;
+  const double e = eig[x], f = occ[x];
+  w[x] = f > 0.0 ? f * exp(-(mu - e) * tau) : 0.0;
+  w[nkb + x] = f < 1.0 ? (1.0 - f) * exp(-(e - mu) * tau) : 0.0;
+}
+
+// G[g][R][i][j] (slab of one tau) from the lower triangles of P[g][k] (Hermitian).
+// One thread per (g, i, j); twiddle[k][R] = e^{-i 2 pi k.R}.
+__global__ void k_phase_sum(const double2 *P, const double2 *twiddle, int nk, int nR, int nao,
+                            double inv_nk, double *G, size_t g_stride, unsigned long long *maxabs) {
+  const size_t n2 = (size_t)nao * nao;
+  const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= 2 * n2) return;
+  const int g = (int)(x / n2);
+  const size_t ij = x % n2;
+  const int i = (int)(ij / nao), j = (int)(ij % nao);
+  const bool lower = i >= j;
+  const size_t src = lower ? ij : (size_t)j * nao + i;
+  double mre = 0.0, mim = 0.0;
+  for (int R = 0; R < nR; ++R) {
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < nk; ++k) {
+      double2 p = P[((size_t)g * nk + k) * n2 + src];
+      if (!lower) p.y = -p.y;
+      const double2 t = twiddle[(size_t)k * nR + R];
+      re = fma(p.x, t.x, re);
+      re = fma(-p.y, t.y, re);
+      im = fma(p.x, t.y, im);
+      im = fma(p.y, t.x, im);
+    }
+    re *= inv_nk;
+    im *= inv_nk;
+    G[(size_t)g * g_stride + (size_t)R * n2 + ij] = re;
+    mre = fmax(mre, fabs(re));
+    mim = fmax(mim, fabs(im));
+  }
+  // non-negative doubles order like their bit patterns
+  atomicMax(&maxabs[0], __double_as_longlong(mre));
+  atomicMax(&maxabs[1], __double_as_longlong(mim));
+}
+
+}  // namespace
+
+double green_build(Handle &h) {
+  const int nk = h.mesh.size(), nR = nk, nao = h.nao, nb = h.nao, ntau = h.ntau;
+  const size_t n2 = (size_t)nao * nao;
+  const double mu = h.efermi_k[0];
+  cudaStream_t s = h.stream;
+  h.ensure(h.d_g, 2 * (size_t)ntau * nR * n2 * sizeof(double));
+  // workspace: weights, P, twiddles, max; the KS data is already on the device
+  const size_t b_e = (size_t)nk * nb * 8, b_w = 2 * b_e, b_p = 2 * (size_t)nk * n2 * 16,
+               b_t = (size_t)nk * nR * 16;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t o_w = 0, o_p = o_w + al(b_w), o_t = o_p + al(b_p), o_m = o_t + al(b_t), total = o_m + 256;
+  h.ensure(h.work, total);
+  char *wk = (char *)h.work.p;
+  const double2 *d_wfc = (const double2 *)h.d_wfc.p;
+  const double *d_eig = (const double *)h.d_eig.p, *d_occ = (const double *)h.d_occ.p;
+  double *d_w = (double *)(wk + o_w);
+  double2 *d_P = (double2 *)(wk + o_p), *d_tw = (double2 *)(wk + o_t);
+  unsigned long long *d_max = (unsigned long long *)(wk + o_m);
+  std::vector<double2> tw((size_t)nk * nR);
+  for (int k = 0; k < nk; ++k) {
+    int a, b, c;
+    h.mesh.split(k, a, b, c);
+    for (int R = 0; R < nR; ++R) {
+      int x, y, z;
+      h.mesh.split(R, x, y, z);
+      // k.R in units of 2 pi with exact rational reduction
+      const long long num = (long long)a * x * h.mesh.n2 * h.mesh.n3 + (long long)b * y * h.mesh.n1 * h.mesh.n3 +
+                            (long long)c * z * h.mesh.n1 * h.mesh.n2;
+      const long long den = (long long)h.mesh.n1 * h.mesh.n2 * h.mesh.n3;
+      const double th = 2.0 * M_PI * (double)(num % den) / (double)den;
+      tw[(size_t)k * nR + R] = make_double2(std::cos(th), -std::sin(th));
+    }
+  }
+  LR_CUDA(cudaMemcpyAsync(d_tw, tw.data(), b_t, cudaMemcpyHostToDevice, s));
+  LR_CUDA(cudaStreamSynchronize(s));   // tw is a host temporary
+  LR_CUDA(cudaMemsetAsync(d_max, 0, 16, s));
+  // band ranges with non-zero occupied / virtual weight per k
+  std::vector<int> olo(nk, nb), ohi(nk, 0), vlo(nk, nb), vhi(nk, 0);
+  for (int k = 0; k < nk; ++k)
+    for (int n = 0; n < nb; ++n) {
+      const double f = h.occ[(size_t)k * nb + n];
+      if (f > 0) { olo[k] = std::min(olo[k], n); ohi[k] = n + 1; }
+      if (f < 1) { vlo[k] = std::min(vlo[k], n); vhi[k] = n + 1; }
+    }
+  const size_t g_stride = (size_t)ntau * nR * n2;
+  for (int it = 0; it < ntau; ++it) {
+    k_weights<<<(nk * nb + 255) / 256, 256, 0, s>>>(d_eig, d_occ, mu, h.tau[it], nk * nb, d_w);
+    ++launch_counter();
+    std::vector<ZGemm> batch;
+    for (int g = 0; g < 2; ++g)
+      for (int k = 0; k < nk; ++k) {
+        const int lo = g == 0 ? olo[k] : vlo[k], hi = g == 0 ? ohi[k] : vhi[k];
+        ZGemm z{};
+        z.A = d_wfc + ((size_t)k * nb + lo) * nao;
+        z.B = z.A;
+        z.C = d_P + ((size_t)g * nk + k) * n2;
+        z.kscale = d_w + (size_t)g * nk * nb + (size_t)k * nb + lo;
+        z.M = nao;
+        z.N = nao;
+        z.K = hi > lo ? hi - lo : 0;
+        z.lda = z.ldb = nao;
+        z.ldc = nao;
+        z.alpha = make_double2(1.0, 0.0);
+        z.beta = make_double2(0.0, 0.0);
+        if (z.K == 0) {
+          LR_CUDA(cudaMemsetAsync(z.C, 0, n2 * 16, s));
+          continue;
+        }
+        batch.push_back(z);
+      }
+    ZGemmFlags f;
+    f.transA = true;   // A stored [band][i]
+    f.conjB = true;    // B = conj(wfc) stored [band][j]
+    f.lower_only = true;
+    zgemm_batched(batch, f, s, h);
+    const size_t nthr = 2 * n2;
+    k_phase_sum<<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(d_P, d_tw, nk, nR, nao, 1.0 / nk,
+                                                              (double *)h.d_g.p + (size_t)it * nR * n2, g_stride,
+                                                              d_max);
+    ++launch_counter();
+    LR_CUDA(cudaGetLastError());
+  }
+  unsigned long long mx[2];
+  LR_CUDA(cudaMemcpyAsync(mx, d_max, 16, cudaMemcpyDeviceToHost, s));
+  LR_CUDA(cudaStreamSynchronize(s));
+  double mre, mim;
+  std::memcpy(&mre, &mx[0], 8);
+  std::memcpy(&mim, &mx[1], 8);
+  return mre > 0 ? mim / mre : mim;
+}
+
+}  // namespace librpa

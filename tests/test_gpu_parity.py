@@ -1,0 +1,252 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Every step of the path has its own check: G (Eq. green_mat), chi0(R, tau)
+(Algorithm 1), chi0(q, i omega) (cosine + Fourier transforms) and E_c (ln det
+and quadrature).  Tolerances: G to 1e-12 and chi0 to 1e-10 relative to the
+largest element, E_c to 1e-8 Ha absolute.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2407_19930_gb300 import librpa_gpu as L
+from paper_2407_19930_gb300 import synthetic as syn
+from oracle import grid as ogrid, pipeline
+from oracle import green as ogreen
+from oracle.chi0_alg1 import chi0_alg1
+
+pytestmark = pytest.mark.gpu
+
+TOL_G = 1e-12
+TOL_CHI = 1e-10
+TOL_EC = 1e-8
+
+
+def _run(inp, grid, **kw):
+    h = L.librpa_gpu_create(**kw)
+    try:
+        L.set_inputs(h, inp, grid)
+        st = inp.st
+        chi = L.librpa_gpu_chi0(h, out=(st.nk, len(grid["omega"]), st.naux))
+        ec, ecq, ecw = L.librpa_gpu_ec(h, st.nk, len(grid["omega"]))
+        gos, gvs, cts = [], [], []
+        for it in range(len(grid["tau"])):
+            gos.append([]), gvs.append([]), cts.append([])
+            for iR in range(st.nk):
+                go, gv = L.librpa_gpu_get_green(h, it, iR, st.nao)
+                gos[-1].append(go), gvs[-1].append(gv)
+                cts[-1].append(L.librpa_gpu_get_chi0_tau(h, it, iR, st.naux))
+        stats = L.librpa_gpu_get_stats(h)
+        return dict(chi_qw=chi, ec=ec, ec_q=ecq, ec_w=ecw, go=np.array(gos), gv=np.array(gvs),
+                    chi_tau=np.array(cts), stats=stats)
+    finally:
+        L.librpa_gpu_destroy(h)
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+CONFIGS = {
+    "tiny": lambda: syn.config_tiny(),
+    "cubic": lambda: syn.config_cubic(),
+    "mixed": lambda: syn.config_mixed(),
+    "one_atom_gamma": lambda: syn.make_inputs(
+        syn.Structure(lat=np.eye(3) * 7.0, pos=np.zeros((1, 3)), n_ao=np.array([6]), n_aux=np.array([17]),
+                      n_low=np.array([2]), kmesh=(1, 1, 1)), 5, vscale=1e-2),
+    "cubic_3x1x2": lambda: syn.make_inputs(
+        syn.cubic_two_atom(nao=5, naux=33, nlow=2, kmesh=(3, 1, 2)), 31, vscale=2e-3),
+}
+
+
+@pytest.fixture(scope="module", params=list(CONFIGS))
+def case(request):
+    inp = CONFIGS[request.param]()
+    ntau = 8 if request.param != "mixed" else 10
+    grid = ogrid.make_grid(ntau, *inp.delta_range)
+    ref = pipeline.rpa_energy(inp, grid)
+    gpu = _run(inp, grid)
+    return request.param, inp, grid, ref, gpu
+
+
+def test_green(case):
+    name, inp, grid, ref, gpu = case
+    assert _rel(gpu["go"], ref["go"]) < TOL_G
+    assert _rel(gpu["gv"], ref["gv"]) < TOL_G
+
+
+def test_chi0_tau(case):
+    name, inp, grid, ref, gpu = case
+    assert _rel(gpu["chi_tau"], ref["chi_tau"]) < TOL_CHI
+
+
+def test_chi0_q_omega(case):
+    name, inp, grid, ref, gpu = case
+    st = inp.st
+    for iq in range(st.nk):
+        for k in range(len(grid["omega"])):
+            assert _rel(gpu["chi_qw"][iq, k], ref["chi_qw"][iq, k]) < TOL_CHI
+
+
+def test_correlation_energy(case):
+    name, inp, grid, ref, gpu = case
+    assert gpu["ec"] < 0
+    assert abs(gpu["ec"] - ref["ec"]) < TOL_EC
+    assert np.abs(gpu["ec_q"] - ref["ec_q"]).max() < TOL_EC
+    assert np.abs(gpu["ec_w"] - ref["ec_w"]).max() < TOL_EC
+    assert abs(gpu["ec_q"].sum() - gpu["ec"]) < 1e-12 * abs(gpu["ec"])
+
+
+def test_stats_are_reported(case):
+    name, inp, grid, ref, gpu = case
+    s = gpu["stats"]
+    assert s["flop_chi0"] > 0 and s["ms_chi0"] > 0 and s["launches"] > 0 and s["bytes_device"] > 0
+
+
+def test_library_grid_path():
+    """Without set_grid the library builds the grid from the KS spectrum (row a0);
+    it must equal the oracle's grid on the same transition range."""
+    inp = syn.config_cubic()
+    h = L.librpa_gpu_create()
+    try:
+        L.set_inputs(h, inp)
+        L.librpa_gpu_chi0(h)
+        g = L.librpa_gpu_get_grid(h)
+        ec, _, _ = L.librpa_gpu_ec(h)
+    finally:
+        L.librpa_gpu_destroy(h)
+    ref = ogrid.make_grid(16, *inp.delta_range)
+    for key in ("tau", "omega", "w_omega"):
+        assert _rel(g[key], ref[key]) < 1e-13
+    out = pipeline.rpa_energy(inp, g)
+    assert abs(ec - out["ec"]) < TOL_EC
+
+
+def test_torch_memory_and_stream():
+    """Device memory from torch's caching allocator and a torch stream give the same result."""
+    torch = pytest.importorskip("torch")
+    inp = syn.config_tiny()
+    grid = ogrid.make_grid(6, *inp.delta_range)
+    a = _run(inp, grid)
+    s = torch.cuda.Stream()
+    b = _run(inp, grid, torch_stream=s, torch_alloc=True)
+    assert abs(a["ec"] - b["ec"]) < 1e-14 * abs(a["ec"])
+    assert np.array_equal(a["chi_tau"], b["chi_tau"])
+
+
+# ------------------------------------------------------------------ error paths
+
+
+def test_call_order_and_arguments():
+    inp = syn.config_tiny()
+    h = L.librpa_gpu_create()
+    try:
+        with pytest.raises(L.LibrpaError) as e:
+            L.librpa_gpu_chi0(h)
+        assert e.value.code == L.LIBRPA_E_STATE
+        st = inp.st
+        L.librpa_gpu_set_structure(h, st.lat, st.pos, st.n_ao, st.n_aux, st.kmesh)
+        with pytest.raises(L.LibrpaError) as e:
+            L.librpa_gpu_set_lri_coeffs(h, 0, 5, (0, 0, 0), inp.lri[0][3])
+        assert e.value.code == L.LIBRPA_E_ARG
+        with pytest.raises(L.LibrpaError) as e:   # beyond r_cut
+            L.librpa_gpu_set_lri_coeffs(h, 0, 0, (9, 0, 0), np.zeros((4, 3, 3)))
+        assert e.value.code == L.LIBRPA_E_ARG
+        for I, K, R, C in inp.lri:
+            L.librpa_gpu_set_lri_coeffs(h, I, K, R, C)
+        with pytest.raises(L.LibrpaError) as e:   # set_green missing
+            L.librpa_gpu_chi0(h)
+        assert e.value.code == L.LIBRPA_E_STATE
+        for ik in range(st.nk):
+            L.librpa_gpu_set_green(h, 0, ik, inp.eig[ik], inp.occ[ik], inp.wfc[ik], inp.efermi)
+        L.librpa_gpu_chi0(h)
+        with pytest.raises(L.LibrpaError) as e:   # set_coulomb missing
+            L.librpa_gpu_ec(h)
+        assert e.value.code == L.LIBRPA_E_STATE
+        assert "set_coulomb" in L.librpa_gpu_last_error(h)
+    finally:
+        L.librpa_gpu_destroy(h)
+
+
+def test_not_positive_definite_coulomb():
+    """An indefinite V(q) is reported as E_NOT_PD, and the handle stays usable."""
+    inp = syn.config_tiny()
+    grid = ogrid.make_grid(6, *inp.delta_range)
+    h = L.librpa_gpu_create()
+    try:
+        L.set_inputs(h, inp, grid)
+        L.librpa_gpu_chi0(h)
+        L.librpa_gpu_set_coulomb(h, 1, -inp.vq[1])
+        with pytest.raises(L.LibrpaError) as e:
+            L.librpa_gpu_ec(h)
+        assert e.value.code == L.LIBRPA_E_NOT_PD
+        L.librpa_gpu_set_coulomb(h, 1, inp.vq[1])
+        ec, _, _ = L.librpa_gpu_ec(h)
+        assert ec < 0
+    finally:
+        L.librpa_gpu_destroy(h)
+
+
+def test_hbm_budget():
+    inp = syn.config_tiny()
+    o = L.librpa_gpu_default_opts()
+    o.hbm_budget = 4096
+    h = L.librpa_gpu_create(o)
+    try:
+        st = inp.st
+        L.librpa_gpu_set_structure(h, st.lat, st.pos, st.n_ao, st.n_aux, st.kmesh)
+        with pytest.raises(L.LibrpaError) as e:
+            big = np.eye(st.naux)
+            for iq in range(st.nk):
+                L.librpa_gpu_set_coulomb(h, iq, big)
+            for I, K, R, C in inp.lri:
+                L.librpa_gpu_set_lri_coeffs(h, I, K, R, C)
+            for ik in range(st.nk):
+                L.librpa_gpu_set_green(h, 0, ik, inp.eig[ik], inp.occ[ik], inp.wfc[ik], inp.efermi)
+            L.librpa_gpu_chi0(h)
+        assert e.value.code == L.LIBRPA_E_NOMEM
+    finally:
+        L.librpa_gpu_destroy(h)
+
+
+# ------------------------------------------------------------------ full size (graphene slab)
+
+
+@pytest.mark.slow
+def test_graphene_full_size_sampled():
+    """The 35-atom graphene + water slab (N_aux = 2010, 4x4x1 k, 16 tau points) in the
+    configuration the benchmark times: sampled chi0(R, tau) blocks against the oracle's
+    Algorithm 1, and properties that hold at any size for the rest."""
+    inp = syn.config_graphene()
+    st = inp.st
+    grid = ogrid.make_grid(16, *inp.delta_range)
+    h = L.librpa_gpu_create()
+    try:
+        L.set_inputs(h, inp, grid)
+        L.librpa_gpu_chi0(h)
+        ec, ecq, ecw = L.librpa_gpu_ec(h, st.nk, 16)
+        samples = [(0, 0), (5, 3), (15, 15), (9, 7)]          # (iR, itau)
+        pairs = [(0, 0), (3, 34), (34, 12), (32, 33)]          # (U, V): C-C, C-H, H-C, O-H
+        chis = {p: L.librpa_gpu_get_chi0_tau(h, p[1], p[0], st.naux) for p in samples}
+        cq = {(iq, k): L.librpa_gpu_get_chi0_freq(h, iq, k, st.naux) for iq, k in ((0, 0), (1, 5), (5, 15))}
+        mq = {(iq, k): L.librpa_gpu_get_chi0_freq(h, int(syn.minus_index(st.kmesh)[iq]), k, st.naux)
+              for iq, k in cq}
+    finally:
+        L.librpa_gpu_destroy(h)
+    go, gv = ogreen.green(st.kmesh, inp.kfrac, inp.eig, inp.occ, inp.wfc, inp.efermi, grid["tau"])
+    ref = chi0_alg1(st, inp.lri, go, gv, samples, pairs=pairs)
+    ao = np.concatenate([[0], np.cumsum(st.n_aux)])
+    for p, (iR, it) in enumerate(samples):
+        scale = np.abs(chis[(iR, it)]).max()
+        for U, V in pairs:
+            blk_g = chis[(iR, it)][ao[U]:ao[U + 1], ao[V]:ao[V + 1]]
+            blk_o = ref[p][ao[U]:ao[U + 1], ao[V]:ao[V + 1]]
+            assert np.abs(blk_g - blk_o).max() <= TOL_CHI * scale
+    for key, m in cq.items():
+        s = np.abs(m).max()
+        assert np.abs(m - m.conj().T).max() <= 1e-12 * s
+        assert np.abs(mq[key] - m.conj()).max() <= 1e-12 * s
+        assert np.linalg.eigvalsh(m).max() <= 1e-12 * s
+    assert ec < 0 and np.all(ecq < 0) and np.all(ecw < 0)
+    assert math.isfinite(ec)
