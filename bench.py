@@ -204,12 +204,12 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     L.load(build_if_missing=False)
-    inp = syn.config_graphene()
+    inp = syn.config_graphene(kmesh=args.kmesh)
     st = inp.st
     stream = torch.cuda.Stream(device=local)
     o = L.librpa_gpu_default_opts()
     o.device = local
-    o.n_tau = 16
+    o.n_tau = args.ntau
     h = L.librpa_gpu_create(o, torch_stream=stream, torch_alloc=True)
 
     def barrier():
@@ -299,10 +299,12 @@ def run_gpu(args):
         "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded tight-binding KS data, LRI coefficients and Coulomb matrices "
                                 "of the paper's graphene/H2O workload shape)",
-        "config": {"workload": WORKLOAD, "atoms": st.natoms, "n_ao": st.nao, "n_aux": st.naux,
-                   "kmesh": "x".join(map(str, st.kmesh)), "n_tau": 16, "precision": "fp64",
+        "config": {"workload": WORKLOAD if (args.kmesh, args.ntau) == ((4, 4, 1), 16) else
+                   "profiling variant: graphene slab, %s k-mesh, %d tau" % ("x".join(map(str, st.kmesh)), args.ntau),
+                   "atoms": st.natoms, "n_ao": st.nao, "n_aux": st.naux,
+                   "kmesh": "x".join(map(str, st.kmesh)), "n_tau": args.ntau, "precision": "fp64",
                    "l2": "inputs larger than L2: chi0(R,tau) %.1f GB and G %.2f GB are streamed every step"
-                         % (16 * st.nk * st.naux ** 2 * 8 / 1e9, 2 * 16 * st.nk * st.nao ** 2 * 8 / 1e9)},
+                         % (args.ntau * st.nk * st.naux ** 2 * 8 / 1e9, 2 * args.ntau * st.nk * st.nao ** 2 * 8 / 1e9)},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "chi0_tflops": chi0_tflops,
@@ -315,13 +317,13 @@ def run_gpu(args):
                      "launches": nl, "flop": fl},
         "clocks": clk,
     }
-    if ws == 1:
+    if ws == 1 and not args.no_cpu:
         from oracle import build as obuild, grid as ogrid
         obuild.build()
-        cb = cpu_sample(inp, ogrid.make_grid(16, *inp.delta_range))
+        cb = cpu_sample(inp, ogrid.make_grid(args.ntau, *inp.delta_range))
         line["cpu_baseline"] = {"value": 1.0 / cb["t_energy_s"], "unit": UNIT, "cores": cb["cores"],
                                 "kind": "oracle", "sample": cb["sample"],
-                                "chi0_tflops": s["flop_chi0"] / (16 * st.nk) / cb["t_point_s"] / 1e12}
+                                "chi0_tflops": s["flop_chi0"] / (args.ntau * st.nk) / cb["t_point_s"] / 1e12}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -335,7 +337,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    # smaller variants of the same workload, for profiler captures only (not bench lines)
+    ap.add_argument("--kmesh", default="4,4,1", help="k-mesh of the graphene slab (profiling variants)")
+    ap.add_argument("--ntau", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     args = ap.parse_args()
+    args.kmesh = tuple(int(x) for x in args.kmesh.split(","))
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
