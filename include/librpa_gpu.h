@@ -57,8 +57,17 @@ extern "C" {
 #define LIBRPA_E_TIMEOUT (-6) /* a bounded device wait ran out */
 #define LIBRPA_E_NUMERIC (-7) /* a non-finite or inconsistent intermediate (e.g. complex G for real input) */
 
-/* ---------------------------------------------------------------- precision modes */
-#define LIBRPA_FP64 0 /* every step in FP64 (FP64 tensor-core MMA for the contractions) */
+/* ---------------------------------------------------------------- precision modes
+ * The dense GEMMs of the chi0 contraction (Algorithm 1) and of the ln det stage can run on the
+ * BF16 tensor cores with every FP64 operand row split into S exact BF16 digit planes
+ * (row value = 2^E sum_s d_s 2^{-7-8(s-1)}, |d_s| <= 128), digit products accumulated exactly
+ * and summed in FP64: S = 5 keeps 39 bits per operand (FP64-accurate to ~1e-12 relative),
+ * S = 3 about 23 bits, S = 1 plain BF16.  The exponentials of G(tau), the transform weights,
+ * the Cholesky factorisations' diagonal blocks and the E_c sum always stay FP64. */
+#define LIBRPA_FP64 0     /* every step in FP64 on the FP64 pipes (DMMA / DFMA) */
+#define LIBRPA_FP64_TC 1  /* chi0 and ln det GEMMs with 5 digit planes: FP64-accurate on the tensor cores */
+#define LIBRPA_SPLIT 2    /* chi0 GEMMs with 3 digit planes (mixed), ln det GEMMs with 5 */
+#define LIBRPA_BF16 3     /* chi0 GEMMs with 1 digit plane (BF16), ln det GEMMs with 5 */
 
 typedef struct librpa_gpu *librpa_gpu_t;
 
@@ -75,9 +84,11 @@ typedef struct {
   librpa_gpu_free_fn dev_free;   /* NULL = cudaFree */
   void *alloc_ctx;               /* passed to dev_alloc / dev_free */
   int n_tau;                     /* grid size (tau = omega points) when the library builds the grid */
-  int precision;                 /* LIBRPA_FP64 */
+  int precision;                 /* LIBRPA_FP64, LIBRPA_FP64_TC, LIBRPA_SPLIT or LIBRPA_BF16 */
   size_t hbm_budget;             /* bytes the handle may allocate; 0 = no limit */
   int check_level;               /* 0 = none; 1 = check G is real and the pivots finite */
+  int chi0_slices;               /* 0 = from precision; 1..5 = digit planes of the chi0 GEMMs */
+  int ec_slices;                 /* 0 = from precision; 1..5 = digit planes of the ln det GEMMs */
 } librpa_gpu_opts;
 
 /* Per-stage device times (ms, CUDA events on the handle's stream) and work counts of

@@ -147,7 +147,9 @@ void librpa_gpu_default_opts(librpa_gpu_opts *o) {
 int librpa_gpu_create(librpa_gpu_t *hp, const librpa_gpu_opts *o) {
   if (!hp || !o) return LIBRPA_E_ARG;
   *hp = nullptr;
-  if (o->n_tau < 1 || o->n_tau > 64 || o->precision != LIBRPA_FP64) return LIBRPA_E_ARG;
+  if (o->n_tau < 1 || o->n_tau > 64 || o->precision < LIBRPA_FP64 || o->precision > LIBRPA_BF16 ||
+      o->chi0_slices < 0 || o->chi0_slices > 5 || o->ec_slices < 0 || o->ec_slices > 5)
+    return LIBRPA_E_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
     cudaGetLastError();
@@ -157,6 +159,12 @@ int librpa_gpu_create(librpa_gpu_t *hp, const librpa_gpu_opts *o) {
   librpa_gpu *h = new (std::nothrow) librpa_gpu();
   if (!h) return LIBRPA_E_NOMEM;
   h->opts = *o;
+  {
+    // digit planes per stage: presets, then explicit overrides
+    static const int chi0_preset[4] = {0, 5, 3, 1}, ec_preset[4] = {0, 5, 5, 5};
+    h->chi0_S = o->chi0_slices ? o->chi0_slices : chi0_preset[o->precision];
+    h->ec_S = o->ec_slices ? o->ec_slices : ec_preset[o->precision];
+  }
   if (cudaSetDevice(o->device) != cudaSuccess) {
     delete h;
     return LIBRPA_E_CUDA;

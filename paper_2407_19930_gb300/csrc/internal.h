@@ -84,6 +84,8 @@ struct Chi0Plan {
 // ----------------------------------------------------------------- handle
 struct Handle {
   librpa_gpu_opts opts{};
+  int chi0_S = 0;   // digit planes of the chi0 GEMMs (0 = FP64 pipes)
+  int ec_S = 0;     // digit planes of the ln det GEMMs (0 = FP64 pipes)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::string last_error;

@@ -8,12 +8,20 @@
 // per (q, omega): W = chi0 L, A = I - L^H W (lower triangle), factor A.  The factorisations are
 // right-looking and blocked (panel width NB): the diagonal block is factored in shared memory by
 // one CTA per matrix, the panel below it by a triangular solve, and the trailing matrix is
-// updated by the batched complex GEMM; every matrix of a batch advances panel by panel in step,
-// so each launch has work from all of them.  Everything is FP64.
+// updated by a batched GEMM; every matrix of a batch advances panel by panel in step, so each
+// launch has work from all of them.
+//
+// Two arithmetic routes for the dense GEMMs (W, L^H W and the trailing updates):
+//   * native FP64 (complex GEMM on the FP64 pipe, k_zgemm.cu);
+//   * digit-sliced on the BF16 tensor cores (k_ozgemm.cu, S digit planes): complex products as
+//     2 x 2 real blocks [[Re, -Im], [Im, Re]], W produced transposed so that the second GEMM reads
+//     it row by row.
+// The diagonal blocks, the panel solves, the logarithms and the energy sum are FP64 in both.
 #include <cmath>
 #include <vector>
 
 #include "internal.h"
+#include "ozgemm.h"
 
 namespace librpa {
 namespace {
@@ -169,14 +177,22 @@ __global__ void k_energy(const double *lndet, const double *trace, const double 
   out[0] = tot;
 }
 
-// Blocked Cholesky of a batch of n x n matrices (lower triangle, in place), all in step.
+// Sliced-operand scratch of the tensor-core route.
+struct TcScratch {
+  oz::Sliced pa, pb;      // panel of the trailing updates (as A' and as B'^T)
+  int *err = nullptr;
+  int S = 0;
+};
+
+// Blocked Cholesky of `mats` (n x n, lower, in place, uniform stride when tc != nullptr), in step.
 void potrf_batched(Handle &h, double2 *const *d_mats, const std::vector<double2 *> &mats, int n, int ld,
-                   double *lndet, int *info) {
+                   double *lndet, int *info, TcScratch *tc) {
   cudaStream_t s = h.stream;
   const int B = (int)mats.size();
   const size_t smem = (size_t)NB * (NB + 1) * sizeof(double2);
   LR_CUDA(cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   LR_CUDA(cudaFuncSetAttribute(k_trsm_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smem)));
+  const long long bstride = B > 1 ? (long long)(mats[1] - mats[0]) : 0;
   for (int p0 = 0; p0 < n; p0 += NB) {
     k_potrf_diag<<<B, 256, smem, s>>>(d_mats, n, ld, p0, lndet, info);
     ++launch_counter();
@@ -185,6 +201,31 @@ void potrf_batched(Handle &h, double2 *const *d_mats, const std::vector<double2 
     dim3 g((unsigned)((rest + 63) / 64), (unsigned)B);
     k_trsm_panel<<<g, 64, 2 * smem, s>>>(d_mats, n, ld, p0);
     ++launch_counter();
+    // algorithmic work: the lower triangle (with diagonal) of a rest x rest update of rank nb
+    const double fl = 8.0 * B * (0.5 * rest * (rest + 1.0)) * nb;
+    if (tc) {
+      // A22 -= P P^H with P = A[p0+nb.., p0..p0+nb): stacked real GEMM, K' = 2 nb
+      const double2 *P = mats[0] + (size_t)(p0 + nb) * ld + p0;
+      oz::sliced_bind(tc->pa, tc->pa.digits, 2 * rest * B, 2 * nb, tc->S);
+      oz::sliced_bind(tc->pb, tc->pb.digits, rest * B, 2 * nb, tc->S);
+      oz::split_complex(P, ld, oz::OP_N, true, rest, nb, B, bstride, tc->pa, s);
+      oz::split_complex(P, ld, oz::OP_H, false, rest, nb, B, bstride, tc->pb, s);
+      oz::Out o;
+      o.C = (double *)(mats[0] + (size_t)(p0 + nb) * ld + p0 + nb);
+      o.ldc = ld;
+      o.batch_stride = bstride;
+      o.mode = 1;
+      o.alpha = -1.0;
+      o.beta = 1.0;
+      Handle::Timed tm{nullptr, nullptr, fl, 1};
+      LR_CUDA(cudaEventCreate(&tm.a));
+      LR_CUDA(cudaEventCreate(&tm.b));
+      LR_CUDA(cudaEventRecord(tm.a, s));
+      oz::gemm(tc->pa, tc->pb, 2 * rest, rest, B, o, 0, 0, 2, tc->err, s);
+      LR_CUDA(cudaEventRecord(tm.b, s));
+      h.timed.push_back(tm);
+      continue;
+    }
     std::vector<ZGemm> batch;
     for (int b = 0; b < B; ++b) {
       ZGemm z{};
@@ -206,45 +247,72 @@ void potrf_batched(Handle &h, double2 *const *d_mats, const std::vector<double2 
     f.transB = true;
     f.conjB = true;
     f.lower_only = true;
-    // algorithmic work: the lower triangle (with diagonal) of a rest x rest update of rank nb
-    zgemm_batched(batch, f, s, h, 1, 8.0 * B * (0.5 * rest * (rest + 1.0)) * nb);
+    zgemm_batched(batch, f, s, h, 1, fl);
   }
   LR_CUDA(cudaGetLastError());
 }
 
+size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+
 }  // namespace
 
 int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
-  const int n = h.naux, nq = h.mesh.size(), nw = h.ntau;
+  const int n = h.naux, nq = h.mesh.size(), nw = h.ntau, S = h.ec_S;
   const size_t n2 = (size_t)n * n;
   cudaStream_t s = h.stream;
-  // workspace: L[nq], W[nw], A[nw] (complex n x n), pointer tables, lndet/trace/info, output
+  // workspace: L[nq], W[nw], A[nw] (complex n x n), pointer tables, lndet/trace/info, output,
+  // and for the tensor-core route the digit planes
   const size_t mat = n2 * sizeof(double2);
-  const size_t o_L = 0, o_W = o_L + nq * mat, o_A = o_W + nw * mat, o_ptr = o_A + nw * mat;
-  const size_t n_ptr = (size_t)nq + nw + 8;
-  const size_t o_ld = o_ptr + ((n_ptr * 8 + 255) / 256) * 256;
-  const size_t o_tr = o_ld + ((size_t)nq * nw * 8 + 8 * 1024 + 255) / 256 * 256;
-  const size_t o_inf = o_tr + ((size_t)nq * nw * 8 + 255) / 256 * 256;
-  const size_t o_out = o_inf + ((size_t)(nq + nq * nw) * 4 + 255) / 256 * 256;
-  const size_t o_wo = o_out + ((size_t)(1 + nq + nw) * 8 + 255) / 256 * 256;
-  const size_t total = o_wo + (size_t)nw * 8 + 256;
-  h.ensure(h.work, total);
+  const int bmax = std::max(nq, nw);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += al256(bytes); return o; };
+  const size_t o_L = take(nq * mat), o_W = take(nw * mat), o_A = take(nw * mat);
+  const size_t o_ptr = take(((size_t)nq + nw + 8) * 8);
+  const size_t o_ld = take(((size_t)nq * nw + nq) * 8), o_tr = take((size_t)nq * nw * 8);
+  const size_t o_inf = take((size_t)(nq + nq * nw) * 4), o_out = take((size_t)(1 + nq + nw) * 8);
+  const size_t o_wo = take((size_t)nw * 8), o_err = take(4);
+  size_t o_sx = 0, o_sw = 0, o_sl = 0, o_slh = 0, o_pa = 0, o_pb = 0;
+  if (S > 0) {
+    o_sx = take(oz::sliced_bytes(nw * 2 * n, 2 * n, S));
+    o_sw = take(oz::sliced_bytes(nw * n, 2 * n, S));
+    o_sl = take(oz::sliced_bytes(n, 2 * n, S));
+    o_slh = take(oz::sliced_bytes(2 * n, 2 * n, S));
+    o_pa = take(oz::sliced_bytes(bmax * 2 * n, 2 * NB, S));
+    o_pb = take(oz::sliced_bytes(bmax * n, 2 * NB, S));
+  }
+  h.ensure(h.work, off);
   char *w = (char *)h.work.p;
   double2 *Lq = (double2 *)(w + o_L), *Wm = (double2 *)(w + o_W), *Am = (double2 *)(w + o_A);
   double2 **ptrs = (double2 **)(w + o_ptr);
   double *lndet = (double *)(w + o_ld), *trace = (double *)(w + o_tr), *out = (double *)(w + o_out);
   double *wo = (double *)(w + o_wo);
   int *info = (int *)(w + o_inf);
+  int *err = (int *)(w + o_err);
   double *lndet_v = lndet + (size_t)nq * nw;   // scratch for the V(q) factorisations
   LR_CUDA(cudaMemsetAsync(lndet, 0, ((size_t)nq * nw + nq) * 8, s));
   LR_CUDA(cudaMemsetAsync(info, 0, (size_t)(nq + nq * nw) * 4, s));
+  LR_CUDA(cudaMemsetAsync(err, 0, 4, s));
   LR_CUDA(cudaMemcpyAsync(wo, h.w_omega.data(), (size_t)nw * 8, cudaMemcpyHostToDevice, s));
+  TcScratch tcs;
+  TcScratch *tc = nullptr;
+  oz::Sliced sx, sw, sl, slh;
+  if (S > 0) {
+    tcs.S = S;
+    tcs.err = err;
+    oz::sliced_bind(tcs.pa, w + o_pa, bmax * 2 * n, 2 * NB, S);
+    oz::sliced_bind(tcs.pb, w + o_pb, bmax * n, 2 * NB, S);
+    oz::sliced_bind(sx, w + o_sx, nw * 2 * n, 2 * n, S);
+    oz::sliced_bind(sw, w + o_sw, nw * n, 2 * n, S);
+    oz::sliced_bind(sl, w + o_sl, n, 2 * n, S);
+    oz::sliced_bind(slh, w + o_slh, 2 * n, 2 * n, S);
+    tc = &tcs;
+  }
   // Cholesky of every V(q)
   LR_CUDA(cudaMemcpyAsync(Lq, h.d_vq.p, nq * mat, cudaMemcpyDeviceToDevice, s));
   std::vector<double2 *> lp(nq);
   for (int q = 0; q < nq; ++q) lp[q] = Lq + q * n2;
   LR_CUDA(cudaMemcpyAsync(ptrs, lp.data(), nq * 8, cudaMemcpyHostToDevice, s));
-  potrf_batched(h, ptrs, lp, n, n, lndet_v, info);
+  potrf_batched(h, ptrs, lp, n, n, lndet_v, info, tc);
   {
     dim3 g((unsigned)((n2 + 255) / 256), (unsigned)nq);
     k_zero_upper<<<g, 256, 0, s>>>(ptrs, n, n);
@@ -255,54 +323,91 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   std::vector<double2 *> ap(nw);
   for (int k = 0; k < nw; ++k) ap[k] = Am + k * n2;
   LR_CUDA(cudaMemcpyAsync(aptr, ap.data(), nw * 8, cudaMemcpyHostToDevice, s));
+  // algorithmic work (8 flops per complex MAC): W = chi0 L with L lower triangular,
+  // sum_j (n - j) = n (n + 1) / 2 MACs per row; A = -L^H W on the lower triangle,
+  // sum_{i >= j} (n - i) MACs per matrix
+  const double dn = n;
+  const double fl_w = 8.0 * nw * dn * (dn * (dn + 1) / 2), fl_a = 8.0 * nw * (dn * (dn + 1) * (dn + 2) / 6);
   for (int q = 0; q < nq; ++q) {
-    // W = chi0(q, omega) L_q  (L lower triangular: k >= j)
-    std::vector<ZGemm> b1, b2;
-    for (int k = 0; k < nw; ++k) {
-      ZGemm z{};
-      z.A = chi + ((size_t)q * nw + k) * n2;
-      z.B = Lq + q * n2;
-      z.C = Wm + k * n2;
-      z.M = z.N = z.K = n;
-      z.lda = z.ldb = z.ldc = n;
-      z.alpha = make_double2(1.0, 0.0);
-      z.beta = make_double2(0.0, 0.0);
-      b1.push_back(z);
-      ZGemm y{};
-      y.A = Lq + q * n2;     // op(A) = L^H: stored [K][M], conjugated
-      y.B = Wm + k * n2;
-      y.C = Am + k * n2;
-      y.M = y.N = y.K = n;
-      y.lda = y.ldb = y.ldc = n;
-      y.alpha = make_double2(-1.0, 0.0);
-      y.beta = make_double2(0.0, 0.0);
-      b2.push_back(y);
+    if (S > 0) {
+      const double2 *L = Lq + q * n2;
+      oz::split_complex(L, n, oz::OP_N, false, n, n, 1, 0, sl, s);     // B'^T of W = chi0 L
+      oz::split_complex(L, n, oz::OP_H, true, n, n, 1, 0, slh, s);     // A' of L^H W
+      oz::split_complex(chi + (size_t)q * nw * n2, n, oz::OP_N, true, n, n, nw, (long long)n2, sx, s);
+      oz::Out o1;   // W^T, so that the second GEMM reads W column by column as rows
+      o1.C = (double *)Wm;
+      o1.ldc = n;
+      o1.batch_stride = (long long)n2;
+      o1.mode = 2;
+      Handle::Timed t1{nullptr, nullptr, fl_w, 1};
+      LR_CUDA(cudaEventCreate(&t1.a));
+      LR_CUDA(cudaEventCreate(&t1.b));
+      LR_CUDA(cudaEventRecord(t1.a, s));
+      oz::gemm(sx, sl, 2 * n, n, nw, o1, 0, 2, 0, err, s);
+      LR_CUDA(cudaEventRecord(t1.b, s));
+      h.timed.push_back(t1);
+      oz::split_complex(Wm, n, oz::OP_T, false, n, n, nw, (long long)n2, sw, s);   // B'^T rows j: W[k][j]
+      oz::Out o2;
+      o2.C = (double *)Am;
+      o2.ldc = n;
+      o2.batch_stride = (long long)n2;
+      o2.mode = 1;
+      o2.alpha = -1.0;
+      Handle::Timed t2{nullptr, nullptr, fl_a, 1};
+      LR_CUDA(cudaEventCreate(&t2.a));
+      LR_CUDA(cudaEventCreate(&t2.b));
+      LR_CUDA(cudaEventRecord(t2.a, s));
+      oz::gemm(slh, sw, 2 * n, n, nw, o2, 1, 0, 2, err, s);
+      LR_CUDA(cudaEventRecord(t2.b, s));
+      h.timed.push_back(t2);
+    } else {
+      // W = chi0(q, omega) L_q  (L lower triangular: k >= j)
+      std::vector<ZGemm> b1, b2;
+      for (int k = 0; k < nw; ++k) {
+        ZGemm z{};
+        z.A = chi + ((size_t)q * nw + k) * n2;
+        z.B = Lq + q * n2;
+        z.C = Wm + k * n2;
+        z.M = z.N = z.K = n;
+        z.lda = z.ldb = z.ldc = n;
+        z.alpha = make_double2(1.0, 0.0);
+        z.beta = make_double2(0.0, 0.0);
+        b1.push_back(z);
+        ZGemm y{};
+        y.A = Lq + q * n2;     // op(A) = L^H: stored [K][M], conjugated
+        y.B = Wm + k * n2;
+        y.C = Am + k * n2;
+        y.M = y.N = y.K = n;
+        y.lda = y.ldb = y.ldc = n;
+        y.alpha = make_double2(-1.0, 0.0);
+        y.beta = make_double2(0.0, 0.0);
+        b2.push_back(y);
+      }
+      ZGemmFlags f1;
+      f1.kfrom = 2;
+      zgemm_batched(b1, f1, s, h, 1, fl_w);
+      ZGemmFlags f2;
+      f2.transA = true;
+      f2.conjA = true;
+      f2.kfrom = 1;
+      f2.lower_only = true;
+      zgemm_batched(b2, f2, s, h, 1, fl_a);
     }
-    // algorithmic work (8 flops per complex MAC): W = chi0 L with L lower triangular,
-    // sum_j (n - j) = n (n + 1) / 2 MACs per row; A = -L^H W on the lower triangle,
-    // sum_{i >= j} (n - i) MACs per matrix
-    const double dn = n;
-    ZGemmFlags f1;
-    f1.kfrom = 2;
-    zgemm_batched(b1, f1, s, h, 1, 8.0 * nw * dn * (dn * (dn + 1) / 2));
-    ZGemmFlags f2;
-    f2.transA = true;
-    f2.conjA = true;
-    f2.kfrom = 1;
-    f2.lower_only = true;
-    zgemm_batched(b2, f2, s, h, 1, 8.0 * nw * (dn * (dn + 1) * (dn + 2) / 6));
     k_diag_shift<<<nw, 256, 0, s>>>(aptr, n, n, trace + (size_t)q * nw);
     ++launch_counter();
-    potrf_batched(h, aptr, ap, n, n, lndet + (size_t)q * nw, info + nq + (size_t)q * nw);
+    potrf_batched(h, aptr, ap, n, n, lndet + (size_t)q * nw, info + nq + (size_t)q * nw, tc);
   }
   k_energy<<<1, 1, 0, s>>>(lndet, trace, wo, nq, nw, out);
   ++launch_counter();
   LR_CUDA(cudaGetLastError());
   std::vector<double> res(1 + nq + nw);
   std::vector<int> inf(nq + (size_t)nq * nw);
+  int e_host = 0;
   LR_CUDA(cudaMemcpyAsync(res.data(), out, res.size() * 8, cudaMemcpyDeviceToHost, s));
   LR_CUDA(cudaMemcpyAsync(inf.data(), info, inf.size() * 4, cudaMemcpyDeviceToHost, s));
+  LR_CUDA(cudaMemcpyAsync(&e_host, err, 4, cudaMemcpyDeviceToHost, s));
   LR_CUDA(cudaStreamSynchronize(s));
+  if (e_host) return LIBRPA_E_TIMEOUT;
   for (int v : inf)
     if (v) return LIBRPA_E_NOT_PD;
   *ec = res[0];

@@ -27,6 +27,9 @@ LIBRPA_E_NOT_PD = -5
 LIBRPA_E_TIMEOUT = -6
 LIBRPA_E_NUMERIC = -7
 LIBRPA_FP64 = 0
+LIBRPA_FP64_TC = 1
+LIBRPA_SPLIT = 2
+LIBRPA_BF16 = 3
 
 _CODES = {v: k for k, v in globals().items() if k.startswith("LIBRPA_E_")}
 
@@ -37,7 +40,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 class librpa_gpu_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("n_tau", ctypes.c_int),
-                ("precision", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("check_level", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("check_level", ctypes.c_int),
+                ("chi0_slices", ctypes.c_int), ("ec_slices", ctypes.c_int)]
 
 
 class librpa_gpu_stats(ctypes.Structure):
