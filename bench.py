@@ -41,6 +41,11 @@ WORKLOAD = ("graphene 4x4 supercell + H2O-shaped molecule: 35 atoms, n_ao 431, N
 # (1.25 TFLOP/s / 2250 TFLOP/s); no FP64 figure is in the measured-peaks file.
 NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
 
+# precision presets of the library (include/librpa_gpu.h): name -> (LIBRPA_* value, dtype label)
+PRECISIONS = {"fp64": (0, "f64"), "fp64_tc": (1, "f64-accurate: bf16 digit planes (5) on tcgen05"),
+              "split": (2, "mixed: chi0 GEMMs on 3 bf16 digit planes, ln det on 5"),
+              "bf16": (3, "mixed: chi0 GEMMs on 1 bf16 digit plane, ln det on 5")}
+
 # DRAM traffic per launch of the dominant kernels from one ncu capture (see profiles/),
 # valid only while the kernel source is unchanged (sha256 of the file at capture time).
 TRAFFIC = {}
@@ -210,6 +215,7 @@ def run_gpu(args):
     o = L.librpa_gpu_default_opts()
     o.device = local
     o.n_tau = args.ntau
+    o.precision = PRECISIONS[args.precision][0]
     h = L.librpa_gpu_create(o, torch_stream=stream, torch_alloc=True)
 
     def barrier():
@@ -297,12 +303,13 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded tight-binding KS data, LRI coefficients and Coulomb matrices "
-                                "of the paper's graphene/H2O workload shape)",
+        "dtype": PRECISIONS[args.precision][1],
+        "data": "synthetic (seeded tight-binding KS data, LRI coefficients and Coulomb matrices "
+                "of the paper's graphene/H2O workload shape)",
         "config": {"workload": WORKLOAD if (args.kmesh, args.ntau) == ((4, 4, 1), 16) else
                    "profiling variant: graphene slab, %s k-mesh, %d tau" % ("x".join(map(str, st.kmesh)), args.ntau),
                    "atoms": st.natoms, "n_ao": st.nao, "n_aux": st.naux,
-                   "kmesh": "x".join(map(str, st.kmesh)), "n_tau": args.ntau, "precision": "fp64",
+                   "kmesh": "x".join(map(str, st.kmesh)), "n_tau": args.ntau, "precision": args.precision,
                    "l2": "inputs larger than L2: chi0(R,tau) %.1f GB and G %.2f GB are streamed every step"
                          % (args.ntau * st.nk * st.naux ** 2 * 8 / 1e9, 2 * args.ntau * st.nk * st.nao ** 2 * 8 / 1e9)},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
@@ -341,6 +348,7 @@ def main():
     ap.add_argument("--kmesh", default="4,4,1", help="k-mesh of the graphene slab (profiling variants)")
     ap.add_argument("--ntau", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64")
     args = ap.parse_args()
     args.kmesh = tuple(int(x) for x in args.kmesh.split(","))
     if args.impl == "reference":

@@ -121,6 +121,7 @@ void free_device_state(Handle &h) {
   h.release(h.d_occ);
   h.release(h.zgemm_args);
   h.release(h.gemm_args);
+  h.release(h.oz_args);
   h.release(h.work);
   for (DevBuf *b : h.plan.all()) h.release(*b);
   h.lri_dirty = true;
@@ -160,8 +161,9 @@ int librpa_gpu_create(librpa_gpu_t *hp, const librpa_gpu_opts *o) {
   if (!h) return LIBRPA_E_NOMEM;
   h->opts = *o;
   {
-    // digit planes per stage: presets, then explicit overrides
-    static const int chi0_preset[4] = {0, 5, 3, 1}, ec_preset[4] = {0, 5, 5, 5};
+    // arithmetic per stage (-1 = FP64 pipes, 0 = plain BF16, 1..5 = digit planes): presets,
+    // then explicit overrides
+    static const int chi0_preset[4] = {-1, 5, 3, 0}, ec_preset[4] = {-1, 5, 5, 5};
     h->chi0_S = o->chi0_slices ? o->chi0_slices : chi0_preset[o->precision];
     h->ec_S = o->ec_slices ? o->ec_slices : ec_preset[o->precision];
   }

@@ -75,17 +75,24 @@ struct Chi0Plan {
   // device copies of the per-atom tables, point list, workspace and GEMM descriptors
   DevBuf t_n_ao, t_n_aux, t_ao_off, t_aux_off, t_m, t_lam_off, t_kap_off, t_bg_off, t_ag_off, t_n_off, t_x_off,
       t_o_off, t_pts, ws, gargs1, gargs2;
+  // tensor-core route: digit planes of the packed coefficients in the two row groupings
+  // (rows (nu, j) per atom with K = m_V for the N and X steps; rows mu with K = n_U m_U for
+  // the final contraction), the planes' shape, and the ragged-entry tables of the O operand
+  int tc_S = 0, max_m = 0, max_nm = 0, cpnx_rows = 0;
+  std::vector<int> cpnx_off;
+  DevBuf cp_nx, cp_f, t_oe_off, t_oe_k, gargs3;
   std::vector<DevBuf *> all() {
     return {&d_lam, &d_uni, &d_kap, &t_n_ao, &t_n_aux, &t_ao_off, &t_aux_off, &t_m, &t_lam_off, &t_kap_off,
-            &t_bg_off, &t_ag_off, &t_n_off, &t_x_off, &t_o_off, &t_pts, &ws, &gargs1, &gargs2};
+            &t_bg_off, &t_ag_off, &t_n_off, &t_x_off, &t_o_off, &t_pts, &ws, &gargs1, &gargs2,
+            &cp_nx, &cp_f, &t_oe_off, &t_oe_k, &gargs3};
   }
 };
 
 // ----------------------------------------------------------------- handle
 struct Handle {
   librpa_gpu_opts opts{};
-  int chi0_S = 0;   // digit planes of the chi0 GEMMs (0 = FP64 pipes)
-  int ec_S = 0;     // digit planes of the ln det GEMMs (0 = FP64 pipes)
+  int chi0_S = -1;  // chi0 GEMMs: -1 = FP64 pipes, 0 = plain BF16, 1..5 = BF16 digit planes
+  int ec_S = -1;    // ln det GEMMs: same encoding
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::string last_error;
@@ -123,6 +130,7 @@ struct Handle {
   DevBuf d_cpack;     // packed LRI coefficients
   DevBuf zgemm_args;  // descriptors and tile lists of batched GEMM launches
   DevBuf gemm_args;
+  DevBuf oz_args;     // descriptors of the tensor-core GEMM launches
   DevBuf work;        // per-call workspace
   bool chi0_done = false, lri_dirty = true;
   Chi0Plan plan;

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "ozgemm.h"
 
 namespace librpa {
 namespace {
@@ -179,8 +180,12 @@ struct OArgs {
   long long o_sz_p;
 };
 
+// T = double for the FP64-accurate modes; T = float when the contraction GEMMs themselves keep
+// at most ~23 bits (mixed modes), where the FP32 pipe (~72 TFLOP/s) carries the same accuracy.
+template <class T>
 __global__ void __launch_bounds__(256) k_oassemble(OArgs a) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sm = reinterpret_cast<T *>(smraw);
   const int V = blockIdx.y % a.natoms;
   const int U = (blockIdx.y / a.natoms) % a.natoms;
   const int p = blockIdx.y / (a.natoms * a.natoms);
@@ -188,9 +193,9 @@ __global__ void __launch_bounds__(256) k_oassemble(OArgs a) {
   const int c0 = blockIdx.x * 64;
   if (c0 >= mU) return;
   const int nU = a.n_ao[U], nV = a.n_ao[V], two = 2 * nV;
-  double *Lm = sm;                 // [nU][two]
-  double *LX = Lm + nU * two;      // [nU][two]
-  double *RG = LX + nU * two;      // [two][64]
+  T *Lm = sm;                 // [nU][two]
+  T *LX = Lm + nU * two;      // [nU][two]
+  T *RG = LX + nU * two;      // [two][64]
   const Point pt = a.pts[p];
   const int tid = threadIdx.x, col = tid & 63, rg = tid >> 6;
   const size_t n2 = (size_t)a.nao * a.nao;
@@ -235,13 +240,13 @@ __global__ void __launch_bounds__(256) k_oassemble(OArgs a) {
     }
     __syncthreads();
     if (!live) continue;
-    double acc[16];
+    T acc[16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) acc[r] = 0.0;
+    for (int r = 0; r < 16; ++r) acc[r] = T(0);
     for (int t = 0; t < two; ++t) {
       const double *Ns = t < nV ? NB : NA;
-      const double rn = Ns[(size_t)(nu * nV + (t % nV)) * a.m_all + ucol];
-      const double rgv = RG[t * 64 + col];
+      const T rn = (T)Ns[(size_t)(nu * nV + (t % nV)) * a.m_all + ucol];
+      const T rgv = RG[t * 64 + col];
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         const int i = rg + 4 * r;
@@ -419,9 +424,257 @@ void chi0_plan(Handle &h) {
   upload(h, P.t_n_off, P.n_off);
   upload(h, P.t_x_off, P.x_off);
   upload(h, P.t_o_off, P.o_off);
+  // tensor-core route: digit planes of the packed coefficients, split once per plan
+  P.max_m = P.max_nm = 0;
+  P.cpnx_off.assign(nat + 1, 0);
+  for (int a = 0; a < nat; ++a) {
+    P.max_m = std::max(P.max_m, P.m[a]);
+    P.max_nm = std::max(P.max_nm, h.n_ao[a] * P.m[a]);
+    P.cpnx_off[a + 1] = P.cpnx_off[a] + h.n_aux[a] * h.n_ao[a];
+  }
+  P.cpnx_rows = P.cpnx_off[nat];
+  P.tc_S = h.chi0_S;
+  if (P.tc_S >= 0) {
+    const int S = P.tc_S;
+    const double *Cp = (const double *)h.d_cpack.p;
+    oz::Sliced cpnx, cpf;
+    h.ensure(P.cp_nx, oz::sliced_bytes(P.cpnx_rows, P.max_m, S));
+    h.ensure(P.cp_f, oz::sliced_bytes(h.naux, P.max_nm, S));
+    oz::sliced_bind(cpnx, P.cp_nx.p, P.cpnx_rows, P.max_m, S);
+    oz::sliced_bind(cpf, P.cp_f.p, h.naux, P.max_nm, S);
+    for (int a = 0; a < nat; ++a) {
+      const int nm = h.n_ao[a] * P.m[a];
+      // rows (nu, j) of atom a, K = m_a (N and X steps)
+      oz::split_real(Cp + P.cp_off[a], P.m[a], false, h.n_aux[a] * h.n_ao[a], P.m[a], 1, 0, cpnx, h.stream,
+                     P.cpnx_off[a]);
+      // rows mu of atom a, K = n_a m_a (final contraction)
+      oz::split_real(Cp + P.cp_off[a], nm, false, h.n_aux[a], nm, 1, 0, cpf, h.stream, h.aux_off[a]);
+    }
+    LR_CUDA(cudaStreamSynchronize(h.stream));
+  }
 }
 
+namespace {
+
+// O = M + M* + Z + Z* for the np points of a batch (FP64 pipe).
+void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw, double *Ow) {
+  Chi0Plan &P = h.plan;
+  const int nat = h.natoms;
+  int maxn = 0, max_chunks = 0;
+  for (int a = 0; a < nat; ++a) {
+    maxn = std::max(maxn, h.n_ao[a]);
+    max_chunks = std::max(max_chunks, (P.m[a] + 63) / 64);
+  }
+  const bool fp32 = h.chi0_S >= 0 && h.chi0_S <= 3;
+  const size_t osmem = (size_t)(2 * maxn * 2 * maxn + 2 * maxn * 64) * (fp32 ? sizeof(float) : sizeof(double));
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
+  OArgs oa;
+  oa.G = (const double *)h.d_g.p;
+  oa.g_gstride = (size_t)h.ntau * h.mesh.size() * h.nao * h.nao;
+  oa.nR_stride = h.mesh.size();
+  oa.nao = h.nao;
+  oa.natoms = nat;
+  oa.naux = h.naux;
+  oa.n1 = h.mesh.n1;
+  oa.n2 = h.mesh.n2;
+  oa.n3 = h.mesh.n3;
+  oa.pts = dpts;
+  oa.n_ao = (const int *)P.t_n_ao.p;
+  oa.n_aux = (const int *)P.t_n_aux.p;
+  oa.ao_off = (const int *)P.t_ao_off.p;
+  oa.aux_off = (const int *)P.t_aux_off.p;
+  oa.m = (const int *)P.t_m.p;
+  oa.kap = (const int *)P.d_kap.p;
+  oa.kap_off = (const long long *)P.t_kap_off.p;
+  oa.N = Nw;
+  oa.n_off = (const long long *)P.t_n_off.p;
+  oa.n_sz_g = P.n_sz;
+  oa.n_sz_p = 2 * P.n_sz;
+  oa.m_all = P.m_all;
+  oa.X = Xw;
+  oa.x_off = (const long long *)P.t_x_off.p;
+  oa.x_sz_g = P.x_sz;
+  oa.x_sz_p = 2 * P.x_sz;
+  oa.O = Ow;
+  oa.o_off = (const long long *)P.t_o_off.p;
+  oa.o_sz_p = P.o_sz;
+  dim3 og((unsigned)max_chunks, (unsigned)(np * nat * nat));
+  if (fp32)
+    k_oassemble<float><<<og, 256, osmem, h.stream>>>(oa);
+  else
+    k_oassemble<double><<<og, 256, osmem, h.stream>>>(oa);
+  ++launch_counter();
+  LR_CUDA(cudaGetLastError());
+}
+
+// Points of the (R, tau) grid in flat order: point idx = itau * nR + iR.
+std::vector<Point> make_points(Handle &h, long long p0, int np) {
+  const int nR = h.mesh.size();
+  std::vector<Point> pts(np);
+  for (int q = 0; q < np; ++q) {
+    const long long idx = p0 + q;
+    pts[q].itau = (int)(idx / nR);
+    pts[q].iR = (int)(idx % nR);
+    h.mesh.split(pts[q].iR, pts[q].R[0], pts[q].R[1], pts[q].R[2]);
+  }
+  return pts;
+}
+
+void timed_grouped(Handle &h, const oz::Sliced &a, const oz::Sliced &b, const std::vector<oz::Entry> &es, int *err,
+                   DevBuf &args) {
+  double fl = 0;
+  for (const oz::Entry &e : es) fl += 2.0 * e.M * e.N * e.K;
+  Handle::Timed t{nullptr, nullptr, fl, 0};
+  LR_CUDA(cudaEventCreate(&t.a));
+  LR_CUDA(cudaEventCreate(&t.b));
+  LR_CUDA(cudaEventRecord(t.a, h.stream));
+  oz::gemm_grouped(a, b, es, err, h.stream, h, args);
+  LR_CUDA(cudaEventRecord(t.b, h.stream));
+  h.timed.push_back(t);
+}
+
+// Tensor-core route: the N, X and final GEMMs on digit planes (S = h.chi0_S).
+void chi0_run_tc(Handle &h) {
+  Chi0Plan &P = h.plan;
+  const int nat = h.natoms, nR = h.mesh.size(), ntau = h.ntau, naux = h.naux, nao = h.nao, S = h.chi0_S;
+  cudaStream_t s = h.stream;
+  h.ensure(h.d_chi_tau, (size_t)ntau * nR * naux * naux * sizeof(double));
+  const int rows_bg = 2 * nat * P.m_all, rows_ag = 2 * nat * nao, rows_o = nat * naux;
+  // per point: FP64 N, X, O and the digit planes of Bg, Ag and O
+  const size_t fp = 8 * (size_t)(2 * P.n_sz + 2 * P.x_sz + P.o_sz);
+  const size_t per_point = fp + oz::sliced_bytes(rows_bg, P.max_m, S) + oz::sliced_bytes(rows_ag, P.max_m, S) +
+                           oz::sliced_bytes(rows_o, P.max_nm, S) + 4096;
+  const long long total_pts = (long long)ntau * nR;
+  long long npb = std::max<long long>(1, (2LL << 30) / (long long)per_point);
+  npb = std::min(npb, total_pts);
+  const size_t b_n = 8 * (size_t)npb * 2 * P.n_sz, b_x = 8 * (size_t)npb * 2 * P.x_sz, b_o = 8 * (size_t)npb * P.o_sz;
+  const size_t b_bg = oz::sliced_bytes((int)npb * rows_bg, P.max_m, S);
+  const size_t b_ag = oz::sliced_bytes((int)npb * rows_ag, P.max_m, S);
+  const size_t b_od = oz::sliced_bytes((int)npb * rows_o, P.max_nm, S);
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  h.ensure(P.ws, al(b_n) + al(b_x) + al(b_o) + al(b_bg) + al(b_ag) + al(b_od) + 256);
+  char *w = (char *)P.ws.p;
+  double *Nw = (double *)w;
+  double *Xw = (double *)(w + al(b_n));
+  double *Ow = (double *)(w + al(b_n) + al(b_x));
+  char *wbg = w + al(b_n) + al(b_x) + al(b_o);
+  char *wag = wbg + al(b_bg), *wod = wag + al(b_ag);
+  int *err = (int *)(wod + al(b_od));
+  LR_CUDA(cudaMemsetAsync(err, 0, 4, s));
+  oz::Sliced cpnx, cpf;
+  oz::sliced_bind(cpnx, P.cp_nx.p, P.cpnx_rows, P.max_m, S);
+  oz::sliced_bind(cpf, P.cp_f.p, naux, P.max_nm, S);
+  const double spin = 2.0;
+  const size_t g_gstride = (size_t)ntau * nR * nao * nao;
+  for (long long p0 = 0; p0 < total_pts; p0 += npb) {
+    const int np = (int)std::min(npb, total_pts - p0);
+    std::vector<Point> pts = make_points(h, p0, np);
+    h.ensure(P.t_pts, np * sizeof(Point));
+    LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
+    // digit planes of the gathered Green's-function operands, straight from G
+    oz::GatherSrc gs;
+    gs.kind = 0;
+    gs.G = (const double *)h.d_g.p;
+    gs.g_gstride = (long long)g_gstride;
+    gs.nR = nR;
+    gs.nao = nao;
+    gs.n1 = h.mesh.n1;
+    gs.n2 = h.mesh.n2;
+    gs.n3 = h.mesh.n3;
+    gs.natoms = nat;
+    gs.rows_per_entry = P.m_all;
+    gs.pts = (const int *)P.t_pts.p;
+    gs.uni = (const int *)P.d_uni.p;
+    gs.lam = (const int *)P.d_lam.p;
+    gs.lam_off = (const long long *)P.t_lam_off.p;
+    gs.m = (const int *)P.t_m.p;
+    oz::Sliced sbg, sag, sod;
+    oz::sliced_bind(sbg, wbg, np * rows_bg, P.max_m, S);
+    oz::sliced_bind(sag, wag, np * rows_ag, P.max_m, S);
+    oz::sliced_bind(sod, wod, np * rows_o, P.max_nm, S);
+    oz::split_gather(gs, np * rows_bg, P.max_m, sbg, s);
+    gs.kind = 1;
+    gs.rows_per_entry = nao;
+    oz::split_gather(gs, np * rows_ag, P.max_m, sag, s);
+    // N-step: N_V = Cpack_V Bg_V^T;  X-step: X_V = Ag_V Cpack_V^T
+    std::vector<oz::Entry> en, ex;
+    for (int q = 0; q < np; ++q)
+      for (int g = 0; g < 2; ++g)
+        for (int V = 0; V < nat; ++V) {
+          const int rowsV = h.n_aux[V] * h.n_ao[V], e = (q * 2 + g) * nat + V;
+          oz::Entry a{};
+          a.a_row0 = P.cpnx_off[V];
+          a.b_row0 = e * P.m_all;
+          a.M = rowsV;
+          a.N = P.m_all;
+          a.K = P.m[V];
+          a.C = Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V];
+          a.ldc = P.m_all;
+          a.alpha = 1.0;
+          en.push_back(a);
+          oz::Entry b{};
+          b.a_row0 = e * nao;
+          b.b_row0 = P.cpnx_off[V];
+          b.M = nao;
+          b.N = rowsV;
+          b.K = P.m[V];
+          b.C = Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V];
+          b.ldc = rowsV;
+          b.alpha = 1.0;
+          ex.push_back(b);
+        }
+    timed_grouped(h, cpnx, sbg, en, err, P.gargs1);
+    timed_grouped(h, sag, cpnx, ex, err, P.gargs2);
+    run_oassemble(h, (const Point *)P.t_pts.p, np, Nw, Xw, Ow);
+    // digit planes of O (rows nu per (point, U), K = n_U m_U), then the final contraction
+    {
+      std::vector<long long> off(np * nat);
+      std::vector<int> ke(np * nat);
+      for (int q = 0; q < np; ++q)
+        for (int U = 0; U < nat; ++U) {
+          off[q * nat + U] = (long long)q * P.o_sz + P.o_off[U];
+          ke[q * nat + U] = h.n_ao[U] * P.m[U];
+        }
+      h.ensure(P.t_oe_off, off.size() * 8);
+      h.ensure(P.t_oe_k, ke.size() * 4);
+      LR_CUDA(cudaMemcpyAsync(P.t_oe_off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s));
+      LR_CUDA(cudaMemcpyAsync(P.t_oe_k.p, ke.data(), ke.size() * 4, cudaMemcpyHostToDevice, s));
+      oz::split_ragged(Ow, (const long long *)P.t_oe_off.p, (const int *)P.t_oe_k.p, naux, np * nat, P.max_nm, sod, s);
+      LR_CUDA(cudaStreamSynchronize(s));   // the host tables above are temporaries
+    }
+    std::vector<oz::Entry> ef;
+    for (int q = 0; q < np; ++q) {
+      double *chi = (double *)h.d_chi_tau.p + ((size_t)pts[q].itau * nR + pts[q].iR) * naux * naux;
+      for (int U = 0; U < nat; ++U) {
+        oz::Entry f{};
+        f.a_row0 = h.aux_off[U];
+        f.b_row0 = (q * nat + U) * naux;
+        f.M = h.n_aux[U];
+        f.N = naux;
+        f.K = h.n_ao[U] * P.m[U];
+        f.C = chi + (size_t)h.aux_off[U] * naux;
+        f.ldc = naux;
+        f.alpha = -spin;
+        ef.push_back(f);
+      }
+    }
+    timed_grouped(h, cpf, sod, ef, err, P.gargs3);
+  }
+  int e_host = 0;
+  LR_CUDA(cudaMemcpyAsync(&e_host, err, 4, cudaMemcpyDeviceToHost, s));
+  LR_CUDA(cudaStreamSynchronize(s));
+  if (e_host) throw Error{LIBRPA_E_TIMEOUT, "chi0: a bounded wait in the tensor-core GEMM ran out"};
+}
+
+}  // namespace
+
 void chi0_run(Handle &h, double *ms_gemm) {
+  if (ms_gemm) *ms_gemm = 0;
+  if (h.chi0_S >= 0) {
+    chi0_run_tc(h);
+    return;
+  }
   Chi0Plan &P = h.plan;
   const int nat = h.natoms, nR = h.mesh.size(), ntau = h.ntau, naux = h.naux, nao = h.nao;
   cudaStream_t s = h.stream;
@@ -442,16 +695,8 @@ void chi0_run(Handle &h, double *ms_gemm) {
   double *Ow = Xw + npb * 2 * P.x_sz;
   const double *Cp = (const double *)h.d_cpack.p;
   const double spin = 2.0;
-  // O-assembly shared memory: Lm + LX + RG
-  int maxn = 0;
-  for (int a = 0; a < nat; ++a) maxn = std::max(maxn, h.n_ao[a]);
-  const size_t osmem = (size_t)(2 * maxn * 2 * maxn + 2 * maxn * 64) * sizeof(double);
-  LR_CUDA(cudaFuncSetAttribute(k_oassemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
-  int max_chunks = 0, max_m = 0;
-  for (int a = 0; a < nat; ++a) {
-    max_chunks = std::max(max_chunks, (P.m[a] + 63) / 64);
-    max_m = std::max(max_m, P.m[a]);
-  }
+  int max_m = 0;
+  for (int a = 0; a < nat; ++a) max_m = std::max(max_m, P.m[a]);
   for (long long p0 = 0; p0 < total_pts; p0 += npb) {
     const int np = (int)std::min(npb, total_pts - p0);
     std::vector<Point> pts(np);
@@ -493,41 +738,7 @@ void chi0_run(Handle &h, double *ms_gemm) {
           b1.push_back(dx);
         }
     dgemm_batched(h, b1, s, P.gargs1);
-    // O assembly
-    OArgs oa;
-    oa.G = (const double *)h.d_g.p;
-    oa.g_gstride = g_gstride;
-    oa.nR_stride = nR;
-    oa.nao = nao;
-    oa.natoms = nat;
-    oa.naux = naux;
-    oa.n1 = h.mesh.n1;
-    oa.n2 = h.mesh.n2;
-    oa.n3 = h.mesh.n3;
-    oa.pts = dpts;
-    oa.n_ao = (const int *)P.t_n_ao.p;
-    oa.n_aux = (const int *)P.t_n_aux.p;
-    oa.ao_off = (const int *)P.t_ao_off.p;
-    oa.aux_off = (const int *)P.t_aux_off.p;
-    oa.m = (const int *)P.t_m.p;
-    oa.kap = (const int *)P.d_kap.p;
-    oa.kap_off = (const long long *)P.t_kap_off.p;
-    oa.N = Nw;
-    oa.n_off = (const long long *)P.t_n_off.p;
-    oa.n_sz_g = P.n_sz;
-    oa.n_sz_p = 2 * P.n_sz;
-    oa.m_all = P.m_all;
-    oa.X = Xw;
-    oa.x_off = (const long long *)P.t_x_off.p;
-    oa.x_sz_g = P.x_sz;
-    oa.x_sz_p = 2 * P.x_sz;
-    oa.O = Ow;
-    oa.o_off = (const long long *)P.t_o_off.p;
-    oa.o_sz_p = P.o_sz;
-    dim3 og((unsigned)max_chunks, (unsigned)(np * nat * nat));
-    k_oassemble<<<og, 256, osmem, s>>>(oa);
-    ++launch_counter();
-    LR_CUDA(cudaGetLastError());
+    run_oassemble(h, dpts, np, Nw, Xw, Ow);
     // final contraction into chi0(R, tau)
     std::vector<DGemm> b2;
     for (int q = 0; q < np; ++q) {

@@ -221,7 +221,7 @@ void potrf_batched(Handle &h, double2 *const *d_mats, const std::vector<double2 
       LR_CUDA(cudaEventCreate(&tm.a));
       LR_CUDA(cudaEventCreate(&tm.b));
       LR_CUDA(cudaEventRecord(tm.a, s));
-      oz::gemm(tc->pa, tc->pb, 2 * rest, rest, B, o, 0, 0, 2, tc->err, s);
+      oz::gemm(tc->pa, tc->pb, 2 * rest, rest, B, o, 0, 0, 2, tc->err, s, h);
       LR_CUDA(cudaEventRecord(tm.b, s));
       h.timed.push_back(tm);
       continue;
@@ -272,7 +272,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   const size_t o_inf = take((size_t)(nq + nq * nw) * 4), o_out = take((size_t)(1 + nq + nw) * 8);
   const size_t o_wo = take((size_t)nw * 8), o_err = take(4);
   size_t o_sx = 0, o_sw = 0, o_sl = 0, o_slh = 0, o_pa = 0, o_pb = 0;
-  if (S > 0) {
+  if (S >= 0) {
     o_sx = take(oz::sliced_bytes(nw * 2 * n, 2 * n, S));
     o_sw = take(oz::sliced_bytes(nw * n, 2 * n, S));
     o_sl = take(oz::sliced_bytes(n, 2 * n, S));
@@ -296,7 +296,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   TcScratch tcs;
   TcScratch *tc = nullptr;
   oz::Sliced sx, sw, sl, slh;
-  if (S > 0) {
+  if (S >= 0) {
     tcs.S = S;
     tcs.err = err;
     oz::sliced_bind(tcs.pa, w + o_pa, bmax * 2 * n, 2 * NB, S);
@@ -329,7 +329,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   const double dn = n;
   const double fl_w = 8.0 * nw * dn * (dn * (dn + 1) / 2), fl_a = 8.0 * nw * (dn * (dn + 1) * (dn + 2) / 6);
   for (int q = 0; q < nq; ++q) {
-    if (S > 0) {
+    if (S >= 0) {
       const double2 *L = Lq + q * n2;
       oz::split_complex(L, n, oz::OP_N, false, n, n, 1, 0, sl, s);     // B'^T of W = chi0 L
       oz::split_complex(L, n, oz::OP_H, true, n, n, 1, 0, slh, s);     // A' of L^H W
@@ -343,7 +343,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
       LR_CUDA(cudaEventCreate(&t1.a));
       LR_CUDA(cudaEventCreate(&t1.b));
       LR_CUDA(cudaEventRecord(t1.a, s));
-      oz::gemm(sx, sl, 2 * n, n, nw, o1, 0, 2, 0, err, s);
+      oz::gemm(sx, sl, 2 * n, n, nw, o1, 0, 2, 0, err, s, h);
       LR_CUDA(cudaEventRecord(t1.b, s));
       h.timed.push_back(t1);
       oz::split_complex(Wm, n, oz::OP_T, false, n, n, nw, (long long)n2, sw, s);   // B'^T rows j: W[k][j]
@@ -357,7 +357,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
       LR_CUDA(cudaEventCreate(&t2.a));
       LR_CUDA(cudaEventCreate(&t2.b));
       LR_CUDA(cudaEventRecord(t2.a, s));
-      oz::gemm(slh, sw, 2 * n, n, nw, o2, 1, 0, 2, err, s);
+      oz::gemm(slh, sw, 2 * n, n, nw, o2, 1, 0, 2, err, s, h);
       LR_CUDA(cudaEventRecord(t2.b, s));
       h.timed.push_back(t2);
     } else {

@@ -1,20 +1,18 @@
 // FP64-accurate GEMM on the BF16 tensor cores of sm_103a (see ozgemm.h for the scheme).
 //
-// Kernel structure (one CTA = one 128 x 64 output tile, 4 warps):
-//   * thread 0 issues TMA loads (cp.async.bulk.tensor, SWIZZLE_128B, K-major) of the S digit
-//     planes of the A tile (128 x 64) and of the B tile (64 x 64) for each 64-wide K step, then
-//     the tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 64, K = 16) of every digit
-//     pair into the TMEM accumulator of its diagonal, and commits to an mbarrier;
-//   * after a flush group of K steps (the largest group whose FP32 sums stay exact) all four
-//     warps read the accumulators (tcgen05.ld 32x32b, warp w owns TMEM lanes 32w..32w+31 = tile
-//     rows), convert them to integers and add them into exact int64 register sums;
-//   * the final int64 sums are scaled by 2^(E_A + E_B - 14 - 8(S-1)) into FP64.
-// Every wait on an mbarrier is bounded by the global timer; on a timeout the kernel records the
-// failure in *err, waits (bounded) for its own copies in flight, frees TMEM and returns.
+// Operands are split once into BF16 digit planes (k_row_expo + k_digits, or k_plain for plain
+// BF16); the GEMM kernel streams them with TMA (cp.async.bulk.tensor) into a shared-memory ring
+// and multiplies every digit pair with tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128,
+// N = 64, K = 16) into the TMEM accumulator of its diagonal; flush groups (the largest K range
+// whose FP32 sums stay exact) are moved into exact int64 register sums, scaled by
+// 2^(E_A + E_B - 14 - 8(S-1)) into FP64 at the end.  Every wait on an mbarrier is bounded by the
+// global timer; on a timeout the kernel records the failure in *err, waits (bounded) for its own
+// copies in flight, frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <cstdint>
+#include <cstring>
 #include <string>
 
 #include "internal.h"
@@ -26,9 +24,7 @@ namespace {
 
 // ------------------------------------------------------------------ splitting
 
-__device__ __forceinline__ int biased_exp(double v) {
-  return (int)((__double_as_longlong(v) >> 52) & 0x7FF);
-}
+__device__ __forceinline__ int biased_exp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
 
 // balanced base-256 digits of x = v 2^-E (|x| < 1): x ~ sum_s d_s 2^{-7-8(s-1)}, |d_s| <= 128
 template <int S>
@@ -92,42 +88,100 @@ struct CplxSrc {
   }
 };
 
+struct GatherDev {
+  GatherSrc g;
+  __device__ static int fold(int a, int n) {
+    const int r = a % n;
+    return r < 0 ? r + n : r;
+  }
+  __device__ double get(int r, int k) const {
+    const int e = r / g.rows_per_entry, rr = r % g.rows_per_entry;
+    const int V = e % g.natoms, gg = (e / g.natoms) % 2, p = e / (2 * g.natoms);
+    if (k >= g.m[V]) return 0.0;
+    const int *pt = g.pts + 5 * p;
+    const int *c = g.lam + 6 * (g.lam_off[V] + k);
+    int iR, row, col;
+    if (g.kind == 0) {
+      const int *u = g.uni + 6 * rr;
+      iR = (fold(u[1] - pt[2] - c[1], g.n1) * g.n2 + fold(u[2] - pt[3] - c[2], g.n2)) * g.n3 +
+           fold(u[3] - pt[4] - c[3], g.n3);
+      row = c[5];
+      col = u[5];
+    } else {
+      iR = (fold(pt[2] + c[1], g.n1) * g.n2 + fold(pt[3] + c[2], g.n2)) * g.n3 + fold(pt[4] + c[3], g.n3);
+      row = rr;
+      col = c[5];
+    }
+    const double *Gp = g.G + gg * g.g_gstride + ((long long)pt[1] * g.nR + iR) * g.nao * g.nao;
+    return Gp[(long long)row * g.nao + col];
+  }
+};
+
+struct RaggedSrc {
+  const double *base;
+  const long long *off;
+  const int *Ke;
+  int rows_pe;
+  __device__ double get(int r, int k) const {
+    const int e = r / rows_pe, rr = r % rows_pe;
+    const int K = Ke[e];
+    return k < K ? base[off[e] + (long long)rr * K + k] : 0.0;
+  }
+};
+
 // exponent of each row: one warp per row
 template <class Src>
-__global__ void k_row_expo(Src src, int rows, int K, int *expo) {
+__global__ void k_row_expo(Src src, int rows, int K, int row0, int *expo) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (w >= rows) return;
   int m = 0;
   for (int k = lane; k < K; k += 32) m = max(m, biased_exp(src.get(w, k)));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) expo[w] = m - 1022;
+  if (lane == 0) expo[row0 + w] = m - 1022;
 }
 
 template <int S, class Src>
-__global__ void k_digits(Src src, int rows, int K, int kpad, const int *expo, __nv_bfloat16 *dig) {
+__global__ void k_digits(Src src, int rows, int K, int kpad, int row0, long long plane, const int *expo,
+                         __nv_bfloat16 *dig) {
   const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= (long long)rows * kpad) return;
   const int r = (int)(x / kpad), k = (int)(x % kpad);
   int d[S];
-  make_digits<S>(k < K ? src.get(r, k) : 0.0, expo[r], d);
-  const long long plane = (long long)rows * kpad;
+  make_digits<S>(k < K ? src.get(r, k) : 0.0, expo[row0 + r], d);
+  const long long o = (long long)row0 * kpad + x;
 #pragma unroll
-  for (int s = 0; s < S; ++s) dig[s * plane + x] = __float2bfloat16_rn((float)d[s]);
+  for (int s = 0; s < S; ++s) dig[s * plane + o] = __float2bfloat16_rn((float)d[s]);
 }
 
 template <class Src>
-void split_any(const Src &src, Sliced &o, cudaStream_t s) {
-  const int rows = o.rows, K = o.K, kpad = o.kpad;
-  k_row_expo<Src><<<(unsigned)(((long long)rows * 32 + 255) / 256), 256, 0, s>>>(src, rows, K, o.expo);
+__global__ void k_plain(Src src, int rows, int K, int kpad, int row0, __nv_bfloat16 *dig) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (long long)rows * kpad) return;
+  const int r = (int)(x / kpad), k = (int)(x % kpad);
+  dig[(long long)row0 * kpad + x] = __double2bfloat16(k < K ? src.get(r, k) : 0.0);
+}
+
+template <class Src>
+void split_any(const Src &src, int rows, int K, int row0, Sliced &o, cudaStream_t s) {
+  if (row0 < 0 || row0 + rows > o.rows || K > o.kpad) throw Error{LIBRPA_E_ARG, "split: rows or K exceed the operand"};
+  const int kpad = o.kpad;
+  const long long plane = (long long)o.rows * kpad;
   const long long n = (long long)rows * kpad;
   const unsigned g = (unsigned)((n + 255) / 256);
+  if (o.S == 0) {
+    k_plain<Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, o.digits);
+    ++launch_counter();
+    LR_CUDA(cudaGetLastError());
+    return;
+  }
+  k_row_expo<Src><<<(unsigned)(((long long)rows * 32 + 255) / 256), 256, 0, s>>>(src, rows, K, row0, o.expo);
   switch (o.S) {
-    case 1: k_digits<1, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, o.expo, o.digits); break;
-    case 2: k_digits<2, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, o.expo, o.digits); break;
-    case 3: k_digits<3, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, o.expo, o.digits); break;
-    case 4: k_digits<4, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, o.expo, o.digits); break;
-    default: k_digits<5, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, o.expo, o.digits); break;
+    case 1: k_digits<1, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, o.digits); break;
+    case 2: k_digits<2, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, o.digits); break;
+    case 3: k_digits<3, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, o.digits); break;
+    case 4: k_digits<4, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, o.digits); break;
+    default: k_digits<5, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, o.digits); break;
   }
   launch_counter() += 2;
   LR_CUDA(cudaGetLastError());
@@ -187,16 +241,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)(16 >> 4) << 16;     // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
-  return d;
-}
 
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = BN
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -221,13 +265,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-struct KArgs {
-  int M, N, K;
-  int a_rows_pb, b_rows_pb;   // rows of one batch entry in the A / B digit planes
-  const int *ea, *eb;
-  Out out;
-  int km, kn, lower_div;
-  int *err;
+struct Tile {
+  int e, m0, n0;
 };
 
 template <int S>
@@ -236,122 +275,183 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
 }
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s
 
+// Pipelined, warp-specialised kernel (one CTA = one 128 x 64 output tile of one GEMM entry):
+//   warp 4 (one lane): TMA producer over a ring of NST shared-memory stages, each holding the
+//     NP digit planes of a 128 x 32 A slice and a 64 x 32 B slice (SWIZZLE_64B, K-major);
+//   warp 5 (one lane): tcgen05.mma issuer; commits free a stage when its MMAs complete and,
+//     at the end of a flush group, signal the epilogue;
+//   warps 0-3: epilogue; warp w owns TMEM lanes 32w..32w+31 (= tile rows); after each flush
+//     group they move the diagonal accumulators into exact int64 register sums and hand the
+//     TMEM columns back to the issuer.
+constexpr int PBK = 32;   // K per stage: one 64-byte swizzle row of BF16
+constexpr int NST = 3;    // pipeline depth
+
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart
+__device__ __forceinline__ uint64_t smem_desc64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(16 >> 4) << 16;     // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)4 << 61;             // SWIZZLE_64B
+  return d;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 template <int S>
-__global__ void __launch_bounds__(128, 1)
-    k_ozgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const KArgs a) {
+__global__ void __launch_bounds__(192, 1)
+    k_ozgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+             const Entry *__restrict__ entries, const Tile *__restrict__ tiles, const int *__restrict__ expoA,
+             const int *__restrict__ expoB, int *err) {
+  constexpr int NP = S > 0 ? S : 1;                   // digit planes (S = 0: one plane of plain BF16)
+  constexpr uint32_t A_BYTES = BM * PBK * 2, B_BYTES = BN * PBK * 2;
+  constexpr uint32_t STAGE = NP * (A_BYTES + B_BYTES);
+  // K steps per flush group: NP pairs x (32 G) x 2^14 <= 2^24 keeps the FP32 sums exact; plain
+  // BF16 accumulates over the whole K in FP32
+  constexpr int G = S == 0 ? (1 << 30) : 32 / NP;
+  constexpr uint32_t TMEM_COLS = tmem_cols<NP>();
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar_tma, bar_mma;
+  __shared__ uint64_t full[NST], empty[NST], tfull, tempty;
   __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, bz = blockIdx.z;
-  if (a.lower_div > 0 && n0 > m0 / a.lower_div) return;
+  const Tile tl = tiles[blockIdx.x];
+  const Entry en = entries[tl.e];
+  const int n0 = tl.n0, m0 = tl.m0;
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *sA = smem;                    // S planes of 128 x 64 BF16 (16 KB each)
-  uint8_t *sB = smem + S * BM * BK * 2;  // S planes of  64 x 64 BF16 ( 8 KB each)
-  constexpr uint32_t TX = S * (BM + BN) * BK * 2;
-  constexpr int G = 16 / S;              // K steps per flush: S pairs x (64 G) x 2^14 <= 2^24
   if (tid == 0) {
-    mbar_init(&bar_tma, 1);
-    mbar_init(&bar_mma, 1);
+#pragma unroll
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&tfull, 1);
+    mbar_init(&tempty, 4);
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  constexpr uint32_t TMEM_COLS = tmem_cols<S>();
   if (warp == 0) tmem_alloc(&tmem_slot, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-
+  int kbeg = m0 * en.km + n0 * en.kn;
+  kbeg = kbeg / PBK * PBK;
+  const int nsteps = en.K > kbeg ? (en.K - kbeg + PBK - 1) / PBK : 0;
+  const int ngroups = (nsteps + G - 1) / G;
+  const int arow = en.a_row0 + m0, brow = en.b_row0 + n0;
   long long acc[BN];
 #pragma unroll
   for (int j = 0; j < BN; ++j) acc[j] = 0;
-  int kbeg = m0 * a.km + n0 * a.kn;
-  kbeg = kbeg / BK * BK;
-  const int nsteps = a.K > kbeg ? (a.K - kbeg + BK - 1) / BK : 0;
-  uint32_t ph_tma = 0, ph_mma = 0;
-  const int arow = bz * a.a_rows_pb + m0, brow = bz * a.b_rows_pb + n0;
   bool failed = false;
-  for (int g0 = 0; g0 < nsteps && !failed; g0 += G) {
-    const int gn = min(G, nsteps - g0);
-    for (int c = 0; c < gn; ++c) {
-      const int k0 = kbeg + (g0 + c) * BK;
-      if (tid == 0) {
-        mbar_expect_tx(&bar_tma, TX);
+  if (warp == 4) {
+    if (lane == 0) {
+      for (int i = 0; i < nsteps; ++i) {
+        const int st = i % NST;
+        if (abort_flag || !mbar_wait(&empty[st], ((i / NST) & 1) ^ 1, WAIT_NS)) {
+          abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(&full[st], STAGE);
+        uint8_t *sa = smem + st * STAGE, *sb = sa + NP * A_BYTES;
+        const int k0 = kbeg + i * PBK;
 #pragma unroll
-        for (int s = 0; s < S; ++s) tma_load_3d(sA + s * BM * BK * 2, &tmA, &bar_tma, k0, arow, s);
+        for (int p = 0; p < NP; ++p) tma_load_3d(sa + p * A_BYTES, &tmA, &full[st], k0, arow, p);
 #pragma unroll
-        for (int s = 0; s < S; ++s) tma_load_3d(sB + s * BN * BK * 2, &tmB, &bar_tma, k0, brow, s);
+        for (int p = 0; p < NP; ++p) tma_load_3d(sb + p * B_BYTES, &tmB, &full[st], k0, brow, p);
       }
-      bool ok = mbar_wait(&bar_tma, ph_tma, WAIT_NS);
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
-      ph_tma ^= 1;
-      if (tid == 0) {
-        tc_fence_after();
-#pragma unroll
-        for (int s = 1; s <= S; ++s)
-#pragma unroll
-          for (int t = 1; t + s <= S + 1; ++t) {
-            const uint32_t dt = tmem + (uint32_t)(s + t - 2) * BN;
-            const uint32_t abase = smem_u32(sA + (s - 1) * BM * BK * 2);
-            const uint32_t bbase = smem_u32(sB + (t - 1) * BN * BK * 2);
-#pragma unroll
-            for (int j = 0; j < BK / 16; ++j)
-              umma(dt, smem_desc(abase + 32 * j), smem_desc(bbase + 32 * j), (c == 0 && j == 0 && s == 1) ? 0u : 1u);
-          }
-        umma_commit(&bar_mma);
-      }
-      ok = mbar_wait(&bar_mma, ph_mma, WAIT_NS);
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
-      ph_mma ^= 1;
     }
-    if (failed) break;
-    tc_fence_after();
-    // flush the diagonals of this group into the int64 sums
+  } else if (warp == 5) {
+    if (lane == 0) {
+      for (int i = 0; i < nsteps; ++i) {
+        const int st = i % NST, gi = i / G, c = i % G;
+        if (c == 0 && gi > 0 && (abort_flag || !mbar_wait(&tempty, (gi - 1) & 1, WAIT_NS))) {
+          abort_flag = 1;
+          break;
+        }
+        if (abort_flag || !mbar_wait(&full[st], (i / NST) & 1, WAIT_NS)) {
+          abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + NP * A_BYTES;
 #pragma unroll
-    for (int d = 2; d <= S + 1; ++d) {
-      const long long mul = 1LL << (8 * (S + 1 - d));
+        for (int s = 1; s <= NP; ++s)
+#pragma unroll
+          for (int t = 1; t + s <= NP + 1; ++t)
+#pragma unroll
+            for (int j = 0; j < PBK / 16; ++j)
+              umma(tmem + (uint32_t)(s + t - 2) * BN, smem_desc64(sa + (s - 1) * A_BYTES + 32 * j),
+                   smem_desc64(sb + (t - 1) * B_BYTES + 32 * j), (c == 0 && j == 0 && s == 1) ? 0u : 1u);
+        umma_commit(&empty[st]);
+        if (c == G - 1 || i == nsteps - 1) umma_commit(&tfull);
+      }
+    }
+  } else {
+    for (int gi = 0; gi < ngroups; ++gi) {
+      bool ok = !abort_flag && mbar_wait(&tfull, gi & 1, WAIT_NS);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        abort_flag = 1;
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      if constexpr (S > 0) {
+#pragma unroll
+        for (int d = 2; d <= S + 1; ++d) {
+          const long long mul = 1LL << (8 * (S + 1 - d));
+#pragma unroll
+          for (int cb = 0; cb < BN / 16; ++cb) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d - 2) * BN + cb * 16, r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) * mul;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty);
+      }
+    }
+    if (!failed) {
+      const int row = m0 + 32 * warp + lane;
+      const int ea = (S > 0 && row < en.M) ? expoA[en.a_row0 + row] : 0;
 #pragma unroll
       for (int cb = 0; cb < BN / 16; ++cb) {
         uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d - 2) * BN + cb * 16, r);
+        if constexpr (S == 0) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + cb * 16, r);
+        if (row >= en.M) continue;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) * mul;
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + cb * 16 + j;
+          if (col >= en.N) break;
+          double v;
+          if constexpr (S == 0)
+            v = nsteps > 0 ? en.alpha * (double)__uint_as_float(r[j]) : 0.0;
+          else
+            v = en.alpha * ldexp((double)acc[cb * 16 + j], ea + expoB[en.b_row0 + col] - 14 - 8 * (S - 1));
+          double *p;
+          if (en.mode == 0)
+            p = en.C + (long long)row * en.ldc + col;
+          else if (en.mode == 1)
+            p = en.C + 2 * ((long long)(row >> 1) * en.ldc + col) + (row & 1);
+          else
+            p = en.C + 2 * ((long long)col * en.ldc + (row >> 1)) + (row & 1);
+          *p = en.beta == 0.0 ? v : v + en.beta * *p;
+        }
       }
     }
-    tc_fence_before();
-    __syncthreads();
   }
-  if (failed) {
-    if (tid == 0) atomicExch(a.err, 1);
+  __syncthreads();
+  if (abort_flag) {
+    if (tid == 0) atomicExch(err, 1);
     // let copies and MMAs already issued land before the CTA gives up its memory
-    mbar_wait(&bar_tma, ph_tma, WAIT_NS);
-    mbar_wait(&bar_mma, ph_mma, WAIT_NS);
-  } else {
-    const int row = m0 + 32 * warp + lane;
-    if (row < a.M) {
-      const int ea = a.ea[(long long)bz * a.a_rows_pb + row];
-      const Out &o = a.out;
-#pragma unroll
-      for (int j = 0; j < BN; ++j) {
-        const int col = n0 + j;
-        if (col >= a.N) break;
-        const int e = ea + a.eb[(long long)bz * a.b_rows_pb + col] - 14 - 8 * (S - 1);
-        const double v = o.alpha * ldexp((double)acc[j], e);
-        double *p;
-        if (o.mode == 0)
-          p = o.C + (long long)bz * o.batch_stride + (long long)row * o.ldc + col;
-        else if (o.mode == 1)
-          p = o.C + 2 * ((long long)bz * o.batch_stride + (long long)(row >> 1) * o.ldc + col) + (row & 1);
-        else
-          p = o.C + 2 * ((long long)bz * o.batch_stride + (long long)col * o.ldc + (row >> 1)) + (row & 1);
-        *p = o.beta == 0.0 ? v : v + o.beta * *p;
-      }
+    if (tid == 0) {
+      for (int s = 0; s < NST; ++s) mbar_wait(&empty[s], 0, WAIT_NS / 8);
     }
   }
   tc_fence_before();
@@ -359,26 +459,28 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 CUtensorMap make_map(const Sliced &o, int box_rows) {
   CUtensorMap m;
-  const cuuint64_t dims[3] = {(cuuint64_t)o.kpad, (cuuint64_t)o.rows, (cuuint64_t)o.S};
+  const cuuint64_t dims[3] = {(cuuint64_t)o.kpad, (cuuint64_t)o.rows, (cuuint64_t)(o.S > 0 ? o.S : 1)};
   const cuuint64_t strides[2] = {(cuuint64_t)o.kpad * 2, (cuuint64_t)o.kpad * 2 * (cuuint64_t)o.rows};
-  const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)PBK, (cuuint32_t)box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = g_encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)o.digits, dims, strides, box, estr,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error{LIBRPA_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r)};
   return m;
 }
 
 template <int S>
-void launch(const CUtensorMap &ma, const CUtensorMap &mb, const KArgs &ka, dim3 grid, cudaStream_t s) {
-  const int smem = S * (BM + BN) * BK * 2 + 1024;
+void launch(const CUtensorMap &ma, const CUtensorMap &mb, const Entry *e, const Tile *t, unsigned ntiles,
+            const int *ea, const int *eb, int *err, cudaStream_t s) {
+  const int smem = NST * (S > 0 ? S : 1) * (BM + BN) * PBK * 2 + 1024;
   LR_CUDA(cudaFuncSetAttribute(k_ozgemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k_ozgemm<S><<<grid, 128, smem, s>>>(ma, mb, ka);
+  k_ozgemm<S><<<ntiles, 192, smem, s>>>(ma, mb, e, t, ea, eb, err);
 }
 
 }  // namespace
@@ -395,7 +497,7 @@ void init() {
 
 size_t sliced_bytes(int rows, int K, int S) {
   const size_t kpad = ((size_t)K + 7) / 8 * 8;
-  const size_t dig = ((size_t)S * rows * kpad * 2 + 255) / 256 * 256;
+  const size_t dig = ((size_t)(S > 0 ? S : 1) * rows * kpad * 2 + 255) / 256 * 256;
   return dig + ((size_t)rows * 4 + 255) / 256 * 256;
 }
 
@@ -405,55 +507,99 @@ void sliced_bind(Sliced &o, void *mem, int rows, int K, int S) {
   o.kpad = (K + 7) / 8 * 8;
   o.S = S;
   o.digits = (__nv_bfloat16 *)mem;
-  const size_t dig = ((size_t)S * rows * o.kpad * 2 + 255) / 256 * 256;
+  const size_t dig = ((size_t)(S > 0 ? S : 1) * rows * o.kpad * 2 + 255) / 256 * 256;
   o.expo = (int *)((char *)mem + dig);
 }
 
 void split_real(const double *src, long long ld, bool trans, int rows, int K, int batch, long long batch_stride,
-                Sliced &out, cudaStream_t s) {
+                Sliced &out, cudaStream_t s, int row0) {
   RealSrc r{src, ld, batch_stride, rows, trans};
-  if (out.rows != rows * batch || out.K != K) throw Error{LIBRPA_E_ARG, "split_real: operand shape mismatch"};
-  split_any(r, out, s);
+  split_any(r, rows * batch, K, row0, out, s);
 }
 
 void split_complex(const double2 *src, long long ld, Op op, bool as_a, int n_out, int n_k, int batch,
                    long long batch_stride, Sliced &out, cudaStream_t s) {
   const int rows_pb = as_a ? 2 * n_out : n_out;
   CplxSrc c{src, ld, batch_stride, rows_pb, (int)op, as_a};
-  if (out.rows != rows_pb * batch || out.K != 2 * n_k) throw Error{LIBRPA_E_ARG, "split_complex: operand shape mismatch"};
-  split_any(c, out, s);
+  split_any(c, rows_pb * batch, 2 * n_k, 0, out, s);
 }
 
-long long gemm(const Sliced &a, const Sliced &b, int M, int N, int batch, const Out &out, int km, int kn,
-               int lower_div, int *err, cudaStream_t s) {
-  if (a.S != b.S || a.K != b.K || a.S < 1 || a.S > SMAX) throw Error{LIBRPA_E_ARG, "oz::gemm: operand mismatch"};
+void split_gather(const GatherSrc &src, int rows, int K, Sliced &out, cudaStream_t s) {
+  GatherDev g{src};
+  split_any(g, rows, K, 0, out, s);
+}
+
+void split_ragged(const double *base, const long long *off, const int *Ke, int rows_per_entry, int n_entries,
+                  int Kmax, Sliced &out, cudaStream_t s) {
+  RaggedSrc r{base, off, Ke, rows_per_entry};
+  split_any(r, rows_per_entry * n_entries, Kmax, 0, out, s);
+}
+
+long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry> &entries, int *err,
+                       cudaStream_t s, Handle &h, DevBuf &args) {
+  if (a.S != b.S || a.S < 0 || a.S > SMAX) throw Error{LIBRPA_E_ARG, "oz::gemm: operand mismatch"};
   init();
+  std::vector<Tile> tiles;
+  for (int e = 0; e < (int)entries.size(); ++e) {
+    const Entry &en = entries[e];
+    if (en.M <= 0 || en.N <= 0) continue;
+    if (en.K > a.kpad || en.K > b.kpad || en.a_row0 < 0 || en.b_row0 < 0 || en.a_row0 + en.M > a.rows ||
+        en.b_row0 + en.N > b.rows)
+      throw Error{LIBRPA_E_ARG, "oz::gemm: entry outside its operands"};
+    for (int m0 = 0; m0 < en.M; m0 += BM)
+      for (int n0 = 0; n0 < en.N; n0 += BN) {
+        if (en.lower_div > 0 && n0 > m0 / en.lower_div) continue;
+        tiles.push_back({e, m0, n0});
+      }
+  }
+  if (tiles.empty()) return 0;
+  const size_t b1 = entries.size() * sizeof(Entry), off2 = (b1 + 255) / 256 * 256, b2 = tiles.size() * sizeof(Tile);
+  std::vector<char> host(off2 + b2);
+  std::memcpy(host.data(), entries.data(), b1);
+  std::memcpy(host.data() + off2, tiles.data(), b2);
+  h.ensure(args, off2 + b2);
+  LR_CUDA(cudaMemcpyAsync(args.p, host.data(), off2 + b2, cudaMemcpyHostToDevice, s));
+  const Entry *de = (const Entry *)args.p;
+  const Tile *dt = (const Tile *)((const char *)args.p + off2);
   const CUtensorMap ma = make_map(a, BM), mb = make_map(b, BN);
-  KArgs ka;
-  ka.M = M;
-  ka.N = N;
-  ka.K = a.K;
-  // an operand holding a single entry is shared by every batch entry
-  ka.a_rows_pb = (batch > 1 && a.rows == M) ? 0 : a.rows / batch;
-  ka.b_rows_pb = (batch > 1 && b.rows == N) ? 0 : b.rows / batch;
-  ka.ea = a.expo;
-  ka.eb = b.expo;
-  ka.out = out;
-  ka.km = km;
-  ka.kn = kn;
-  ka.lower_div = lower_div;
-  ka.err = err;
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)batch);
+  const unsigned nt = (unsigned)tiles.size();
   switch (a.S) {
-    case 1: launch<1>(ma, mb, ka, grid, s); break;
-    case 2: launch<2>(ma, mb, ka, grid, s); break;
-    case 3: launch<3>(ma, mb, ka, grid, s); break;
-    case 4: launch<4>(ma, mb, ka, grid, s); break;
-    default: launch<5>(ma, mb, ka, grid, s); break;
+    case 0: launch<0>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
+    case 1: launch<1>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
+    case 2: launch<2>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
+    case 3: launch<3>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
+    case 4: launch<4>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
+    default: launch<5>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
   }
   ++launch_counter();
   LR_CUDA(cudaGetLastError());
-  return (long long)grid.x * grid.y * grid.z;
+  return (long long)tiles.size();
+}
+
+long long gemm(const Sliced &a, const Sliced &b, int M, int N, int batch, const Out &out, int km, int kn,
+               int lower_div, int *err, cudaStream_t s, Handle &h) {
+  if (a.K != b.K) throw Error{LIBRPA_E_ARG, "oz::gemm: K mismatch"};
+  // an operand holding a single entry is shared by every batch entry
+  const int a_pb = (batch > 1 && a.rows == M) ? 0 : a.rows / batch;
+  const int b_pb = (batch > 1 && b.rows == N) ? 0 : b.rows / batch;
+  std::vector<Entry> es(batch);
+  for (int i = 0; i < batch; ++i) {
+    Entry &e = es[i];
+    e.a_row0 = i * a_pb;
+    e.b_row0 = i * b_pb;
+    e.M = M;
+    e.N = N;
+    e.K = a.K;
+    e.km = km;
+    e.kn = kn;
+    e.lower_div = lower_div;
+    e.C = out.C + (long long)i * out.batch_stride * (out.mode == 0 ? 1 : 2);
+    e.ldc = out.ldc;
+    e.mode = out.mode;
+    e.alpha = out.alpha;
+    e.beta = out.beta;
+  }
+  return gemm_grouped(a, b, es, err, s, h, h.oz_args);
 }
 
 }  // namespace oz

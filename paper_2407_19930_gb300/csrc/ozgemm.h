@@ -13,37 +13,61 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <vector>
 
 namespace librpa {
+struct Handle;
+struct DevBuf;
 namespace oz {
 
 constexpr int BM = 128, BN = 64, BK = 64, SMAX = 5;
 
-// A K-major sliced operand: digits [S][rows][kpad] (BF16) and row exponents [rows].
+// K-major sliced operand: digit planes [S][rows][kpad] (BF16) and row exponents [rows].
 struct Sliced {
   __nv_bfloat16 *digits = nullptr;
   int *expo = nullptr;
-  int rows = 0;     // total rows (all batch entries stacked)
-  int K = 0;        // logical K
+  int rows = 0;     // total rows
+  int K = 0;        // logical K (columns beyond K and up to kpad hold zero digits)
   int kpad = 0;     // row pitch in elements (K rounded up to a multiple of 8)
-  int S = 0;
+  int S = 0;        // digit planes; S = 0 means one plane of plain BF16 values (own exponent per
+                    // element, rounded to nearest) multiplied with FP32 accumulation over all K
 };
 size_t sliced_bytes(int rows, int K, int S);   // bytes for digits + exponents (256-byte aligned parts)
 void sliced_bind(Sliced &o, void *mem, int rows, int K, int S);
 
-// Sources of the splits.
-//  real:    X[r][k] = src[r * ld + k]            (trans = false)   or src[k * ld + r] (trans = true)
+// Row r of a split source is produced by `Src::get(r, k)` for k < K; rows [row0, row0 + rows)
+// of the destination are written (digits for k in [K, kpad) are zero).
+enum Op { OP_N = 0, OP_T = 1, OP_H = 2 };
+//  real:    X[r][k] = src[r * ld + k] (trans = false) or src[k * ld + r] (trans = true); entries of
+//           `rows` rows each are `batch_stride` doubles apart.
+void split_real(const double *src, long long ld, bool trans, int rows, int K, int batch, long long batch_stride,
+                Sliced &out, cudaStream_t s, int row0 = 0);
 //  complex: op(Z)[i][k] with op in {N, T, H}; Z row-major interleaved (re, im), leading dim ld.
 //   as_a = true  -> stacked real matrix A'[2i + c][2k + c'] = [[Re, -Im], [Im, Re]] of op(Z)[i][k]
 //   as_a = false -> B'^T[j][2k + c'] = component c' of op(Z)[k][j]
-// batch entries are separated by `batch_stride` elements (doubles or complex numbers).
-enum Op { OP_N = 0, OP_T = 1, OP_H = 2 };
-void split_real(const double *src, long long ld, bool trans, int rows, int K, int batch, long long batch_stride,
-                Sliced &out, cudaStream_t s);
 void split_complex(const double2 *src, long long ld, Op op, bool as_a, int n_out, int n_k, int batch,
                    long long batch_stride, Sliced &out, cudaStream_t s);
+//  gathered Green's-function blocks of the chi0 contraction (see k_chi0.cu for the tables):
+//   kind 0 (Bg): row (p, g, V, kappa), k = lambda of V:  G^g(tau_p)[bvk(R1_kappa - R_p - R2'_lambda)][ao_lambda][ao_kappa]
+//   kind 1 (Ag): row (p, g, V, i),     k = lambda of V:  G^g(tau_p)[bvk(R_p + R2'_lambda)][i][ao_lambda]
+struct GatherSrc {
+  int kind;
+  const double *G;
+  long long g_gstride;
+  int nR, nao, n1, n2, n3, natoms, rows_per_entry;
+  const int *pts;        // per point: {iR, itau, R0, R1, R2}
+  const int *uni;        // union column table (6 ints per column)
+  const int *lam;        // per-atom column tables (6 ints per column)
+  const long long *lam_off;
+  const int *m;          // m_V
+};
+void split_gather(const GatherSrc &src, int rows, int K, Sliced &out, cudaStream_t s);
+//  ragged entries: row r belongs to entry e = r / rows_per_entry; its K_e columns are
+//  base[off[e] + (r % rows_per_entry) * K_e + k] (zero for k >= K_e); off, K on the device.
+void split_ragged(const double *base, const long long *off, const int *Ke, int rows_per_entry, int n_entries,
+                  int Kmax, Sliced &out, cudaStream_t s);
 
-// Output of a GEMM.
+// Output of a GEMM entry.
 //  mode 0: real C[m][n] (ldc);
 //  mode 1: complex C[i][j] (interleaved) from rows m = 2i + c: component c of C[i][j];
 //  mode 2: complex transposed: component c of C[j][i].
@@ -55,14 +79,28 @@ struct Out {
   double alpha = 1.0, beta = 0.0;
 };
 
-// C = alpha * A B^T + beta * C for `batch` entries: A rows m in [0, M) of entry b are rows
-// b * M .. of `a`, B rows likewise with N; an operand with exactly M (N) rows is shared by all
-// entries.  K range per output tile starts at
-// (m0 * km + n0 * kn) rounded down to BK (for triangular operands); lower_div > 0 skips tiles
-// with n0 > m0 / lower_div.  `err` (device int) is set to 1 if a bounded wait runs out.
-// Returns the number of tiles launched.
+// One GEMM of a grouped launch: C = alpha A[a_row0 .. + M) B[b_row0 .. + N)^T + beta C over
+// K columns.  K range per output tile starts at (m0 * km + n0 * kn) rounded down to BK
+// (triangular operands); lower_div > 0 skips tiles with n0 > m0 / lower_div.
+struct Entry {
+  int a_row0, b_row0, M, N, K;
+  int km, kn, lower_div;
+  double *C;
+  long long ldc;
+  int mode;
+  double alpha, beta;
+};
+
+// Grouped launch over all tiles of all entries; operand digit planes of the A role in `a`, of
+// the B role in `b` (same S).  `err` (device int) is set to 1 if a bounded wait runs out.
+// `args` is scratch for the descriptor upload.  Returns the number of tiles.
+long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry> &entries, int *err,
+                       cudaStream_t s, Handle &h, DevBuf &args);
+
+// Uniform batch: A rows m in [0, M) of entry b are rows b * M .. of `a`, B rows likewise with N;
+// an operand with exactly M (N) rows is shared by all entries.
 long long gemm(const Sliced &a, const Sliced &b, int M, int N, int batch, const Out &out, int km, int kn,
-               int lower_div, int *err, cudaStream_t s);
+               int lower_div, int *err, cudaStream_t s, Handle &h);
 
 // One-time host setup (driver entry point for tensor-map encoding).  Throws on failure.
 void init();
