@@ -157,9 +157,7 @@ __global__ void k_gather_ag(const double *__restrict__ G, size_t g_gstride, cons
 }
 
 // ---------------------------------------------------------------------------------------
-// O assembly.  One CTA per (point, U, V, 64-column chunk of U's packed columns); 256
-// threads = 64 columns x 4 row groups.  Shared memory: Lm[n_U][2 n_V] = [A_UV(R) | B_UV(R)],
-// LX[n_U][2 n_V] = [X^A_nu | X^B_nu] rows of U, RG[2 n_V][64] = [B_{V,kap}(R1-R); A_{V,kap}(R1-R)].
+// O assembly: O^nu_{ik}(K R1) for every (point, U, V), written as O_U[nu][(i, kap)].
 struct OArgs {
   const double *G;       // [2][ntau][nR][nao][nao]
   size_t g_gstride;
@@ -180,10 +178,54 @@ struct OArgs {
   long long o_sz_p;
 };
 
-// T = double for the FP64-accurate modes; T = float when the contraction GEMMs themselves keep
-// at most ~23 bits (mixed modes), where the FP32 pipe (~72 TFLOP/s) carries the same accuracy.
-template <class T>
-__global__ void __launch_bounds__(256) k_oassemble(OArgs a) {
+// Arithmetic of the O assembly.  ArD: FP64 (FP64 modes).  ArF: FP32, for the mixed modes whose
+// contraction GEMMs keep at most ~23 bits.  ArDF: unevaluated sums of two FP32 numbers (about 48
+// significant bits; the product of the high parts split exactly with an FMA, sums by Knuth's
+// two-sum) for the FP64-accurate tensor-core mode: it runs on the FP32 pipe, whose rate on GB300
+// is ~70x that of the FP64 pipe.
+struct ArD {
+  using T = double;
+  __device__ static T from(double x) { return x; }
+  __device__ static double to(T x) { return x; }
+  __device__ static T zero() { return 0.0; }
+  __device__ static T mad(T a, T b, T c) { return fma(a, b, c); }
+};
+struct ArF {
+  using T = float;
+  __device__ static T from(double x) { return (float)x; }
+  __device__ static double to(T x) { return (double)x; }
+  __device__ static T zero() { return 0.f; }
+  __device__ static T mad(T a, T b, T c) { return fmaf(a, b, c); }
+};
+struct ArDF {
+  using T = float2;   // value x + y with |y| <= ulp(x) / 2
+  __device__ static T from(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+  }
+  __device__ static double to(T v) { return (double)v.x + (double)v.y; }
+  __device__ static T zero() { return make_float2(0.f, 0.f); }
+  __device__ static T mad(T a, T b, T c) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);   // a.x b.x = p + e exactly
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float s = c.x + p;        // s + t = c.x + p exactly
+    const float bv = s - c.x;
+    const float t = (c.x - (s - bv)) + (p - bv);
+    const float lo = t + e + c.y;
+    const float hi = s + lo;
+    return make_float2(hi, lo - (hi - s));
+  }
+};
+
+// One CTA per (point, U, V, 64-column chunk of U's packed columns); 64 x NL threads = 64 columns
+// x NL lanes over nu; every thread computes all rows i of U for its (nu, column).  Shared
+// memory (type T): Lm[n_U][2 n_V] = [A_UV(R) | B_UV(R)], RG[2 n_V][64] = [B_{V,kap}(R1-R);
+// A_{V,kap}(R1-R)], LX[NL][n_U][2 n_V] = [X^A_nu | X^B_nu] (rows of U) for the NL nu of a step.
+template <class Ar>
+__global__ void __launch_bounds__(256) k_oassemble(OArgs a, int NL) {
+  using T = typename Ar::T;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sm = reinterpret_cast<T *>(smraw);
   const int V = blockIdx.y % a.natoms;
@@ -193,34 +235,31 @@ __global__ void __launch_bounds__(256) k_oassemble(OArgs a) {
   const int c0 = blockIdx.x * 64;
   if (c0 >= mU) return;
   const int nU = a.n_ao[U], nV = a.n_ao[V], two = 2 * nV;
-  T *Lm = sm;                 // [nU][two]
-  T *LX = Lm + nU * two;      // [nU][two]
-  T *RG = LX + nU * two;      // [two][64]
+  T *Lm = sm;                  // [nU][two]
+  T *RG = Lm + nU * two;       // [two][64]
+  T *LX = RG + two * 64;       // [NL][nU][two]
   const Point pt = a.pts[p];
-  const int tid = threadIdx.x, col = tid & 63, rg = tid >> 6;
+  const int tid = threadIdx.x, col = tid & 63, nl = tid >> 6, nthr = 64 * NL;
   const size_t n2 = (size_t)a.nao * a.nao;
   const double *GB = a.G + ((size_t)pt.itau * a.nR_stride) * n2;                 // G^occ(tau)
   const double *GA = a.G + a.g_gstride + ((size_t)pt.itau * a.nR_stride) * n2;   // G^vir(tau)
   const int aoU = a.ao_off[U], aoV = a.ao_off[V];
-  // Lm: [A_UV(R) | B_UV(R)]
-  for (int e = tid; e < nU * two; e += 256) {
+  for (int e = tid; e < nU * two; e += nthr) {
     const int i = e / two, t = e % two;
     const double *Gs = t < nV ? GA : GB;
-    Lm[e] = Gs[((size_t)pt.iR) * n2 + (size_t)(aoU + i) * a.nao + aoV + (t % nV)];
+    Lm[e] = Ar::from(Gs[((size_t)pt.iR) * n2 + (size_t)(aoU + i) * a.nao + aoV + (t % nV)]);
   }
-  // RG for this thread's column
   const int kc = c0 + col;
   const bool live = kc < mU;
-  int ucol = 0;
-  if (live) {
-    const int *kp = a.kap + 6 * (a.kap_off[U] + kc);
+  const int *kp = a.kap + 6 * (a.kap_off[U] + (live ? kc : 0));
+  const int ucol = kp[5];
+  {
     auto fold = [](int x, int nn) { int r = x % nn; return r < 0 ? r + nn : r; };
     const int iR = (fold(kp[1] - pt.R[0], a.n1) * a.n2 + fold(kp[2] - pt.R[1], a.n2)) * a.n3 +
                    fold(kp[3] - pt.R[2], a.n3);
-    ucol = kp[5];
-    for (int t = rg; t < two; t += 4) {
+    for (int t = nl; t < two; t += NL) {
       const double *Gs = t < nV ? GB : GA;
-      RG[t * 64 + col] = Gs[(size_t)iR * n2 + (size_t)(aoV + (t % nV)) * a.nao + kp[4]];
+      RG[t * 64 + col] = live ? Ar::from(Gs[(size_t)iR * n2 + (size_t)(aoV + (t % nV)) * a.nao + kp[4]]) : Ar::zero();
     }
   }
   const int nauxV = a.n_aux[V];
@@ -231,33 +270,35 @@ __global__ void __launch_bounds__(256) k_oassemble(OArgs a) {
   const int ldx = nauxV * nV;
   double *Ob = a.O + p * a.o_sz_p + a.o_off[U];
   const int ldo = nU * mU;
-  for (int nu = 0; nu < nauxV; ++nu) {
+  for (int nu0 = 0; nu0 < nauxV; nu0 += NL) {
     __syncthreads();   // previous LX consumed; Lm and RG written
-    for (int e = tid; e < nU * two; e += 256) {
-      const int i = e / two, t = e % two;
-      const double *Xs = t < nV ? XA : XB;
-      LX[e] = Xs[(size_t)(aoU + i) * ldx + nu * nV + (t % nV)];
+    for (int e = tid; e < NL * nU * two; e += nthr) {
+      const int q = e / (nU * two), r = e % (nU * two), i = r / two, t = r % two;
+      const int nu = nu0 + q;
+      LX[e] = nu < nauxV ? Ar::from((t < nV ? XA : XB)[(size_t)(aoU + i) * ldx + nu * nV + (t % nV)]) : Ar::zero();
     }
     __syncthreads();
-    if (!live) continue;
-    T acc[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r) acc[r] = T(0);
-    for (int t = 0; t < two; ++t) {
-      const double *Ns = t < nV ? NB : NA;
-      const T rn = (T)Ns[(size_t)(nu * nV + (t % nV)) * a.m_all + ucol];
-      const T rgv = RG[t * 64 + col];
-#pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        const int i = rg + 4 * r;
-        if (i < nU) acc[r] = fma(Lm[i * two + t], rn, fma(LX[i * two + t], rgv, acc[r]));
-      }
-    }
+    const int nu = nu0 + nl;
+    if (!live || nu >= nauxV) continue;
+    const T *lx = LX + nl * nU * two;
     double *orow = Ob + (size_t)(a.aux_off[V] + nu) * ldo;
+    for (int i0 = 0; i0 < nU; i0 += 16) {
+      T acc[16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int i = rg + 4 * r;
-      if (i < nU) orow[(size_t)i * mU + kc] = acc[r];
+      for (int r = 0; r < 16; ++r) acc[r] = Ar::zero();
+#pragma unroll 2
+      for (int t = 0; t < two; ++t) {
+        const T rn = Ar::from((t < nV ? NB : NA)[(size_t)(nu * nV + (t % nV)) * a.m_all + ucol]);
+        const T rgv = RG[t * 64 + col];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int i = i0 + r;
+          if (i < nU) acc[r] = Ar::mad(Lm[i * two + t], rn, Ar::mad(lx[i * two + t], rgv, acc[r]));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        if (i0 + r < nU) orow[(size_t)(i0 + r) * mU + kc] = Ar::to(acc[r]);
     }
   }
 }
@@ -465,10 +506,17 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
     maxn = std::max(maxn, h.n_ao[a]);
     max_chunks = std::max(max_chunks, (P.m[a] + 63) / 64);
   }
-  const bool fp32 = h.chi0_S >= 0 && h.chi0_S <= 3;
-  const size_t osmem = (size_t)(2 * maxn * 2 * maxn + 2 * maxn * 64) * (fp32 ? sizeof(float) : sizeof(double));
-  LR_CUDA(cudaFuncSetAttribute(k_oassemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
-  LR_CUDA(cudaFuncSetAttribute(k_oassemble<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
+  // arithmetic: FP64 pipes for the FP64 mode, FP32 for the mixed modes, FP32 pairs (~48 bits)
+  // for the FP64-accurate tensor-core mode
+  const int ar = h.chi0_S < 0 ? 0 : h.chi0_S <= 3 ? 1 : 2;
+  const size_t esz = ar == 1 ? sizeof(float) : 8;
+  int NL = 4;
+  auto smem_for = [&](int nl) { return (size_t)(maxn * 2 * maxn + 2 * maxn * 64 + nl * maxn * 2 * maxn) * esz; };
+  while (NL > 1 && smem_for(NL) > 200 * 1024) NL /= 2;
+  const size_t osmem = smem_for(NL);
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
   OArgs oa;
   oa.G = (const double *)h.d_g.p;
   oa.g_gstride = (size_t)h.ntau * h.mesh.size() * h.nao * h.nao;
@@ -500,10 +548,12 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
   oa.o_off = (const long long *)P.t_o_off.p;
   oa.o_sz_p = P.o_sz;
   dim3 og((unsigned)max_chunks, (unsigned)(np * nat * nat));
-  if (fp32)
-    k_oassemble<float><<<og, 256, osmem, h.stream>>>(oa);
+  if (ar == 0)
+    k_oassemble<ArD><<<og, 64 * NL, osmem, h.stream>>>(oa, NL);
+  else if (ar == 1)
+    k_oassemble<ArF><<<og, 64 * NL, osmem, h.stream>>>(oa, NL);
   else
-    k_oassemble<double><<<og, 256, osmem, h.stream>>>(oa);
+    k_oassemble<ArDF><<<og, 64 * NL, osmem, h.stream>>>(oa, NL);
   ++launch_counter();
   LR_CUDA(cudaGetLastError());
 }
