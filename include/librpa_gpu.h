@@ -209,6 +209,37 @@ int librpa_gpu_chi0(librpa_gpu_t h, double *out_re, double *out_im);
  * Errors: E_STATE, E_NOT_PD, E_NOMEM, E_CUDA. */
 int librpa_gpu_ec(librpa_gpu_t h, double *ec, double *ec_q, double *ec_w);
 
+/* No-allocation variant of the ln det stage, for callers that cannot call cudaMalloc:
+ * host codes that give all of the GPU's memory to their own pool at start-up (a further
+ * cudaMalloc fails or fragments that pool), and callers whose loop must not stall other
+ * streams (cudaMalloc and cudaFree may synchronise the device).  The paper has no
+ * counterpart; it computes the same integrand as librpa_gpu_ec, without a handle.
+ *
+ *   out[k] = ln det(1 - chi_k V) + Re Tr(chi_k V),  k = 0 .. nomega-1,
+ * via V = L L^H and the Cholesky factorisation of I - L^H chi_k L, in FP64.
+ *   naux    matrix order, 1 .. LIBRPA_NOALLOC_MAX_NAUX (larger: E_ARG, nothing launched);
+ *   V       device, [naux][naux] complex interleaved (re, im), row-major, Hermitian positive
+ *           definite (lower triangle read), 16-byte aligned;
+ *   chi     device, [nomega][naux][naux] complex interleaved, 16-byte aligned;
+ *   out     device, [nomega] doubles; NaN where V or I - L^H chi_k L is not positive definite;
+ *   stream  cudaStream_t (NULL: the legacy default stream) of the current device, which
+ *           must hold V, chi and out;
+ *   msg     optional buffer of msg_len bytes for a one-line error description.
+ * The caller owns every buffer; nothing is allocated, the library calls no cudaMalloc,
+ * cudaFree or allocating routine.  The work is enqueued on `stream` and the call returns
+ * without waiting: out is valid once the stream is synchronised.  Scratch is one static
+ * device array of LIBRPA_NOALLOC_SCRATCH_BYTES, held on every GPU that loads the library
+ * until the process exits, shared by all calls and keeping the last call's contents
+ * (each call writes every scratch value before reading it): calls that overlap on the
+ * GPU race, so order them on one stream or with events.  The first call made with a
+ * given device current looks up the array's device address (set-up, once per device);
+ * make that first call before any stream capture.
+ * Errors: E_ARG (sizes, NULL or misaligned pointers; nomega = 0 is a no-op), E_CUDA. */
+#define LIBRPA_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+#define LIBRPA_NOALLOC_MAX_NAUX 591
+int librpa_gpu_ec_noalloc(int naux, int nomega, const double *V, const double *chi, double *out,
+                          void *stream, char *msg, size_t msg_len);
+
 /* Inspection of intermediates kept on the device (host copies of one slice):
  *   get_green:      go, gv  [n_ao_total][n_ao_total] at (itau, iR);
  *   get_chi0_tau:   out     [N_aux][N_aux] = chi0(R, tau) at (itau, iR);

@@ -30,6 +30,8 @@ LIBRPA_FP64 = 0
 LIBRPA_FP64_TC = 1
 LIBRPA_SPLIT = 2
 LIBRPA_BF16 = 3
+LIBRPA_NOALLOC_SCRATCH_BYTES = 16 << 20
+LIBRPA_NOALLOC_MAX_NAUX = 591
 
 _CODES = {v: k for k, v in globals().items() if k.startswith("LIBRPA_E_")}
 
@@ -84,6 +86,8 @@ _SIGS = {
     "librpa_gpu_get_chi0_freq": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _D, _D]),
     "librpa_gpu_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(librpa_gpu_stats)]),
     "librpa_gpu_last_error": (ctypes.c_char_p, [_H]),
+    "librpa_gpu_ec_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "librpa_gpu_destroy": (None, [_H]),
 }
 
@@ -283,6 +287,16 @@ def librpa_gpu_get_stats(h):
 
 def librpa_gpu_last_error(h):
     return (load().librpa_gpu_last_error(h) or b"").decode()
+
+
+def librpa_gpu_ec_noalloc(naux, nomega, V, chi, out, stream=None):
+    """ln det(1 - chi_k V) + Re Tr(chi_k V) for k < nomega into ``out`` (device pointers as
+    ints: V [naux][naux] and chi [nomega][naux][naux] complex interleaved, out [nomega] doubles),
+    enqueued on ``stream`` (a cudaStream_t as int, or None); nothing is allocated."""
+    msg = ctypes.create_string_buffer(256)
+    rc = load().librpa_gpu_ec_noalloc(int(naux), int(nomega), V, chi, out, stream, msg, len(msg))
+    if rc != LIBRPA_OK:
+        raise LibrpaError(rc, msg.value.decode())
 
 
 def librpa_gpu_destroy(h):
