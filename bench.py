@@ -44,7 +44,8 @@ NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
 # precision presets of the library (include/librpa_gpu.h): name -> (LIBRPA_* value, dtype label)
 PRECISIONS = {"fp64": (0, "f64"), "fp64_tc": (1, "f64-accurate: bf16 digit planes (5) on tcgen05"),
               "split": (2, "mixed: chi0 GEMMs on 3 bf16 digit planes, ln det on 5"),
-              "bf16": (3, "mixed: chi0 GEMMs on 1 bf16 digit plane, ln det on 5")}
+              "bf16": (3, "mixed: chi0 GEMMs in plain bf16 (fp32 accumulation), ln det on 5 digit planes")}
+MEV_PER_HA = 27211.386245988
 
 # DRAM traffic per launch of the dominant kernels from one ncu capture (see profiles/),
 # valid only while the kernel source is unchanged (sha256 of the file at capture time).
@@ -282,6 +283,11 @@ def run_gpu(args):
         e2e = args.e2e_steps * ws / te
     finally:
         L.librpa_gpu_destroy(h)
+    # ---------------- the other precision modes on the same workload (1 GPU only)
+    modes = {}
+    if ws == 1:
+        for m in [x for x in args.modes.split(",") if x and x != args.precision]:
+            modes[m] = time_mode(L, inp, stream, local, args.ntau, m, ec, torch)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -324,6 +330,10 @@ def run_gpu(args):
                      "launches": nl, "flop": fl},
         "clocks": clk,
     }
+    if args.precision != "fp64":
+        line["roofline"] = tc_roofline(s, peaks, src)
+    if modes:
+        line["modes"] = modes
     if ws == 1 and not args.no_cpu:
         from oracle import build as obuild, grid as ogrid
         obuild.build()
@@ -335,6 +345,56 @@ def run_gpu(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def tc_roofline(s, peaks, src):
+    """Roofline of the dominant digit-plane GEMM (chi0 or ln det) against the BF16 tensor peak:
+    achieved = MMA flops issued / device time of those launches (both from the library's stats)."""
+    legs = {"k_ozgemm (chi0 GEMMs)": (s["ms_gemm_chi0"], s["flop_exec_gemm_chi0"], s["n_gemm_chi0"]),
+            "k_ozgemm (ln det GEMMs)": (s["ms_gemm_ec"], s["flop_exec_gemm_ec"], s["n_gemm_ec"])}
+    name = max(legs, key=lambda k: legs[k][0])
+    ms, fl, nl = legs[name]
+    if ms <= 0 or fl <= 0:
+        return None
+    peak = peaks["bf16_tflops"]
+    achieved = fl / (ms * 1e-3) / 1e12
+    return {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_note": "BF16 dense burst, %s; sustained %.1f; achieved counts the BF16 MMA flops issued "
+                         "(all digit-plane products, tile padding included)" % (src, peaks.get("bf16_tflops_sustained", peak)),
+            "launches": nl, "flop": fl}
+
+
+def time_mode(L, inp, stream, device, ntau, mode, ec_ref, torch):
+    """One warm-up and one timed step of `mode` on its own handle; E_c against the headline's."""
+    o = L.librpa_gpu_default_opts()
+    o.device = device
+    o.n_tau = ntau
+    o.precision = PRECISIONS[mode][0]
+    h = L.librpa_gpu_create(o, torch_stream=stream, torch_alloc=True)
+    try:
+        L.set_inputs(h, inp)
+        L.librpa_gpu_chi0(h)
+        L.librpa_gpu_ec(h)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.librpa_gpu_chi0(h)
+        ec, _, _ = L.librpa_gpu_ec(h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s = L.librpa_gpu_get_stats(h)
+    finally:
+        L.librpa_gpu_destroy(h)
+    ms = e0.elapsed_time(e1)
+    dmev = abs(ec - ec_ref) * MEV_PER_HA / inp.st.natoms
+    peaks, src = _peaks()
+    return {"dtype": PRECISIONS[mode][1], "ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT,
+            "chi0_tflops_fp64_equiv": s["flop_chi0"] / (s["ms_chi0"] * 1e-3) / 1e12,
+            "stage_ms": {"green": s["ms_green"], "chi0": s["ms_chi0"], "freq": s["ms_freq"], "ec": s["ms_ec"]},
+            "ec_ha": ec, "ec_diff_vs_fp64_mev_per_atom": dmev, "within_0.1_mev_per_atom": dmev <= 0.1,
+            "roofline": tc_roofline(s, peaks, src), "steps": 1, "warmup": 1}
 
 
 def main():
@@ -349,6 +409,8 @@ def main():
     ap.add_argument("--ntau", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64")
+    ap.add_argument("--modes", default="fp64_tc,split",
+                    help="other precision modes timed after the headline (1 GPU; '' for none)")
     args = ap.parse_args()
     args.kmesh = tuple(int(x) for x in args.kmesh.split(","))
     if args.impl == "reference":

@@ -108,6 +108,9 @@ typedef struct {
   long long n_gemm_ec;     /* number of those launches */
   long long launches;      /* kernels launched by the call */
   size_t bytes_device;     /* device bytes held by the handle */
+  double flop_exec_gemm_chi0; /* tensor-core MMA flops issued by the timed chi0 GEMMs (digit-plane
+                                 products, tile padding and all); 0 in the FP64 mode */
+  double flop_exec_gemm_ec;   /* the same for the timed ln det GEMMs */
 } librpa_gpu_stats;
 
 /* Fill *o with defaults: device 0, own stream, cudaMalloc, n_tau = 16, FP64,

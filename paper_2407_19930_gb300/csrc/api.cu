@@ -74,10 +74,12 @@ void Handle::resolve_timers() {
       if (t.kind == 0) {
         stats.ms_gemm_chi0 += ms;
         stats.flop_gemm_chi0 += t.flops;
+        stats.flop_exec_gemm_chi0 += t.exec_flops;
         stats.n_gemm_chi0 += 1;
       } else {
         stats.ms_gemm_ec += ms;
         stats.flop_gemm_ec += t.flops;
+        stats.flop_exec_gemm_ec += t.exec_flops;
         stats.n_gemm_ec += 1;
       }
     }

@@ -132,6 +132,7 @@ struct Handle {
   DevBuf gemm_args;
   DevBuf oz_args;     // descriptors of the tensor-core GEMM launches
   DevBuf work;        // per-call workspace
+  double oz_exec_flops = 0;  // MMA flops issued by the last digit-plane GEMM launch
   bool chi0_done = false, lri_dirty = true;
   Chi0Plan plan;
 
@@ -141,7 +142,8 @@ struct Handle {
   struct Timed {
     cudaEvent_t a, b;
     double flops;
-    int kind;  // 0 = FP64 DMMA GEMM of the chi0 contraction, 1 = complex GEMM of the energy stage
+    int kind;  // 0 = GEMM of the chi0 contraction, 1 = GEMM of the energy stage
+    double exec_flops = 0;  // tensor-core MMA flops issued (digit-plane GEMMs only)
   };
   std::vector<Timed> timed;
   void resolve_timers();

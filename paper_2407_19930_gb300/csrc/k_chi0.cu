@@ -581,6 +581,7 @@ void timed_grouped(Handle &h, const oz::Sliced &a, const oz::Sliced &b, const st
   LR_CUDA(cudaEventRecord(t.a, h.stream));
   oz::gemm_grouped(a, b, es, err, h.stream, h, args);
   LR_CUDA(cudaEventRecord(t.b, h.stream));
+  t.exec_flops = h.oz_exec_flops;
   h.timed.push_back(t);
 }
 

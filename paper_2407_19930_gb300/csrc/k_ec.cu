@@ -345,6 +345,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
       LR_CUDA(cudaEventRecord(t1.a, s));
       oz::gemm(sx, sl, 2 * n, n, nw, o1, 0, 2, 0, err, s, h);
       LR_CUDA(cudaEventRecord(t1.b, s));
+      t1.exec_flops = h.oz_exec_flops;
       h.timed.push_back(t1);
       oz::split_complex(Wm, n, oz::OP_T, false, n, n, nw, (long long)n2, sw, s);   // B'^T rows j: W[k][j]
       oz::Out o2;
@@ -359,6 +360,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
       LR_CUDA(cudaEventRecord(t2.a, s));
       oz::gemm(slh, sw, 2 * n, n, nw, o2, 1, 0, 2, err, s, h);
       LR_CUDA(cudaEventRecord(t2.b, s));
+      t2.exec_flops = h.oz_exec_flops;
       h.timed.push_back(t2);
     } else {
       // W = chi0(q, omega) L_q  (L lower triangular: k >= j)

@@ -540,6 +540,10 @@ long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry
   if (a.S != b.S || a.S < 0 || a.S > SMAX) throw Error{LIBRPA_E_ARG, "oz::gemm: operand mismatch"};
   init();
   std::vector<Tile> tiles;
+  // MMA flops issued: per tile BM x BN x (K rounded up to the K step) per digit-plane product
+  const double prods = a.S == 0 ? 1.0 : a.S * (a.S + 1) / 2.0;
+  double exec = 0;
+  h.oz_exec_flops = 0;
   for (int e = 0; e < (int)entries.size(); ++e) {
     const Entry &en = entries[e];
     if (en.M <= 0 || en.N <= 0) continue;
@@ -550,6 +554,8 @@ long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry
       for (int n0 = 0; n0 < en.N; n0 += BN) {
         if (en.lower_div > 0 && n0 > m0 / en.lower_div) continue;
         tiles.push_back({e, m0, n0});
+        const int kbeg = (m0 * en.km + n0 * en.kn) / PBK * PBK;   // as in the kernel
+        if (en.K > kbeg) exec += 2.0 * BM * BN * (double)((en.K - kbeg + PBK - 1) / PBK * PBK) * prods;
       }
   }
   if (tiles.empty()) return 0;
@@ -573,6 +579,7 @@ long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry
   }
   ++launch_counter();
   LR_CUDA(cudaGetLastError());
+  h.oz_exec_flops = exec;
   return (long long)tiles.size();
 }
 

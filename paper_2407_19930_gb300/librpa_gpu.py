@@ -53,7 +53,8 @@ class librpa_gpu_stats(ctypes.Structure):
                 ("n_gemm_chi0", ctypes.c_longlong), ("ms_gemm_ec", ctypes.c_double),
                 ("flop_gemm_ec", ctypes.c_double), ("n_gemm_ec", ctypes.c_longlong),
                 ("launches", ctypes.c_longlong),
-                ("bytes_device", ctypes.c_size_t)]
+                ("bytes_device", ctypes.c_size_t), ("flop_exec_gemm_chi0", ctypes.c_double),
+                ("flop_exec_gemm_ec", ctypes.c_double)]
 
 
 class LibrpaError(RuntimeError):
