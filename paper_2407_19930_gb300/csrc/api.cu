@@ -303,6 +303,7 @@ int librpa_gpu_set_coulomb(librpa_gpu_t h, int iq, const double *V_re, const dou
                             h->stream));
     LR_CUDA(cudaStreamSynchronize(h->stream));
     h->have_q[iq] = 1;
+    h->vq_sym = -1;
     return LIBRPA_OK;
   });
 }
@@ -409,7 +410,7 @@ int librpa_gpu_chi0(librpa_gpu_t h, double *out_re, double *out_im) {
     h->stats.ms_freq = t;
     for (auto &e : ev) cudaEventDestroy(e);
     h->resolve_timers();
-    h->stats.flop_chi0 = h->plan.flop_per_point * h->ntau * h->mesh.size();
+    h->stats.flop_chi0 = h->plan.flop_per_point * h->ntau * (double)chi0_r_list(h->mesh).size();
     h->stats.launches = launch_counter() - l0;
     h->stats.bytes_device = h->bytes_held;
     if (h->opts.check_level >= 1 && !(imag <= 1e-10))

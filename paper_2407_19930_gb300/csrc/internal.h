@@ -34,6 +34,7 @@ struct Mesh {
   static int fold(int x, int n) { int r = x % n; return r < 0 ? r + n : r; }
   int index(int a, int b, int c) const { return (fold(a, n1) * n2 + fold(b, n2)) * n3 + fold(c, n3); }
   void split(int i, int &a, int &b, int &c) const { a = i / (n2 * n3); b = (i / n3) % n2; c = i % n3; }
+  int neg(int i) const { int a, b, c; split(i, a, b, c); return index(-a, -b, -c); }   // index of -R (or -q)
 };
 
 // ----------------------------------------------------------------- device buffers
@@ -114,6 +115,7 @@ struct Handle {
   std::vector<char> have_k;
   std::vector<double> efermi_k;
   std::vector<char> have_q;
+  int vq_sym = -1;   // V(-q) = conj V(q) for every q: -1 not checked yet, 0 no, 1 yes
 
   // grid
   bool have_grid = false, grid_user = false;
@@ -164,6 +166,9 @@ double green_build(Handle &h);
 // K2 (k_chi0.cu)
 void chi0_plan(Handle &h);
 void chi0_run(Handle &h, double *ms_gemm);
+// lattice vectors R whose chi0(R, tau) is computed (R <= -R in the flat BvK order); the others
+// are filled as chi0(-R, tau)^T
+std::vector<int> chi0_r_list(const Mesh &m);
 // K3 + K4 (k_freq.cu)
 void freq_transform(Handle &h);
 // K5 + K6 (k_ec.cu); returns LIBRPA_OK or LIBRPA_E_NOT_PD

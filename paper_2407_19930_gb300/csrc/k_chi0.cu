@@ -559,13 +559,47 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
 }
 
 // Points of the (R, tau) grid in flat order: point idx = itau * nR + iR.
-std::vector<Point> make_points(Handle &h, long long p0, int np) {
-  const int nR = h.mesh.size();
+// chi0(-R, tau) = chi0(R, tau)^T for the lattice vectors left out of the point list (the pair
+// symmetry of Sec. 2: chi0_{VU}(-R) = chi0_{UV}(R)^T, from G^occ and G^vir being real and
+// symmetric in (r, r')).  One 32 x 32 tile per CTA, staged through shared memory.
+__global__ void k_fill_partner(double *chi, int naux, int n1, int n2, int n3) {
+  __shared__ double t[32][33];
+  const int nR = n1 * n2 * n3;
+  const int iR = blockIdx.z % nR, itau = blockIdx.z / nR;
+  const int a = iR / (n2 * n3), b = (iR / n3) % n2, c = iR % n3;
+  const int pR = (((n1 - a) % n1) * n2 + (n2 - b) % n2) * n3 + (n3 - c) % n3;
+  if (iR <= pR) return;   // computed directly
+  const double *src = chi + ((size_t)itau * nR + pR) * naux * naux;
+  double *dst = chi + ((size_t)itau * nR + iR) * naux * naux;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int gr = r0 + r, gc = c0 + threadIdx.x;
+    if (gr < naux && gc < naux) t[r][threadIdx.x] = src[(size_t)gr * naux + gc];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int gr = c0 + r, gc = r0 + threadIdx.x;   // dst[gr][gc] = src[gc][gr]
+    if (gr < naux && gc < naux) dst[(size_t)gr * naux + gc] = t[threadIdx.x][r];
+  }
+}
+
+void fill_partners(Handle &h) {
+  const int nR = h.mesh.size(), naux = h.naux;
+  if ((int)chi0_r_list(h.mesh).size() == nR) return;
+  const unsigned nt = (unsigned)((naux + 31) / 32);
+  dim3 g(nt, nt, (unsigned)(h.ntau * nR));
+  k_fill_partner<<<g, dim3(32, 8), 0, h.stream>>>((double *)h.d_chi_tau.p, naux, h.mesh.n1, h.mesh.n2, h.mesh.n3);
+  ++launch_counter();
+  LR_CUDA(cudaGetLastError());
+}
+
+std::vector<Point> make_points(Handle &h, const std::vector<int> &rl, long long p0, int np) {
+  const int nr = (int)rl.size();
   std::vector<Point> pts(np);
   for (int q = 0; q < np; ++q) {
     const long long idx = p0 + q;
-    pts[q].itau = (int)(idx / nR);
-    pts[q].iR = (int)(idx % nR);
+    pts[q].itau = (int)(idx / nr);
+    pts[q].iR = rl[idx % nr];
     h.mesh.split(pts[q].iR, pts[q].R[0], pts[q].R[1], pts[q].R[2]);
   }
   return pts;
@@ -596,7 +630,8 @@ void chi0_run_tc(Handle &h) {
   const size_t fp = 8 * (size_t)(2 * P.n_sz + 2 * P.x_sz + P.o_sz);
   const size_t per_point = fp + oz::sliced_bytes(rows_bg, P.max_m, S) + oz::sliced_bytes(rows_ag, P.max_m, S) +
                            oz::sliced_bytes(rows_o, P.max_nm, S) + 4096;
-  const long long total_pts = (long long)ntau * nR;
+  const std::vector<int> rl = chi0_r_list(h.mesh);
+  const long long total_pts = (long long)ntau * rl.size();
   long long npb = std::max<long long>(1, (2LL << 30) / (long long)per_point);
   npb = std::min(npb, total_pts);
   const size_t b_n = 8 * (size_t)npb * 2 * P.n_sz, b_x = 8 * (size_t)npb * 2 * P.x_sz, b_o = 8 * (size_t)npb * P.o_sz;
@@ -620,7 +655,7 @@ void chi0_run_tc(Handle &h) {
   const size_t g_gstride = (size_t)ntau * nR * nao * nao;
   for (long long p0 = 0; p0 < total_pts; p0 += npb) {
     const int np = (int)std::min(npb, total_pts - p0);
-    std::vector<Point> pts = make_points(h, p0, np);
+    std::vector<Point> pts = make_points(h, rl, p0, np);
     h.ensure(P.t_pts, np * sizeof(Point));
     LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
     // digit planes of the gathered Green's-function operands, straight from G
@@ -712,6 +747,7 @@ void chi0_run_tc(Handle &h) {
     }
     timed_grouped(h, cpf, sod, ef, err, P.gargs3);
   }
+  fill_partners(h);
   int e_host = 0;
   LR_CUDA(cudaMemcpyAsync(&e_host, err, 4, cudaMemcpyDeviceToHost, s));
   LR_CUDA(cudaStreamSynchronize(s));
@@ -734,7 +770,8 @@ void chi0_run(Handle &h, double *ms_gemm) {
   h.ensure(h.d_chi_tau, (size_t)ntau * nR * naux * naux * sizeof(double));
   // points per batch: bounded workspace (1 GiB, at least one point)
   const long long per_point = 2 * (P.bg_sz + P.ag_sz + P.n_sz + P.x_sz) + P.o_sz;
-  const long long total_pts = (long long)ntau * nR;
+  const std::vector<int> rl = chi0_r_list(h.mesh);
+  const long long total_pts = (long long)ntau * rl.size();
   long long npb = std::max<long long>(1, (1LL << 27) / std::max<long long>(1, per_point));
   npb = std::min(npb, total_pts);
   DevBuf &ws = P.ws;
@@ -750,13 +787,7 @@ void chi0_run(Handle &h, double *ms_gemm) {
   for (int a = 0; a < nat; ++a) max_m = std::max(max_m, P.m[a]);
   for (long long p0 = 0; p0 < total_pts; p0 += npb) {
     const int np = (int)std::min(npb, total_pts - p0);
-    std::vector<Point> pts(np);
-    for (int q = 0; q < np; ++q) {
-      const long long idx = p0 + q;
-      pts[q].itau = (int)(idx / nR);
-      pts[q].iR = (int)(idx % nR);
-      h.mesh.split(pts[q].iR, pts[q].R[0], pts[q].R[1], pts[q].R[2]);
-    }
+    std::vector<Point> pts = make_points(h, rl, p0, np);
     h.ensure(P.t_pts, np * sizeof(Point));
     LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
     const Point *dpts = (const Point *)P.t_pts.p;
@@ -803,8 +834,16 @@ void chi0_run(Handle &h, double *ms_gemm) {
     }
     dgemm_batched(h, b2, s, P.gargs2);
   }
+  fill_partners(h);
   LR_CUDA(cudaStreamSynchronize(s));
   if (ms_gemm) *ms_gemm = 0;
+}
+
+std::vector<int> chi0_r_list(const Mesh &m) {
+  std::vector<int> rl;
+  for (int i = 0; i < m.size(); ++i)
+    if (i <= m.neg(i)) rl.push_back(i);
+  return rl;
 }
 
 }  // namespace librpa

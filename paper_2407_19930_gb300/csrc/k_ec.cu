@@ -137,6 +137,32 @@ __global__ void k_zero_upper(double2 *const *mats, int n, int ld) {
   if (j > i) M[(size_t)i * ld + j] = make_double2(0.0, 0.0);
 }
 
+// Largest |V(-q) - conj V(q)| over the pairs q < -q (res[0]) and largest |V(q)| (res[1]), as the
+// bit patterns of non-negative doubles (ordered like the values) for atomicMax.
+__global__ void k_conj_check(const double2 *V, int n, int n1, int n2, int n3, unsigned long long *res) {
+  const int q = blockIdx.y;
+  const int a = q / (n2 * n3), b = (q / n3) % n2, c = q % n3;
+  const int p = (((n1 - a) % n1) * n2 + (n2 - b) % n2) * n3 + (n3 - c) % n3;
+  if (p <= q) return;
+  const size_t nn = (size_t)n * n;
+  const double2 *Vq = V + nn * q, *Vp = V + nn * p;
+  double d = 0.0, m = 0.0;
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < nn; x += (size_t)gridDim.x * blockDim.x) {
+    const double2 u = Vq[x], v = Vp[x];
+    d = fmax(d, fmax(fabs(v.x - u.x), fabs(v.y + u.y)));
+    m = fmax(m, fmax(fabs(u.x), fabs(u.y)));
+    if (isnan(u.x + u.y + v.x + v.y)) d = INFINITY;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(res, (unsigned long long)__double_as_longlong(d));
+    atomicMax(res + 1, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
 // A = -L^H chi0 L on entry (lower triangle).  trace[b] = Re Tr(L^H chi0 L) = -sum Re A_ii;
 // then A_ii += 1 (A = I - L^H chi0 L).  One CTA per matrix.
 __global__ void k_diag_shift(double2 *const *mats, int n, int ld, double *trace) {
@@ -307,14 +333,37 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     oz::sliced_bind(slh, w + o_slh, 2 * n, 2 * n, S);
     tc = &tcs;
   }
-  // Cholesky of every V(q)
-  LR_CUDA(cudaMemcpyAsync(Lq, h.d_vq.p, nq * mat, cudaMemcpyDeviceToDevice, s));
-  std::vector<double2 *> lp(nq);
-  for (int q = 0; q < nq; ++q) lp[q] = Lq + q * n2;
-  LR_CUDA(cudaMemcpyAsync(ptrs, lp.data(), nq * 8, cudaMemcpyHostToDevice, s));
+  // q <-> -q: chi0(R) is real, so chi0(-q) = conj chi0(q); when also V(-q) = conj V(q) (to 1e-12
+  // of max |V|), the integrand of -q equals that of q (ln det and trace of complex-conjugate
+  // matrices), and only q <= -q is computed.  The check runs once per set of V(q).
+  if (h.vq_sym < 0) {
+    unsigned long long *res = (unsigned long long *)(w + o_ld);   // lndet is cleared again below
+    LR_CUDA(cudaMemsetAsync(res, 0, 16, s));
+    k_conj_check<<<dim3(64, (unsigned)nq), 256, 0, s>>>((const double2 *)h.d_vq.p, n, h.mesh.n1, h.mesh.n2,
+                                                        h.mesh.n3, res);
+    ++launch_counter();
+    LR_CUDA(cudaGetLastError());
+    double dm[2] = {0, 0};
+    LR_CUDA(cudaMemcpyAsync(dm, res, 16, cudaMemcpyDeviceToHost, s));
+    LR_CUDA(cudaStreamSynchronize(s));
+    h.vq_sym = dm[0] <= 1e-12 * dm[1] ? 1 : 0;
+    LR_CUDA(cudaMemsetAsync(lndet, 0, 16, s));
+  }
+  std::vector<int> qlist;
+  for (int q = 0; q < nq; ++q)
+    if (h.vq_sym != 1 || q <= h.mesh.neg(q)) qlist.push_back(q);
+  const int nql = (int)qlist.size();
+  // Cholesky of every V(q) computed, packed in qlist order (the batched factorisation needs a
+  // uniform stride)
+  std::vector<double2 *> lp(nql);
+  for (int i = 0; i < nql; ++i) {
+    lp[i] = Lq + (size_t)i * n2;
+    LR_CUDA(cudaMemcpyAsync(lp[i], (const char *)h.d_vq.p + (size_t)qlist[i] * mat, mat, cudaMemcpyDeviceToDevice, s));
+  }
+  LR_CUDA(cudaMemcpyAsync(ptrs, lp.data(), nql * 8, cudaMemcpyHostToDevice, s));
   potrf_batched(h, ptrs, lp, n, n, lndet_v, info, tc);
   {
-    dim3 g((unsigned)((n2 + 255) / 256), (unsigned)nq);
+    dim3 g((unsigned)((n2 + 255) / 256), (unsigned)nql);
     k_zero_upper<<<g, 256, 0, s>>>(ptrs, n, n);
     ++launch_counter();
   }
@@ -328,9 +377,10 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   // sum_{i >= j} (n - i) MACs per matrix
   const double dn = n;
   const double fl_w = 8.0 * nw * dn * (dn * (dn + 1) / 2), fl_a = 8.0 * nw * (dn * (dn + 1) * (dn + 2) / 6);
-  for (int q = 0; q < nq; ++q) {
+  for (int qi = 0; qi < nql; ++qi) {
+    const int q = qlist[qi];
     if (S >= 0) {
-      const double2 *L = Lq + q * n2;
+      const double2 *L = Lq + (size_t)qi * n2;
       oz::split_complex(L, n, oz::OP_N, false, n, n, 1, 0, sl, s);     // B'^T of W = chi0 L
       oz::split_complex(L, n, oz::OP_H, true, n, n, 1, 0, slh, s);     // A' of L^H W
       oz::split_complex(chi + (size_t)q * nw * n2, n, oz::OP_N, true, n, n, nw, (long long)n2, sx, s);
@@ -368,7 +418,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
       for (int k = 0; k < nw; ++k) {
         ZGemm z{};
         z.A = chi + ((size_t)q * nw + k) * n2;
-        z.B = Lq + q * n2;
+        z.B = Lq + (size_t)qi * n2;
         z.C = Wm + k * n2;
         z.M = z.N = z.K = n;
         z.lda = z.ldb = z.ldc = n;
@@ -376,7 +426,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
         z.beta = make_double2(0.0, 0.0);
         b1.push_back(z);
         ZGemm y{};
-        y.A = Lq + q * n2;     // op(A) = L^H: stored [K][M], conjugated
+        y.A = Lq + (size_t)qi * n2;     // op(A) = L^H: stored [K][M], conjugated
         y.B = Wm + k * n2;
         y.C = Am + k * n2;
         y.M = y.N = y.K = n;
@@ -399,6 +449,12 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     ++launch_counter();
     potrf_batched(h, aptr, ap, n, n, lndet + (size_t)q * nw, info + nq + (size_t)q * nw, tc);
   }
+  for (int q : qlist) {   // the integrands of -q
+    const int p = h.mesh.neg(q);
+    if (p == q || h.vq_sym != 1) continue;
+    LR_CUDA(cudaMemcpyAsync(lndet + (size_t)p * nw, lndet + (size_t)q * nw, nw * 8, cudaMemcpyDeviceToDevice, s));
+    LR_CUDA(cudaMemcpyAsync(trace + (size_t)p * nw, trace + (size_t)q * nw, nw * 8, cudaMemcpyDeviceToDevice, s));
+  }
   k_energy<<<1, 1, 0, s>>>(lndet, trace, wo, nq, nw, out);
   ++launch_counter();
   LR_CUDA(cudaGetLastError());
@@ -420,7 +476,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   // flop count of this stage (complex MAC = 8 real flops): per q (4/3 n^3 real for the Cholesky of
   // V), per (q, omega): W = chi0 L (n^3/2 MAC), L^H W lower (n^3/6 MAC), Cholesky (n^3/6 MAC)
   const double n3 = (double)n * n * n;
-  h.stats.flop_ec = nq * (8.0 * n3 / 6.0) + (double)nq * nw * 8.0 * (n3 / 2 + n3 / 6 + n3 / 6);
+  h.stats.flop_ec = nql * (8.0 * n3 / 6.0) + (double)nql * nw * 8.0 * (n3 / 2 + n3 / 6 + n3 / 6);
   return LIBRPA_OK;
 }
 

@@ -57,6 +57,9 @@ CONFIGS = {
                       n_low=np.array([2]), kmesh=(1, 1, 1)), 5, vscale=1e-2),
     "cubic_3x1x2": lambda: syn.make_inputs(
         syn.cubic_two_atom(nao=5, naux=33, nlow=2, kmesh=(3, 1, 2)), 31, vscale=2e-3),
+    # 9 cells of which 8 pair up as (R, -R): most chi0(R, tau) come from the pair symmetry
+    "cubic_3x3x1": lambda: syn.make_inputs(
+        syn.cubic_two_atom(nao=4, naux=16, nlow=2, kmesh=(3, 3, 1)), 41, vscale=2e-3),
 }
 
 
@@ -112,7 +115,7 @@ def _opts(precision=L.LIBRPA_FP64, chi0_slices=0, ec_slices=0):
     return o
 
 
-@pytest.fixture(scope="module", params=["cubic", "mixed", "cubic_3x1x2"])
+@pytest.fixture(scope="module", params=["cubic", "mixed", "cubic_3x1x2", "cubic_3x3x1"])
 def tc_case(request):
     """Same inputs as the FP64 parity cases, run with the FP64-accurate tensor-core mode
     (5 BF16 digit planes per operand in the chi0 and ln det GEMMs)."""
@@ -143,7 +146,7 @@ MEV = 27211.386245988
 TOL_MIXED_MEV_PER_ATOM = 0.1
 
 
-@pytest.mark.parametrize("name", ["cubic", "mixed"])
+@pytest.mark.parametrize("name", ["cubic", "mixed", "cubic_3x3x1"])
 def test_split_mode_energy(name):
     """Mixed mode (chi0 GEMMs on 3 BF16 digit planes, FP32 O assembly; ln det FP64-accurate):
     E_c within 0.1 meV/atom of the FP64 oracle."""
@@ -174,6 +177,25 @@ def test_tc_mode_energy(tc_case):
     assert abs(gpu["ec"] - ref["ec"]) < TOL_EC
     assert np.abs(gpu["ec_q"] - ref["ec_q"]).max() < TOL_EC
     assert gpu["stats"]["n_gemm_ec"] > 0
+
+
+def test_unpaired_coulomb_uses_every_q():
+    """With V(-q) != conj V(q) the ln det stage must not pair q with -q: every q is computed and
+    the energy still matches the oracle on the same (unpaired) input."""
+    inp = CONFIGS["cubic_3x3x1"]()
+    st = inp.st
+    rng = np.random.default_rng(5)
+    n = st.naux
+    x = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    vq = np.array(inp.vq)
+    vq[1] = vq[1] + 1e-4 * (x @ x.conj().T) / n      # q = (0,1,0); its partner (0,2,0) unchanged
+    inp.vq = vq
+    grid = ogrid.make_grid(6, *inp.delta_range)
+    ref = pipeline.rpa_energy(inp, grid)
+    gpu = _run(inp, grid)
+    assert abs(gpu["ec"] - ref["ec"]) < TOL_EC
+    assert np.abs(gpu["ec_q"] - ref["ec_q"]).max() < TOL_EC
+    assert abs(ref["ec_q"][1] - ref["ec_q"][2]) > 100 * TOL_EC   # the perturbation is visible
 
 
 def test_library_grid_path():
