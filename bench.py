@@ -157,6 +157,21 @@ def cpu_sample(inp, grid, budget_s=25.0):
 # ------------------------------------------------------------------ arms
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (x itself on one rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world_size, t_max):
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return units_per_rank * world_size / t_max
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -253,12 +268,8 @@ def run_gpu(args):
         ev1.record(stream)
         barrier()
         clk = clocks.stop()
-        t = ev0.elapsed_time(ev1) / 1e3
-        if dist:
-            tt = torch.tensor([t], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        value = args.steps * ws / t
+        t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, "cuda")
+        value = job_value(args.steps, ws, t)
         # ---------------- end to end through host buffers
         h2d = sum(C.nbytes for *_, C in inp.lri) + st.nk * (inp.wfc[0].real.nbytes * 2 + inp.eig[0].nbytes * 2) \
             + st.nk * inp.vq[0].real.nbytes * 2
@@ -275,12 +286,8 @@ def run_gpu(args):
             L.librpa_gpu_chi0(h)
             ec_e2e, _, _ = L.librpa_gpu_ec(h)
         barrier()
-        te = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = args.e2e_steps * ws / te
+        te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = job_value(args.e2e_steps, ws, te) if args.e2e_steps else 0.0
     finally:
         L.librpa_gpu_destroy(h)
     # ---------------- the other precision modes on the same workload (1 GPU only)
