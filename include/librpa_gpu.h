@@ -111,6 +111,7 @@ typedef struct {
   double flop_exec_gemm_chi0; /* tensor-core MMA flops issued by the timed chi0 GEMMs (digit-plane
                                  products, tile padding and all); 0 in the FP64 mode */
   double flop_exec_gemm_ec;   /* the same for the timed ln det GEMMs */
+  size_t bytes_device_peak;   /* largest device footprint of the handle so far */
 } librpa_gpu_stats;
 
 /* Fill *o with defaults: device 0, own stream, cudaMalloc, n_tau = 16, FP64,
@@ -254,6 +255,79 @@ int librpa_gpu_get_chi0_freq(librpa_gpu_t h, int iq, int iomega, double *re, dou
 
 /* Stage timings and counters of the last chi0 / ec calls. Errors: E_ARG. */
 int librpa_gpu_get_stats(librpa_gpu_t h, librpa_gpu_stats *s);
+
+/* ---------------------------------------------------------------- serving loop
+ * Continuous batching of RPA energy requests on one GPU (not in the paper, whose
+ * library computes one system per call; each request runs the same path as
+ * librpa_gpu_chi0 + librpa_gpu_ec).  A request is a handle made by
+ * librpa_gpu_server_request and filled with the usual set_* calls; its inputs stay on
+ * the host until the server admits it.  The server admits queued requests in arrival
+ * order, letting a later request go first when the earlier one does not fit yet (not
+ * after the earlier one has waited 2 s).  A request is admitted when one of `slots`
+ * workers is free and its device-memory estimate (librpa_gpu_estimate_bytes) fits in
+ * what is left of the server's HBM budget.  Each worker runs its request on its own
+ * stream, from a stream-ordered memory pool, so admitted requests overlap on the device.
+ * Once the request is complete, the worker releases its device memory. */
+typedef struct librpa_gpu_server *librpa_gpu_server_t;
+
+typedef struct {
+  int device;         /* CUDA device */
+  int slots;          /* requests on the GPU at once (1 .. 64) */
+  size_t hbm_budget;  /* bytes for all admitted requests together; 0 = 90% of the free memory */
+} librpa_gpu_server_opts;
+
+typedef struct {
+  int status;             /* LIBRPA_OK or the request's error code */
+  double ec;              /* E_c in Ha per cell */
+  double ms_queue;        /* submit -> admission */
+  double ms_run;          /* admission -> result */
+  double ms_total;        /* submit -> result (the latency) */
+  size_t bytes_reserved;  /* the estimate the request was admitted with */
+  size_t bytes_peak;      /* its largest device footprint */
+  int slot;               /* worker that ran it */
+} librpa_gpu_result;
+
+typedef struct {
+  long long submitted, completed, failed;
+  double p50_ms, p99_ms;     /* latency percentiles over the completed requests */
+  double mean_queue_ms;
+  double energies_per_s;     /* completed / (last completion - first submission) */
+  int peak_running;          /* largest number of requests on the GPU at once */
+  size_t peak_reserved;      /* largest sum of admitted estimates */
+  size_t hbm_budget;         /* the budget in use */
+} librpa_gpu_server_stats;
+
+/* Upper bound of the device bytes h will hold during chi0 + ec, from its structure, LRI
+ * blocks, precision and grid size (the user grid, else opts.n_tau).  Needs no GPU.
+ * Errors: E_STATE (no structure), E_ARG. */
+int librpa_gpu_estimate_bytes(librpa_gpu_t h, size_t *bytes);
+
+/* Start the workers.  Errors: E_ARG, E_CUDA. */
+int librpa_gpu_server_create(librpa_gpu_server_t *s, const librpa_gpu_server_opts *o);
+
+/* New request handle (deferred inputs) with precision and grid options from *o (its
+ * device, stream and allocator fields are ignored: the server supplies them).  Fill it
+ * with set_structure, set_lri_coeffs, set_green, set_coulomb and optionally set_grid,
+ * then submit it.  Free it with librpa_gpu_destroy after its result was taken.
+ * Errors: E_ARG, E_NOMEM. */
+int librpa_gpu_server_request(librpa_gpu_server_t s, const librpa_gpu_opts *o, librpa_gpu_t *req);
+
+/* Queue a filled request; *ticket identifies it.  The caller must not use req until
+ * librpa_gpu_server_wait has returned its result.  Errors: E_STATE (inputs missing),
+ * E_NOMEM (its estimate exceeds the whole budget), E_ARG. */
+int librpa_gpu_server_submit(librpa_gpu_server_t s, librpa_gpu_t req, long long *ticket);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request's result.  Returns
+ * LIBRPA_OK with *r filled (r->status is the request's own code), or E_TIMEOUT if it is
+ * not finished yet, E_ARG for an unknown ticket. */
+int librpa_gpu_server_wait(librpa_gpu_server_t s, long long ticket, double timeout_s, librpa_gpu_result *r);
+
+/* Counters and latency percentiles so far.  Errors: E_ARG. */
+int librpa_gpu_server_get_stats(librpa_gpu_server_t s, librpa_gpu_server_stats *st);
+
+/* Finish the running requests, cancel the queued ones (their status becomes
+ * E_STATE), stop the workers and free the pool.  NULL is ignored. */
+void librpa_gpu_server_destroy(librpa_gpu_server_t s);
 
 /* One-line description of the last error on h (never NULL; "" after success). */
 const char *librpa_gpu_last_error(librpa_gpu_t h);

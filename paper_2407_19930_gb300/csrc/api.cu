@@ -11,7 +11,7 @@
 namespace librpa {
 
 long long &launch_counter() {
-  static long long n = 0;
+  static thread_local long long n = 0;   // per host thread: every handle runs on one thread at a time
   return n;
 }
 
@@ -34,6 +34,7 @@ void *Handle::dalloc(size_t bytes) {
   }
   allocs[p] = bytes;
   bytes_held += bytes;
+  bytes_peak = std::max(bytes_peak, bytes_held);
   return p;
 }
 
@@ -130,11 +131,48 @@ void free_device_state(Handle &h) {
 }
 
 }  // namespace
+
+void release_device(Handle &h) { free_device_state(h); }
+
+void materialize(Handle &h) {
+  if (!h.deferred) return;
+  const size_t nk = h.mesh.size(), nb = h.nao, per_k = nb * h.nao, n2 = (size_t)h.naux * h.naux;
+  if (!h.d_wfc.p && !h.stage_wfc.empty()) {
+    h.ensure(h.d_wfc, nk * per_k * 16);
+    h.ensure(h.d_eig, nk * nb * 8);
+    h.ensure(h.d_occ, nk * nb * 8);
+    LR_CUDA(cudaMemcpyAsync(h.d_wfc.p, h.stage_wfc.data(), nk * per_k * 16, cudaMemcpyHostToDevice, h.stream));
+    LR_CUDA(cudaMemcpyAsync(h.d_eig.p, h.eig.data(), nk * nb * 8, cudaMemcpyHostToDevice, h.stream));
+    LR_CUDA(cudaMemcpyAsync(h.d_occ.p, h.occ.data(), nk * nb * 8, cudaMemcpyHostToDevice, h.stream));
+  }
+  if (!h.d_vq.p && !h.stage_vq.empty()) {
+    h.ensure(h.d_vq, n2 * 16 * nk);
+    LR_CUDA(cudaMemcpyAsync(h.d_vq.p, h.stage_vq.data(), n2 * 16 * nk, cudaMemcpyHostToDevice, h.stream));
+  }
+  LR_CUDA(cudaStreamSynchronize(h.stream));
+}
+
+size_t estimate_device_bytes(Handle &h) {
+  const int ntau_saved = h.ntau;
+  if (!h.have_grid) h.ntau = h.opts.n_tau;
+  const size_t nk = h.mesh.size(), nb = h.nao, n2ao = (size_t)h.nao * h.nao, n2 = (size_t)h.naux * h.naux;
+  size_t b = nk * nb * h.nao * 16 + 2 * nk * nb * 8;            // KS data
+  b += nk * n2 * 16;                                              // V(q)
+  b += 2 * (size_t)h.ntau * nk * n2ao * 8;                        // G^occ, G^vir
+  b += nk * (size_t)h.ntau * n2 * 16;                             // chi0(q, i omega)
+  Chi0Plan P;
+  chi0_shape(h, P);
+  b += chi0_device_bytes(h, P);
+  b += std::max(green_work_bytes(h), std::max(freq_work_bytes(h), ec_work_bytes(h)));
+  b += (size_t)64 << 20;                                          // descriptor and tile uploads
+  h.ntau = ntau_saved;
+  return b;
+}
+
 }  // namespace librpa
 
 using namespace librpa;
 
-struct librpa_gpu : public Handle {};
 
 extern "C" {
 
@@ -216,6 +254,8 @@ int librpa_gpu_set_structure(librpa_gpu_t h, int natoms, const double lat[9], co
     h->r_cut = r_cut;
     const int nk = h->mesh.size();
     h->lri.clear();
+    h->stage_wfc.clear();
+    h->stage_vq.clear();
     h->eig.assign((size_t)nk * h->nao, 0.0);
     h->occ.assign((size_t)nk * h->nao, 0.0);
     h->have_k.assign(nk, 0);
@@ -263,8 +303,20 @@ int librpa_gpu_set_green(librpa_gpu_t h, int ispin, int ik, int nbands, const do
       h->eig[(size_t)ik * nb + n] = eig[n];
       h->occ[(size_t)ik * nb + n] = occ[n];
     }
-    cudaSetDevice(h->opts.device);
     const size_t nk = h->mesh.size(), per_k = (size_t)nb * h->nao;
+    if (h->deferred) {   // kept on the host until the request is admitted
+      h->stage_wfc.resize(nk * per_k * 2);
+      double *w = h->stage_wfc.data() + (size_t)ik * per_k * 2;
+      for (size_t x = 0; x < per_k; ++x) {
+        w[2 * x] = wfc_re[x];
+        w[2 * x + 1] = wfc_im[x];
+      }
+      h->efermi_k[ik] = efermi;
+      h->have_k[ik] = 1;
+      h->chi0_done = false;
+      return LIBRPA_OK;
+    }
+    cudaSetDevice(h->opts.device);
     h->ensure(h->d_wfc, nk * per_k * 16);
     h->ensure(h->d_eig, nk * nb * 8);
     h->ensure(h->d_occ, nk * nb * 8);
@@ -291,8 +343,19 @@ int librpa_gpu_set_coulomb(librpa_gpu_t h, int iq, const double *V_re, const dou
   return guarded(h, [&]() -> int {
     if (!h->have_structure) return fail(h, LIBRPA_E_STATE, "set_coulomb before set_structure");
     if (iq < 0 || iq >= h->mesh.size() || !V_re || !V_im) return fail(h, LIBRPA_E_ARG, "set_coulomb: bad q or NULL");
-    cudaSetDevice(h->opts.device);
     const size_t n2 = (size_t)h->naux * h->naux;
+    if (h->deferred) {   // kept on the host until the request is admitted
+      h->stage_vq.resize(n2 * 2 * h->mesh.size());
+      double *v = h->stage_vq.data() + (size_t)iq * n2 * 2;
+      for (size_t x = 0; x < n2; ++x) {
+        v[2 * x] = V_re[x];
+        v[2 * x + 1] = V_im[x];
+      }
+      h->have_q[iq] = 1;
+      h->vq_sym = -1;
+      return LIBRPA_OK;
+    }
+    cudaSetDevice(h->opts.device);
     h->ensure(h->d_vq, n2 * 16 * h->mesh.size());
     std::vector<double> tmp(2 * n2);
     for (size_t x = 0; x < n2; ++x) {
@@ -384,6 +447,7 @@ int librpa_gpu_chi0(librpa_gpu_t h, double *out_re, double *out_im) {
       h->ntau = n;
       h->have_grid = true;
     }
+    materialize(*h);
     h->stats = librpa_gpu_stats{};
     long long l0 = launch_counter();
     cudaEvent_t ev[4];
@@ -413,6 +477,7 @@ int librpa_gpu_chi0(librpa_gpu_t h, double *out_re, double *out_im) {
     h->stats.flop_chi0 = h->plan.flop_per_point * h->ntau * (double)chi0_r_list(h->mesh).size();
     h->stats.launches = launch_counter() - l0;
     h->stats.bytes_device = h->bytes_held;
+    h->stats.bytes_device_peak = h->bytes_peak;
     if (h->opts.check_level >= 1 && !(imag <= 1e-10))
       return fail(h, LIBRPA_E_NUMERIC, "chi0: G(R, tau) has a relative imaginary part of " + std::to_string(imag) +
                                            " (inputs without time-reversal symmetry?)");
@@ -457,6 +522,7 @@ int librpa_gpu_ec(librpa_gpu_t h, double *ec, double *ec_q, double *ec_w) {
     h->resolve_timers();
     h->stats.launches += launch_counter() - l0;
     h->stats.bytes_device = h->bytes_held;
+    h->stats.bytes_device_peak = h->bytes_peak;
     if (rc == LIBRPA_E_NOT_PD)
       return fail(h, rc, "ec: a Cholesky pivot was <= 0 (V(q) or 1 - V^1/2 chi0 V^1/2 not positive definite)");
     return rc;

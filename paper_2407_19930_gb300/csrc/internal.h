@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <map>
@@ -97,8 +98,13 @@ struct Handle {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::string last_error;
-  size_t bytes_held = 0;
+  size_t bytes_held = 0, bytes_peak = 0;
   std::map<void *, size_t> allocs;
+  // deferred inputs (requests of the serving loop): set_green and set_coulomb keep the KS
+  // coefficients and V(q) on the host until materialize() uploads them
+  bool deferred = false;
+  std::vector<double> stage_wfc;   // [nk][nb][nao] complex interleaved
+  std::vector<double> stage_vq;    // [nq][naux][naux] complex interleaved
 
   // structure
   bool have_structure = false;
@@ -163,16 +169,30 @@ int build_grid(int n, double dmin, double dmax, double *tau, double *omega, doub
 // ----------------------------------------------------------------- kernels
 // K1 (k_green.cu): G^occ and G^vir for all (tau, R).  Returns max |Im G| / max |G|.
 double green_build(Handle &h);
+size_t green_work_bytes(const Handle &h);
 // K2 (k_chi0.cu)
 void chi0_plan(Handle &h);
 void chi0_run(Handle &h, double *ms_gemm);
+// host part of chi0_plan: neighbour lists, packed-column sizes, workspace offsets, flops
+void chi0_shape(const Handle &h, Chi0Plan &P);
+// device bytes the chi0 stage holds for this shape (packed C and its digit planes, chi0(R, tau),
+// batch workspace, tables)
+size_t chi0_device_bytes(const Handle &h, const Chi0Plan &P);
 // lattice vectors R whose chi0(R, tau) is computed (R <= -R in the flat BvK order); the others
 // are filled as chi0(-R, tau)^T
 std::vector<int> chi0_r_list(const Mesh &m);
 // K3 + K4 (k_freq.cu)
 void freq_transform(Handle &h);
+size_t freq_work_bytes(const Handle &h);
 // K5 + K6 (k_ec.cu); returns LIBRPA_OK or LIBRPA_E_NOT_PD
 int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w);
+size_t ec_work_bytes(const Handle &h);
+
+// api.cu: upload the deferred inputs of h; release every device buffer of h; an upper bound of
+// the device bytes h holds during chi0 + ec (grid size from the user grid or opts.n_tau)
+void materialize(Handle &h);
+void release_device(Handle &h);
+size_t estimate_device_bytes(Handle &h);
 
 // generic batched complex FP64 GEMM (k_zgemm.cu), used by K1 and K5
 struct ZGemm {
@@ -199,3 +219,6 @@ void zgemm_batched(const std::vector<ZGemm> &batch, const ZGemmFlags &f, cudaStr
 long long &launch_counter();
 
 }  // namespace librpa
+
+// the opaque handle type of the C ABI
+struct librpa_gpu : public librpa::Handle {};

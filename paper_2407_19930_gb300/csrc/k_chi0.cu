@@ -339,8 +339,7 @@ void dgemm_batched(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, D
 
 }  // namespace
 
-void chi0_plan(Handle &h) {
-  Chi0Plan &P = h.plan;
+void chi0_shape(const Handle &h, Chi0Plan &P) {
   const int nat = h.natoms;
   P.natoms = nat;
   P.nao = h.nao;
@@ -384,6 +383,49 @@ void chi0_plan(Handle &h) {
   P.cp_off.assign(nat + 1, 0);
   for (int U = 0; U < nat; ++U) P.cp_off[U + 1] = P.cp_off[U] + (long long)h.n_aux[U] * h.n_ao[U] * P.m[U];
   P.cp_total = P.cp_off[nat];
+  // workspace offsets (elements, per point and per Green's function)
+  P.bg_off.assign(nat + 1, 0);
+  P.ag_off.assign(nat + 1, 0);
+  P.n_off.assign(nat + 1, 0);
+  P.x_off.assign(nat + 1, 0);
+  P.o_off.assign(nat + 1, 0);
+  double fl = 0;
+  for (int V = 0; V < nat; ++V) {
+    const long long rowsV = (long long)h.n_aux[V] * h.n_ao[V];
+    P.bg_off[V + 1] = P.bg_off[V] + (long long)P.m_all * P.m[V];
+    P.ag_off[V + 1] = P.ag_off[V] + (long long)h.nao * P.m[V];
+    P.n_off[V + 1] = P.n_off[V] + rowsV * P.m_all;
+    P.x_off[V + 1] = P.x_off[V] + (long long)h.nao * rowsV;
+    P.o_off[V + 1] = P.o_off[V] + (long long)h.naux * h.n_ao[V] * P.m[V];
+    fl += 2.0 * 2.0 * rowsV * P.m[V] * P.m_all;    // N-step, both G
+    fl += 2.0 * 2.0 * h.nao * P.m[V] * rowsV;      // X-step, both G
+  }
+  for (int U = 0; U < nat; ++U) {
+    const double cols = (double)h.n_ao[U] * P.m[U];
+    for (int V = 0; V < nat; ++V) fl += 2.0 * h.n_aux[V] * cols * 4.0 * h.n_ao[V];   // O assembly
+    fl += 2.0 * h.n_aux[U] * cols * h.naux;                                        // final
+  }
+  P.flop_per_point = fl;
+  P.bg_sz = P.bg_off[nat];
+  P.ag_sz = P.ag_off[nat];
+  P.n_sz = P.n_off[nat];
+  P.x_sz = P.x_off[nat];
+  P.o_sz = P.o_off[nat];
+  P.max_m = P.max_nm = 0;
+  P.cpnx_off.assign(nat + 1, 0);
+  for (int a = 0; a < nat; ++a) {
+    P.max_m = std::max(P.max_m, P.m[a]);
+    P.max_nm = std::max(P.max_nm, h.n_ao[a] * P.m[a]);
+    P.cpnx_off[a + 1] = P.cpnx_off[a] + h.n_aux[a] * h.n_ao[a];
+  }
+  P.cpnx_rows = P.cpnx_off[nat];
+  P.tc_S = h.chi0_S;
+}
+
+void chi0_plan(Handle &h) {
+  Chi0Plan &P = h.plan;
+  chi0_shape(h, P);
+  const int nat = h.natoms;
   std::vector<double> cp(P.cp_total, 0.0);
   for (int U = 0; U < nat; ++U) {
     const int nU = h.n_ao[U], mU = P.m[U];
@@ -425,34 +467,6 @@ void chi0_plan(Handle &h) {
   upload(h, P.d_lam, lam);
   upload(h, P.d_kap, kap);
   upload(h, P.d_uni, un);
-  // workspace offsets (elements, per point and per Green's function)
-  P.bg_off.assign(nat + 1, 0);
-  P.ag_off.assign(nat + 1, 0);
-  P.n_off.assign(nat + 1, 0);
-  P.x_off.assign(nat + 1, 0);
-  P.o_off.assign(nat + 1, 0);
-  double fl = 0;
-  for (int V = 0; V < nat; ++V) {
-    const long long rowsV = (long long)h.n_aux[V] * h.n_ao[V];
-    P.bg_off[V + 1] = P.bg_off[V] + (long long)P.m_all * P.m[V];
-    P.ag_off[V + 1] = P.ag_off[V] + (long long)h.nao * P.m[V];
-    P.n_off[V + 1] = P.n_off[V] + rowsV * P.m_all;
-    P.x_off[V + 1] = P.x_off[V] + (long long)h.nao * rowsV;
-    P.o_off[V + 1] = P.o_off[V] + (long long)h.naux * h.n_ao[V] * P.m[V];
-    fl += 2.0 * 2.0 * rowsV * P.m[V] * P.m_all;    // N-step, both G
-    fl += 2.0 * 2.0 * h.nao * P.m[V] * rowsV;      // X-step, both G
-  }
-  for (int U = 0; U < nat; ++U) {
-    const double cols = (double)h.n_ao[U] * P.m[U];
-    for (int V = 0; V < nat; ++V) fl += 2.0 * h.n_aux[V] * cols * 4.0 * h.n_ao[V];   // O assembly
-    fl += 2.0 * h.n_aux[U] * cols * h.naux;                                        // final
-  }
-  P.flop_per_point = fl;
-  P.bg_sz = P.bg_off[nat];
-  P.ag_sz = P.ag_off[nat];
-  P.n_sz = P.n_off[nat];
-  P.x_sz = P.x_off[nat];
-  P.o_sz = P.o_off[nat];
   upload(h, P.t_n_ao, h.n_ao);
   upload(h, P.t_n_aux, h.n_aux);
   upload(h, P.t_ao_off, h.ao_off);
@@ -466,15 +480,6 @@ void chi0_plan(Handle &h) {
   upload(h, P.t_x_off, P.x_off);
   upload(h, P.t_o_off, P.o_off);
   // tensor-core route: digit planes of the packed coefficients, split once per plan
-  P.max_m = P.max_nm = 0;
-  P.cpnx_off.assign(nat + 1, 0);
-  for (int a = 0; a < nat; ++a) {
-    P.max_m = std::max(P.max_m, P.m[a]);
-    P.max_nm = std::max(P.max_nm, h.n_ao[a] * P.m[a]);
-    P.cpnx_off[a + 1] = P.cpnx_off[a] + h.n_aux[a] * h.n_ao[a];
-  }
-  P.cpnx_rows = P.cpnx_off[nat];
-  P.tc_S = h.chi0_S;
   if (P.tc_S >= 0) {
     const int S = P.tc_S;
     const double *Cp = (const double *)h.d_cpack.p;
@@ -619,6 +624,49 @@ void timed_grouped(Handle &h, const oz::Sliced &a, const oz::Sliced &b, const st
   h.timed.push_back(t);
 }
 
+// Workspace of the tensor-core route for a batch of npb points: FP64 N, X, O and the digit planes
+// of Bg, Ag and O (bounded by 2 GiB, at least one point).
+struct TcWs {
+  long long npb;
+  size_t b_n, b_x, b_o, b_bg, b_ag, b_od, total;
+};
+
+TcWs tc_ws(const Handle &h, const Chi0Plan &P) {
+  const int nat = h.natoms, S = h.chi0_S;
+  const int rows_bg = 2 * nat * P.m_all, rows_ag = 2 * nat * h.nao, rows_o = nat * h.naux;
+  const size_t fp = 8 * (size_t)(2 * P.n_sz + 2 * P.x_sz + P.o_sz);
+  const size_t per_point = fp + oz::sliced_bytes(rows_bg, P.max_m, S) + oz::sliced_bytes(rows_ag, P.max_m, S) +
+                           oz::sliced_bytes(rows_o, P.max_nm, S) + 4096;
+  const long long total_pts = (long long)h.ntau * chi0_r_list(h.mesh).size();
+  TcWs w;
+  w.npb = std::min(std::max<long long>(1, (2LL << 30) / (long long)per_point), total_pts);
+  w.b_n = 8 * (size_t)w.npb * 2 * P.n_sz;
+  w.b_x = 8 * (size_t)w.npb * 2 * P.x_sz;
+  w.b_o = 8 * (size_t)w.npb * P.o_sz;
+  w.b_bg = oz::sliced_bytes((int)w.npb * rows_bg, P.max_m, S);
+  w.b_ag = oz::sliced_bytes((int)w.npb * rows_ag, P.max_m, S);
+  w.b_od = oz::sliced_bytes((int)w.npb * rows_o, P.max_nm, S);
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  w.total = al(w.b_n) + al(w.b_x) + al(w.b_o) + al(w.b_bg) + al(w.b_ag) + al(w.b_od) + 256;
+  return w;
+}
+
+// Workspace of the FP64 route: gathered G operands, N, X and O for npb points (2^27 doubles,
+// at least one point).
+struct DpWs {
+  long long npb, per_point;
+  size_t total;
+};
+
+DpWs dp_ws(const Handle &h, const Chi0Plan &P) {
+  DpWs w;
+  w.per_point = 2 * (P.bg_sz + P.ag_sz + P.n_sz + P.x_sz) + P.o_sz;
+  const long long total_pts = (long long)h.ntau * chi0_r_list(h.mesh).size();
+  w.npb = std::min(std::max<long long>(1, (1LL << 27) / std::max<long long>(1, w.per_point)), total_pts);
+  w.total = (size_t)w.npb * w.per_point * sizeof(double);
+  return w;
+}
+
 // Tensor-core route: the N, X and final GEMMs on digit planes (S = h.chi0_S).
 void chi0_run_tc(Handle &h) {
   Chi0Plan &P = h.plan;
@@ -626,20 +674,13 @@ void chi0_run_tc(Handle &h) {
   cudaStream_t s = h.stream;
   h.ensure(h.d_chi_tau, (size_t)ntau * nR * naux * naux * sizeof(double));
   const int rows_bg = 2 * nat * P.m_all, rows_ag = 2 * nat * nao, rows_o = nat * naux;
-  // per point: FP64 N, X, O and the digit planes of Bg, Ag and O
-  const size_t fp = 8 * (size_t)(2 * P.n_sz + 2 * P.x_sz + P.o_sz);
-  const size_t per_point = fp + oz::sliced_bytes(rows_bg, P.max_m, S) + oz::sliced_bytes(rows_ag, P.max_m, S) +
-                           oz::sliced_bytes(rows_o, P.max_nm, S) + 4096;
   const std::vector<int> rl = chi0_r_list(h.mesh);
   const long long total_pts = (long long)ntau * rl.size();
-  long long npb = std::max<long long>(1, (2LL << 30) / (long long)per_point);
-  npb = std::min(npb, total_pts);
-  const size_t b_n = 8 * (size_t)npb * 2 * P.n_sz, b_x = 8 * (size_t)npb * 2 * P.x_sz, b_o = 8 * (size_t)npb * P.o_sz;
-  const size_t b_bg = oz::sliced_bytes((int)npb * rows_bg, P.max_m, S);
-  const size_t b_ag = oz::sliced_bytes((int)npb * rows_ag, P.max_m, S);
-  const size_t b_od = oz::sliced_bytes((int)npb * rows_o, P.max_nm, S);
+  const TcWs tw = tc_ws(h, P);
+  const long long npb = tw.npb;
+  const size_t b_n = tw.b_n, b_x = tw.b_x, b_o = tw.b_o, b_bg = tw.b_bg, b_ag = tw.b_ag, b_od = tw.b_od;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  h.ensure(P.ws, al(b_n) + al(b_x) + al(b_o) + al(b_bg) + al(b_ag) + al(b_od) + 256);
+  h.ensure(P.ws, tw.total);
   char *w = (char *)P.ws.p;
   double *Nw = (double *)w;
   double *Xw = (double *)(w + al(b_n));
@@ -768,14 +809,12 @@ void chi0_run(Handle &h, double *ms_gemm) {
   const size_t n2 = (size_t)nao * nao;
   const size_t g_gstride = (size_t)ntau * nR * n2;
   h.ensure(h.d_chi_tau, (size_t)ntau * nR * naux * naux * sizeof(double));
-  // points per batch: bounded workspace (1 GiB, at least one point)
-  const long long per_point = 2 * (P.bg_sz + P.ag_sz + P.n_sz + P.x_sz) + P.o_sz;
   const std::vector<int> rl = chi0_r_list(h.mesh);
   const long long total_pts = (long long)ntau * rl.size();
-  long long npb = std::max<long long>(1, (1LL << 27) / std::max<long long>(1, per_point));
-  npb = std::min(npb, total_pts);
+  const DpWs dw = dp_ws(h, P);
+  const long long npb = dw.npb;
   DevBuf &ws = P.ws;
-  h.ensure(ws, (size_t)npb * per_point * sizeof(double));
+  h.ensure(ws, dw.total);
   double *Bg = (double *)ws.p;
   double *Ag = Bg + npb * 2 * P.bg_sz;
   double *Nw = Ag + npb * 2 * P.ag_sz;
@@ -837,6 +876,19 @@ void chi0_run(Handle &h, double *ms_gemm) {
   fill_partners(h);
   LR_CUDA(cudaStreamSynchronize(s));
   if (ms_gemm) *ms_gemm = 0;
+}
+
+size_t chi0_device_bytes(const Handle &h, const Chi0Plan &P) {
+  size_t b = (size_t)P.cp_total * 8;                                    // packed C
+  b += (size_t)h.ntau * h.mesh.size() * h.naux * h.naux * 8;            // chi0(R, tau)
+  b += h.chi0_S >= 0 ? tc_ws(h, P).total : dp_ws(h, P).total;           // batch workspace
+  if (h.chi0_S >= 0)                                                    // digit planes of C
+    b += oz::sliced_bytes(P.cpnx_rows, P.max_m, h.chi0_S) + oz::sliced_bytes(h.naux, P.max_nm, h.chi0_S);
+  // column tables and per-atom tables
+  size_t cols = 0;
+  for (int a = 0; a < h.natoms; ++a) cols += P.m[a];
+  b += (2 * cols + (size_t)P.m_all) * 6 * sizeof(int) + 16 * (size_t)(h.natoms + 1) * 8 + 12 * 256;
+  return b;
 }
 
 std::vector<int> chi0_r_list(const Mesh &m) {

@@ -280,33 +280,58 @@ void potrf_batched(Handle &h, double2 *const *d_mats, const std::vector<double2 
 
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
+// Workspace of the ln det stage: L[nq], W[nw], A[nw] (complex n x n), pointer tables,
+// lndet/trace/info, output, and for the tensor-core route the digit planes.
+struct EcLayout {
+  size_t o_L, o_W, o_A, o_ptr, o_ld, o_tr, o_inf, o_out, o_wo, o_err;
+  size_t o_sx = 0, o_sw = 0, o_sl = 0, o_slh = 0, o_pa = 0, o_pb = 0;
+  size_t total = 0;
+};
+
+EcLayout ec_layout(const Handle &h) {
+  const int n = h.naux, nq = h.mesh.size(), nw = h.ntau, S = h.ec_S;
+  const size_t n2 = (size_t)n * n, mat = n2 * sizeof(double2);
+  const int bmax = std::max(nq, nw);
+  EcLayout l;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += al256(bytes); return o; };
+  l.o_L = take(nq * mat);
+  l.o_W = take(nw * mat);
+  l.o_A = take(nw * mat);
+  l.o_ptr = take(((size_t)nq + nw + 8) * 8);
+  l.o_ld = take(((size_t)nq * nw + nq) * 8);
+  l.o_tr = take((size_t)nq * nw * 8);
+  l.o_inf = take((size_t)(nq + nq * nw) * 4);
+  l.o_out = take((size_t)(1 + nq + nw) * 8);
+  l.o_wo = take((size_t)nw * 8);
+  l.o_err = take(4);
+  if (S >= 0) {
+    l.o_sx = take(oz::sliced_bytes(nw * 2 * n, 2 * n, S));
+    l.o_sw = take(oz::sliced_bytes(nw * n, 2 * n, S));
+    l.o_sl = take(oz::sliced_bytes(n, 2 * n, S));
+    l.o_slh = take(oz::sliced_bytes(2 * n, 2 * n, S));
+    l.o_pa = take(oz::sliced_bytes(bmax * 2 * n, 2 * NB, S));
+    l.o_pb = take(oz::sliced_bytes(bmax * n, 2 * NB, S));
+  }
+  l.total = off;
+  return l;
+}
+
 }  // namespace
+
+size_t ec_work_bytes(const Handle &h) { return ec_layout(h).total; }
 
 int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   const int n = h.naux, nq = h.mesh.size(), nw = h.ntau, S = h.ec_S;
   const size_t n2 = (size_t)n * n;
   cudaStream_t s = h.stream;
-  // workspace: L[nq], W[nw], A[nw] (complex n x n), pointer tables, lndet/trace/info, output,
-  // and for the tensor-core route the digit planes
   const size_t mat = n2 * sizeof(double2);
   const int bmax = std::max(nq, nw);
-  size_t off = 0;
-  auto take = [&](size_t bytes) { const size_t o = off; off += al256(bytes); return o; };
-  const size_t o_L = take(nq * mat), o_W = take(nw * mat), o_A = take(nw * mat);
-  const size_t o_ptr = take(((size_t)nq + nw + 8) * 8);
-  const size_t o_ld = take(((size_t)nq * nw + nq) * 8), o_tr = take((size_t)nq * nw * 8);
-  const size_t o_inf = take((size_t)(nq + nq * nw) * 4), o_out = take((size_t)(1 + nq + nw) * 8);
-  const size_t o_wo = take((size_t)nw * 8), o_err = take(4);
-  size_t o_sx = 0, o_sw = 0, o_sl = 0, o_slh = 0, o_pa = 0, o_pb = 0;
-  if (S >= 0) {
-    o_sx = take(oz::sliced_bytes(nw * 2 * n, 2 * n, S));
-    o_sw = take(oz::sliced_bytes(nw * n, 2 * n, S));
-    o_sl = take(oz::sliced_bytes(n, 2 * n, S));
-    o_slh = take(oz::sliced_bytes(2 * n, 2 * n, S));
-    o_pa = take(oz::sliced_bytes(bmax * 2 * n, 2 * NB, S));
-    o_pb = take(oz::sliced_bytes(bmax * n, 2 * NB, S));
-  }
-  h.ensure(h.work, off);
+  const EcLayout lay = ec_layout(h);
+  const size_t o_L = lay.o_L, o_W = lay.o_W, o_A = lay.o_A, o_ptr = lay.o_ptr, o_ld = lay.o_ld, o_tr = lay.o_tr,
+               o_inf = lay.o_inf, o_out = lay.o_out, o_wo = lay.o_wo, o_err = lay.o_err, o_sx = lay.o_sx,
+               o_sw = lay.o_sw, o_sl = lay.o_sl, o_slh = lay.o_slh, o_pa = lay.o_pa, o_pb = lay.o_pb;
+  h.ensure(h.work, lay.total);
   char *w = (char *)h.work.p;
   double2 *Lq = (double2 *)(w + o_L), *Wm = (double2 *)(w + o_W), *Am = (double2 *)(w + o_A);
   double2 **ptrs = (double2 **)(w + o_ptr);

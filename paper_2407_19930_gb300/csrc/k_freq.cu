@@ -78,6 +78,12 @@ void launch_rq(const double *in, double2 *out, const double2 *ph, int nR, int nq
 
 }  // namespace
 
+size_t freq_work_bytes(const Handle &h) {
+  const size_t nR = h.mesh.size(), n2 = (size_t)h.naux * h.naux;
+  const size_t b_rw = (size_t)h.ntau * nR * n2 * 8, b_g = (size_t)h.ntau * h.ntau * 8, b_p = nR * nR * 16;
+  return b_rw + 256 + b_g + 256 + b_p;
+}
+
 void freq_transform(Handle &h) {
   const int ntau = h.ntau, nR = h.mesh.size(), nq = nR;
   const size_t n2 = (size_t)h.naux * h.naux;
@@ -86,7 +92,7 @@ void freq_transform(Handle &h) {
   h.ensure(h.d_chi_qw, (size_t)nq * ntau * n2 * 16);
   // workspace: chi0(R, i omega) plus the two small matrices
   const size_t b_rw = (size_t)ntau * nR * n2 * 8, b_g = (size_t)ntau * ntau * 8, b_p = (size_t)nq * nR * 16;
-  h.ensure(h.work, b_rw + 256 + b_g + 256 + b_p);
+  h.ensure(h.work, freq_work_bytes(h));
   char *w = (char *)h.work.p;
   double *rw = (double *)w;
   double *dg = (double *)(w + (b_rw + 255) / 256 * 256);

@@ -64,6 +64,13 @@ __global__ void k_phase_sum(const double2 *P, const double2 *twiddle, int nk, in
 
 }  // namespace
 
+size_t green_work_bytes(const Handle &h) {
+  const size_t nk = h.mesh.size(), nR = nk, nb = h.nao, n2 = (size_t)h.nao * h.nao;
+  const size_t b_e = nk * nb * 8, b_w = 2 * b_e, b_p = 2 * nk * n2 * 16, b_t = nk * nR * 16;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  return al(b_w) + al(b_p) + al(b_t) + 256;
+}
+
 double green_build(Handle &h) {
   const int nk = h.mesh.size(), nR = nk, nao = h.nao, nb = h.nao, ntau = h.ntau;
   const size_t n2 = (size_t)nao * nao;
@@ -74,8 +81,8 @@ double green_build(Handle &h) {
   const size_t b_e = (size_t)nk * nb * 8, b_w = 2 * b_e, b_p = 2 * (size_t)nk * n2 * 16,
                b_t = (size_t)nk * nR * 16;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t o_w = 0, o_p = o_w + al(b_w), o_t = o_p + al(b_p), o_m = o_t + al(b_t), total = o_m + 256;
-  h.ensure(h.work, total);
+  const size_t o_w = 0, o_p = o_w + al(b_w), o_t = o_p + al(b_p), o_m = o_t + al(b_t);
+  h.ensure(h.work, green_work_bytes(h));
   char *wk = (char *)h.work.p;
   const double2 *d_wfc = (const double2 *)h.d_wfc.p;
   const double *d_eig = (const double *)h.d_eig.p, *d_occ = (const double *)h.d_occ.p;

@@ -13,6 +13,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -486,13 +487,14 @@ void launch(const CUtensorMap &ma, const CUtensorMap &mb, const Entry *e, const 
 }  // namespace
 
 void init() {
-  if (g_encode) return;
-  void *fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-    throw Error{LIBRPA_E_CUDA, "cuTensorMapEncodeTiled entry point not available"};
-  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  static std::once_flag once;   // handles on several host threads (the serving loop) share it
+  std::call_once(once, [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e == cudaSuccess && q == cudaDriverEntryPointSuccess && fn) g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  });
+  if (!g_encode) throw Error{LIBRPA_E_CUDA, "cuTensorMapEncodeTiled entry point not available"};
 }
 
 size_t sliced_bytes(int rows, int K, int S) {

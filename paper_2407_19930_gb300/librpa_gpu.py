@@ -54,7 +54,24 @@ class librpa_gpu_stats(ctypes.Structure):
                 ("flop_gemm_ec", ctypes.c_double), ("n_gemm_ec", ctypes.c_longlong),
                 ("launches", ctypes.c_longlong),
                 ("bytes_device", ctypes.c_size_t), ("flop_exec_gemm_chi0", ctypes.c_double),
-                ("flop_exec_gemm_ec", ctypes.c_double)]
+                ("flop_exec_gemm_ec", ctypes.c_double), ("bytes_device_peak", ctypes.c_size_t)]
+
+
+class librpa_gpu_server_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("slots", ctypes.c_int), ("hbm_budget", ctypes.c_size_t)]
+
+
+class librpa_gpu_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("ec", ctypes.c_double), ("ms_queue", ctypes.c_double),
+                ("ms_run", ctypes.c_double), ("ms_total", ctypes.c_double), ("bytes_reserved", ctypes.c_size_t),
+                ("bytes_peak", ctypes.c_size_t), ("slot", ctypes.c_int)]
+
+
+class librpa_gpu_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_queue_ms", ctypes.c_double),
+                ("energies_per_s", ctypes.c_double), ("peak_running", ctypes.c_int),
+                ("peak_reserved", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t)]
 
 
 class LibrpaError(RuntimeError):
@@ -87,6 +104,16 @@ _SIGS = {
     "librpa_gpu_get_chi0_freq": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, _D, _D]),
     "librpa_gpu_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(librpa_gpu_stats)]),
     "librpa_gpu_last_error": (ctypes.c_char_p, [_H]),
+    "librpa_gpu_estimate_bytes": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_size_t)]),
+    "librpa_gpu_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p),
+                                                ctypes.POINTER(librpa_gpu_server_opts)]),
+    "librpa_gpu_server_request": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(librpa_gpu_opts),
+                                                 ctypes.POINTER(_H)]),
+    "librpa_gpu_server_submit": (ctypes.c_int, [ctypes.c_void_p, _H, ctypes.POINTER(ctypes.c_longlong)]),
+    "librpa_gpu_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double,
+                                              ctypes.POINTER(librpa_gpu_result)]),
+    "librpa_gpu_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(librpa_gpu_server_stats)]),
+    "librpa_gpu_server_destroy": (None, [ctypes.c_void_p]),
     "librpa_gpu_ec_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "librpa_gpu_destroy": (None, [_H]),
@@ -298,6 +325,62 @@ def librpa_gpu_ec_noalloc(naux, nomega, V, chi, out, stream=None):
     rc = load().librpa_gpu_ec_noalloc(int(naux), int(nomega), V, chi, out, stream, msg, len(msg))
     if rc != LIBRPA_OK:
         raise LibrpaError(rc, msg.value.decode())
+
+
+def librpa_gpu_estimate_bytes(h):
+    b = ctypes.c_size_t(0)
+    _check(h, load().librpa_gpu_estimate_bytes(h, ctypes.byref(b)))
+    return b.value
+
+
+def librpa_gpu_server_create(device=0, slots=2, hbm_budget=0):
+    o = librpa_gpu_server_opts(device, slots, hbm_budget)
+    s = ctypes.c_void_p()
+    rc = load().librpa_gpu_server_create(ctypes.byref(s), ctypes.byref(o))
+    if rc != LIBRPA_OK:
+        raise LibrpaError(rc, "server_create")
+    return s
+
+
+def librpa_gpu_server_request(s, opts=None):
+    """A request handle; fill it with the set_* calls (or set_inputs) and submit it."""
+    if opts is None:
+        opts = librpa_gpu_default_opts()
+    h = _H()
+    rc = load().librpa_gpu_server_request(s, ctypes.byref(opts), ctypes.byref(h))
+    if rc != LIBRPA_OK:
+        raise LibrpaError(rc, "server_request")
+    return h
+
+
+def librpa_gpu_server_submit(s, req):
+    t = ctypes.c_longlong(0)
+    _check(req, load().librpa_gpu_server_submit(s, req, ctypes.byref(t)))
+    return t.value
+
+
+def librpa_gpu_server_wait(s, ticket, timeout_s=-1.0):
+    """Returns the result as a dict, or None if it is not ready within timeout_s."""
+    r = librpa_gpu_result()
+    rc = load().librpa_gpu_server_wait(s, int(ticket), float(timeout_s), ctypes.byref(r))
+    if rc == LIBRPA_E_TIMEOUT:
+        return None
+    if rc != LIBRPA_OK:
+        raise LibrpaError(rc, "server_wait")
+    return {f: getattr(r, f) for f, _ in r._fields_}
+
+
+def librpa_gpu_server_get_stats(s):
+    st = librpa_gpu_server_stats()
+    rc = load().librpa_gpu_server_get_stats(s, ctypes.byref(st))
+    if rc != LIBRPA_OK:
+        raise LibrpaError(rc, "server_get_stats")
+    return {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def librpa_gpu_server_destroy(s):
+    if s:
+        load().librpa_gpu_server_destroy(s)
 
 
 def librpa_gpu_destroy(h):

@@ -364,3 +364,16 @@ def config_mixed(seed=11, kmesh=(2, 2, 1), vscale=6e-4) -> Inputs:
     rng = np.random.default_rng(seed)
     st = random_cell(rng, 4, kmesh)
     return make_inputs(st, seed, vscale=vscale)
+
+
+def config_request(index, natoms_range=(2, 64), seed_base=4004, vscale=2e-4) -> Inputs:
+    """Request ``index`` of the serving and batched workloads: a random cell of
+    U{natoms_range} atoms (species as in ``random_cell``), a k-mesh drawn from
+    1x1x1, 2x2x1 and 3x3x1, seeded by (seed_base, index).  ``vscale`` is one
+    conservative value for every size (the largest calibrated workloads above
+    need 3e-4 to 1e-3)."""
+    rng = np.random.default_rng([seed_base, index])
+    natoms = int(rng.integers(natoms_range[0], natoms_range[1] + 1))
+    kmesh = [(1, 1, 1), (2, 2, 1), (3, 3, 1)][int(rng.integers(0, 3))]
+    st = random_cell(rng, natoms, kmesh)
+    return make_inputs(st, seed_base * 1000 + index, vscale=vscale)

@@ -1,0 +1,116 @@
+"""Serving loop: continuous batching of RPA energy requests (the serving row of the survey's
+next items).  Each result in a mixed, overlapping batch must equal the same request run alone,
+and the device-memory estimate used for admission must bound the memory actually held."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2407_19930_gb300 import librpa_gpu as L
+from oracle import grid as ogrid
+
+from test_gpu_parity import CONFIGS, _opts
+
+pytestmark = pytest.mark.gpu
+
+# (config, precision): FP64, the FP64-accurate tensor-core mode and the mixed mode side by side
+MIX = [("tiny", L.LIBRPA_FP64), ("cubic", L.LIBRPA_FP64), ("mixed", L.LIBRPA_SPLIT),
+       ("cubic_3x1x2", L.LIBRPA_FP64_TC), ("one_atom_gamma", L.LIBRPA_FP64), ("cubic_3x3x1", L.LIBRPA_SPLIT),
+       ("cubic", L.LIBRPA_FP64_TC), ("mixed", L.LIBRPA_FP64)]
+
+
+def _grid(name, inp):
+    return ogrid.make_grid(8 if name != "mixed" else 10, *inp.delta_range)
+
+
+def _alone(inp, grid, precision):
+    h = L.librpa_gpu_create(_opts(precision))
+    try:
+        L.set_inputs(h, inp, grid)
+        est = L.librpa_gpu_estimate_bytes(h)
+        L.librpa_gpu_chi0(h)
+        ec, _, _ = L.librpa_gpu_ec(h)
+        peak = L.librpa_gpu_get_stats(h)["bytes_device_peak"]
+    finally:
+        L.librpa_gpu_destroy(h)
+    return ec, est, peak
+
+
+@pytest.fixture(scope="module")
+def alone():
+    out = []
+    for name, prec in MIX:
+        inp = CONFIGS[name]()
+        grid = _grid(name, inp)
+        out.append((name, prec, inp, grid) + _alone(inp, grid, prec))
+    return out
+
+
+def test_estimate_bounds_the_device_footprint(alone):
+    for name, prec, inp, grid, ec, est, peak in alone:
+        assert 0 < peak <= est, (name, prec, peak, est)
+
+
+def test_mix_equals_alone(alone):
+    ests = sorted(a[5] for a in alone)
+    budget = ests[-1] + ests[-2] + ests[-3]   # at most three of the largest at once: requests must wait
+    s = L.librpa_gpu_server_create(slots=3, hbm_budget=budget)
+    reqs = []
+    try:
+        tickets = []
+        for name, prec, inp, grid, ec, est, peak in alone:
+            r = L.librpa_gpu_server_request(s, _opts(prec))
+            reqs.append(r)
+            L.set_inputs(r, inp, grid)
+            tickets.append(L.librpa_gpu_server_submit(s, r))
+        res = [L.librpa_gpu_server_wait(s, t, 300.0) for t in tickets]
+        st = L.librpa_gpu_server_get_stats(s)
+    finally:
+        L.librpa_gpu_server_destroy(s)
+        for r in reqs:
+            L.librpa_gpu_destroy(r)
+    for (name, prec, inp, grid, ec, est, peak), r in zip(alone, res):
+        assert r is not None and r["status"] == L.LIBRPA_OK, (name, r)
+        assert abs(r["ec"] - ec) <= 1e-12 * abs(ec), (name, prec, r["ec"], ec)
+        assert r["bytes_peak"] <= r["bytes_reserved"] == est
+        assert r["ms_total"] >= r["ms_run"] > 0
+    assert st["completed"] == len(alone) and st["failed"] == 0
+    assert st["peak_running"] >= 2            # requests overlapped on the device
+    assert st["peak_reserved"] <= budget
+    assert 0 < st["p50_ms"] <= st["p99_ms"]
+
+
+def test_request_larger_than_the_budget_is_refused():
+    inp = CONFIGS["cubic"]()
+    s = L.librpa_gpu_server_create(slots=1, hbm_budget=1 << 20)
+    r = L.librpa_gpu_server_request(s, _opts(L.LIBRPA_FP64))
+    try:
+        L.set_inputs(r, inp, _grid("cubic", inp))
+        with pytest.raises(L.LibrpaError) as e:
+            L.librpa_gpu_server_submit(s, r)
+        assert e.value.code == L.LIBRPA_E_NOMEM
+    finally:
+        L.librpa_gpu_server_destroy(s)
+        L.librpa_gpu_destroy(r)
+
+
+def test_requests_arriving_while_others_run_are_admitted():
+    """A second wave submitted while the first is on the GPU is admitted as slots free up."""
+    s = L.librpa_gpu_server_create(slots=2)
+    reqs, tickets = [], []
+    try:
+        for wave in range(2):
+            for name in ("cubic", "mixed"):
+                inp = CONFIGS[name]()
+                r = L.librpa_gpu_server_request(s, _opts(L.LIBRPA_SPLIT))
+                reqs.append(r)
+                L.set_inputs(r, inp, _grid(name, inp))
+                tickets.append(L.librpa_gpu_server_submit(s, r))
+            time.sleep(0.05)
+        res = [L.librpa_gpu_server_wait(s, t, 300.0) for t in tickets]
+    finally:
+        L.librpa_gpu_server_destroy(s)
+        for r in reqs:
+            L.librpa_gpu_destroy(r)
+    assert all(r["status"] == L.LIBRPA_OK for r in res)
+    assert res[0]["ec"] == res[2]["ec"] and res[1]["ec"] == res[3]["ec"]
