@@ -256,6 +256,42 @@ int librpa_gpu_get_chi0_freq(librpa_gpu_t h, int iq, int iomega, double *re, dou
 /* Stage timings and counters of the last chi0 / ec calls. Errors: E_ARG. */
 int librpa_gpu_get_stats(librpa_gpu_t h, librpa_gpu_stats *s);
 
+/* ---------------------------------------------------------------- batched energies
+ * Many independent structures in one pass (not in the paper, which computes one system
+ * per call).  Every handle must be filled (set_* calls) before librpa_gpu_batch_run.
+ * All handles run on the first handle's stream.  In the FP64 mode, the chi0 contraction
+ * of every handle whose points fit one workspace batch runs as single grouped GEMM launches
+ * over all handles' tiles, which have uneven shapes.  The GEMM tile shape is picked by
+ * timing the variants on the first run; from the second run on, that launch sequence is
+ * replayed from a CUDA graph.  The other handles (tensor-core modes, structures too
+ * large for one batch) run their own chi0 path in the same pass.  G, the transforms and
+ * the ln det stage run per handle.  While a batch exists, run its handles only through
+ * the batch.  After changing a handle's LRI blocks or structure, the next run re-plans
+ * and captures again.  Destroy the batch before its handles. */
+typedef struct librpa_gpu_batch *librpa_gpu_batch_t;
+
+typedef struct {
+  int n, n_merged;         /* handles; handles whose chi0 ran in the merged launches */
+  int graph;               /* 1 if the last run replayed the captured graph */
+  int var_nx, var_fin;     /* FP64 GEMM tile variants chosen: 0 = 64x64, 1 = 32x64, 2 = 64x32,
+                              3 = 32x32, 4 = 128x64 (M x N); -1 = none */
+  int failed_index;        /* handle of the last error (its last_error has the message), or -1 */
+  double ms_green, ms_chi0, ms_freq, ms_ec, ms_total;   /* device time of the last run */
+  long long launches;      /* kernel launches of the last run (graph nodes included) */
+} librpa_gpu_batch_stats;
+
+/* Group n distinct handles of one device.  Errors: E_ARG, E_NOMEM. */
+int librpa_gpu_batch_create(librpa_gpu_batch_t *b, librpa_gpu_t *hs, int n);
+
+/* E_c of every handle into ec[n] (Ha per cell).  Errors: those of librpa_gpu_chi0 and
+ * librpa_gpu_ec, for the handle in stats.failed_index. */
+int librpa_gpu_batch_run(librpa_gpu_batch_t b, double *ec);
+
+int librpa_gpu_batch_get_stats(librpa_gpu_batch_t b, librpa_gpu_batch_stats *st);
+
+/* Free the batch's graph and descriptor buffers (not its handles).  NULL is ignored. */
+void librpa_gpu_batch_destroy(librpa_gpu_batch_t b);
+
 /* ---------------------------------------------------------------- serving loop
  * Continuous batching of RPA energy requests on one GPU (not in the paper, whose
  * library computes one system per call; each request runs the same path as

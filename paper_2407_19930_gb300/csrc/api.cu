@@ -169,6 +169,45 @@ size_t estimate_device_bytes(Handle &h) {
   return b;
 }
 
+int chi0_prepare(Handle &h) {
+  if (!h.have_structure) return fail(&h, LIBRPA_E_STATE, "chi0 before set_structure");
+  for (int k = 0; k < h.mesh.size(); ++k)
+    if (!h.have_k[k]) return fail(&h, LIBRPA_E_STATE, "chi0: set_green missing for k index " + std::to_string(k));
+  {
+    std::vector<char> seen(h.natoms, 0);
+    for (auto &kv : h.lri) seen[std::get<0>(kv.first)] = 1;
+    for (int a = 0; a < h.natoms; ++a)
+      if (!seen[a]) return fail(&h, LIBRPA_E_STATE, "chi0: no LRI block for atom " + std::to_string(a));
+  }
+  for (int k = 1; k < h.mesh.size(); ++k)
+    if (h.efermi_k[k] != h.efermi_k[0]) return fail(&h, LIBRPA_E_ARG, "chi0: efermi differs between k points");
+  cudaSetDevice(h.opts.device);
+  if (!h.have_grid) {
+    // transition-energy range of the KS spectrum: smallest virtual minus largest
+    // occupied energy, and largest virtual minus smallest occupied energy
+    const int nb = h.nao, nk = h.mesh.size();
+    double eo_max = -1e300, eo_min = 1e300, ev_min = 1e300, ev_max = -1e300;
+    for (int k = 0; k < nk; ++k)
+      for (int n = 0; n < nb; ++n) {
+        double e = h.eig[(size_t)k * nb + n], f = h.occ[(size_t)k * nb + n];
+        if (f > 0) { eo_max = std::fmax(eo_max, e); eo_min = std::fmin(eo_min, e); }
+        if (f < 1) { ev_min = std::fmin(ev_min, e); ev_max = std::fmax(ev_max, e); }
+      }
+    double dmin = ev_min - eo_max, dmax = ev_max - eo_min;
+    if (!(dmin > 0)) return fail(&h, LIBRPA_E_ARG, "chi0: no gap between occupied and virtual states");
+    int n = h.opts.n_tau;
+    h.tau.resize(n);
+    h.omega.resize(n);
+    h.w_omega.resize(n);
+    h.gamma.resize((size_t)n * n);
+    int rc = build_grid(n, dmin, dmax, h.tau.data(), h.omega.data(), h.w_omega.data(), h.gamma.data());
+    if (rc) return fail(&h, rc, "chi0: grid construction failed");
+    h.ntau = n;
+    h.have_grid = true;
+  }
+  return LIBRPA_OK;
+}
+
 }  // namespace librpa
 
 using namespace librpa;
@@ -412,41 +451,7 @@ int librpa_gpu_get_grid(librpa_gpu_t h, int *n, double *tau, double *omega, doub
 
 int librpa_gpu_chi0(librpa_gpu_t h, double *out_re, double *out_im) {
   return guarded(h, [&]() -> int {
-    if (!h->have_structure) return fail(h, LIBRPA_E_STATE, "chi0 before set_structure");
-    for (int k = 0; k < h->mesh.size(); ++k)
-      if (!h->have_k[k]) return fail(h, LIBRPA_E_STATE, "chi0: set_green missing for k index " + std::to_string(k));
-    {
-      std::vector<char> seen(h->natoms, 0);
-      for (auto &kv : h->lri) seen[std::get<0>(kv.first)] = 1;
-      for (int a = 0; a < h->natoms; ++a)
-        if (!seen[a]) return fail(h, LIBRPA_E_STATE, "chi0: no LRI block for atom " + std::to_string(a));
-    }
-    for (int k = 1; k < h->mesh.size(); ++k)
-      if (h->efermi_k[k] != h->efermi_k[0]) return fail(h, LIBRPA_E_ARG, "chi0: efermi differs between k points");
-    cudaSetDevice(h->opts.device);
-    if (!h->have_grid) {
-      // transition-energy range of the KS spectrum: smallest virtual minus largest
-      // occupied energy, and largest virtual minus smallest occupied energy
-      const int nb = h->nao, nk = h->mesh.size();
-      double eo_max = -1e300, eo_min = 1e300, ev_min = 1e300, ev_max = -1e300;
-      for (int k = 0; k < nk; ++k)
-        for (int n = 0; n < nb; ++n) {
-          double e = h->eig[(size_t)k * nb + n], f = h->occ[(size_t)k * nb + n];
-          if (f > 0) { eo_max = std::fmax(eo_max, e); eo_min = std::fmin(eo_min, e); }
-          if (f < 1) { ev_min = std::fmin(ev_min, e); ev_max = std::fmax(ev_max, e); }
-        }
-      double dmin = ev_min - eo_max, dmax = ev_max - eo_min;
-      if (!(dmin > 0)) return fail(h, LIBRPA_E_ARG, "chi0: no gap between occupied and virtual states");
-      int n = h->opts.n_tau;
-      h->tau.resize(n);
-      h->omega.resize(n);
-      h->w_omega.resize(n);
-      h->gamma.resize((size_t)n * n);
-      int rc = build_grid(n, dmin, dmax, h->tau.data(), h->omega.data(), h->w_omega.data(), h->gamma.data());
-      if (rc) return fail(h, rc, "chi0: grid construction failed");
-      h->ntau = n;
-      h->have_grid = true;
-    }
+    if (int rc = chi0_prepare(*h)) return rc;
     materialize(*h);
     h->stats = librpa_gpu_stats{};
     long long l0 = launch_counter();

@@ -81,6 +81,10 @@ struct Chi0Plan {
   // (rows (nu, j) per atom with K = m_V for the N and X steps; rows mu with K = n_U m_U for
   // the final contraction), the planes' shape, and the ragged-entry tables of the O operand
   int tc_S = 0, max_m = 0, max_nm = 0, cpnx_rows = 0;
+  // FP64 route: tile variants of the N/X and final GEMM launches (-1 = tune on first use), and a
+  // generation number bumped by every re-plan (batched runs key their captured graphs on it)
+  int var_nx = -1, var_fin = -1;
+  long long gen = 0;
   std::vector<int> cpnx_off;
   DevBuf cp_nx, cp_f, t_oe_off, t_oe_k, gargs3;
   std::vector<DevBuf *> all() {
@@ -178,6 +182,24 @@ void chi0_shape(const Handle &h, Chi0Plan &P);
 // device bytes the chi0 stage holds for this shape (packed C and its digit planes, chi0(R, tau),
 // batch workspace, tables)
 size_t chi0_device_bytes(const Handle &h, const Chi0Plan &P);
+// Batched chi0 of several handles (FP64 route, all points of each handle in one batch): the
+// N/X and final GEMMs of all handles as single grouped launches on hs[0]'s stream; the launch
+// sequence is captured in a CUDA graph on the first call and replayed while no plan changes.
+struct MergedChi0 {
+  std::vector<Handle *> hs;
+  std::vector<long long> gens;
+  DevBuf nx_args, fin_args;   // allocated through hs[0]
+  int var_nx = -1, var_fin = -1;
+  cudaGraphExec_t exec = nullptr;
+  long long nodes = 0;
+  bool graph_failed = false;
+  void reset();
+};
+// returns true when the launches were replayed from the captured graph
+bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m);
+// whether h's FP64 route holds all its points in one batch (a condition of chi0_run_merged)
+bool chi0_fits_one_batch(const Handle &h);
+
 // lattice vectors R whose chi0(R, tau) is computed (R <= -R in the flat BvK order); the others
 // are filled as chi0(-R, tau)^T
 std::vector<int> chi0_r_list(const Mesh &m);
@@ -190,6 +212,9 @@ size_t ec_work_bytes(const Handle &h);
 
 // api.cu: upload the deferred inputs of h; release every device buffer of h; an upper bound of
 // the device bytes h holds during chi0 + ec (grid size from the user grid or opts.n_tau)
+// checks before the chi0 stage (inputs complete, one Fermi level) and the grid from the KS
+// spectrum when none was set; returns LIBRPA_OK or an error code with h.last_error set
+int chi0_prepare(Handle &h);
 void materialize(Handle &h);
 void release_device(Handle &h);
 size_t estimate_device_bytes(Handle &h);

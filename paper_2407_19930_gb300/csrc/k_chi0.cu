@@ -44,7 +44,7 @@ struct DTile {
   int e, m0, n0;
 };
 
-constexpr int GM = 64, GN = 64, GK = 16, GT = 128, GPAD = GK + 1;
+constexpr int GK = 16, GPAD = GK + 1;
 
 __device__ __forceinline__ void dmma_m8n8k4(double &c0, double &c1, double a, double b) {
   asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
@@ -52,13 +52,19 @@ __device__ __forceinline__ void dmma_m8n8k4(double &c0, double &c1, double a, do
                : "d"(a), "d"(b));
 }
 
-__global__ void __launch_bounds__(GT) k_dgemm_nt(const DGemm *__restrict__ gs, const DTile *__restrict__ tiles) {
+// CTA tile (32 WM) x (32 WN), one 32 x 32 warp tile per warp, K staged 16 at a time through
+// shared memory.  Every variant accumulates each output element over K in the same order
+// (chunks of 16, m8n8k4 steps of 4), so the tile shape never changes the result.
+template <int WM, int WN>
+__global__ void __launch_bounds__(32 * WM * WN) k_dgemm_nt(const DGemm *__restrict__ gs,
+                                                           const DTile *__restrict__ tiles) {
+  constexpr int BM = 32 * WM, BN = 32 * WN, NT = 32 * WM * WN;
   const DTile t = tiles[blockIdx.x];
   const DGemm g = gs[t.e];
-  __shared__ double As[GM][GPAD];
-  __shared__ double Bs[GN][GPAD];
+  __shared__ double As[BM][GPAD];
+  __shared__ double Bs[BN][GPAD];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;
+  const int wm = warp / WN, wn = warp % WN;
   const int gid = lane >> 2, tig = lane & 3;
   double acc[4][4][2];
 #pragma unroll
@@ -67,10 +73,13 @@ __global__ void __launch_bounds__(GT) k_dgemm_nt(const DGemm *__restrict__ gs, c
     for (int c = 0; c < 4; ++c) acc[r][c][0] = acc[r][c][1] = 0.0;
   for (int k0 = 0; k0 < g.K; k0 += GK) {
 #pragma unroll
-    for (int s = 0; s < (GM * GK) / GT; ++s) {
-      const int e = tid + GT * s, row = e / GK, k = e % GK;
-      const int gm = t.m0 + row, gn = t.n0 + row, gk = k0 + k;
+    for (int e = tid; e < BM * GK; e += NT) {
+      const int row = e / GK, k = e % GK, gm = t.m0 + row, gk = k0 + k;
       As[row][k] = (gm < g.M && gk < g.K) ? g.A[(size_t)gm * g.lda + gk] : 0.0;
+    }
+#pragma unroll
+    for (int e = tid; e < BN * GK; e += NT) {
+      const int row = e / GK, k = e % GK, gn = t.n0 + row, gk = k0 + k;
       Bs[row][k] = (gn < g.N && gk < g.K) ? g.B[(size_t)gn * g.ldb + gk] : 0.0;
     }
     __syncthreads();
@@ -102,6 +111,21 @@ __global__ void __launch_bounds__(GT) k_dgemm_nt(const DGemm *__restrict__ gs, c
         const double v = g.alpha * acc[r][c][h];
         *p = g.beta == 0.0 ? v : v + g.beta * *p;
       }
+  }
+}
+
+// tile variants {WM, WN}: 64x64 first (the default before tuning)
+constexpr int kNumVariants = 5;
+constexpr int kVarWM[kNumVariants] = {2, 1, 2, 1, 4};
+constexpr int kVarWN[kNumVariants] = {2, 2, 1, 1, 2};
+
+void launch_dgemm_variant(int v, unsigned ntiles, const DGemm *g, const DTile *t, cudaStream_t s) {
+  switch (v) {
+    case 0: k_dgemm_nt<2, 2><<<ntiles, 128, 0, s>>>(g, t); break;
+    case 1: k_dgemm_nt<1, 2><<<ntiles, 64, 0, s>>>(g, t); break;
+    case 2: k_dgemm_nt<2, 1><<<ntiles, 64, 0, s>>>(g, t); break;
+    case 3: k_dgemm_nt<1, 1><<<ntiles, 32, 0, s>>>(g, t); break;
+    default: k_dgemm_nt<4, 2><<<ntiles, 256, 0, s>>>(g, t); break;
   }
 }
 
@@ -310,32 +334,87 @@ T *upload(Handle &h, DevBuf &b, const std::vector<T> &v) {
   return (T *)b.p;
 }
 
-void dgemm_batched(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, DevBuf &args) {
+// Descriptors and tiles of one grouped FP64 GEMM launch, resident on the device, so that the
+// launch can be repeated or captured in a CUDA graph.
+struct DLaunch {
+  const DGemm *g = nullptr;
+  const DTile *t = nullptr;
+  unsigned ntiles = 0;
+  int v = 0;
+  double flops = 0;
+};
+
+DLaunch dgemm_prepare(Handle &h, const std::vector<DGemm> &batch, int v, cudaStream_t s, DevBuf &args) {
+  const int BM = 32 * kVarWM[v], BN = 32 * kVarWN[v];
   std::vector<DTile> tiles;
-  for (int e = 0; e < (int)batch.size(); ++e)
-    for (int m0 = 0; m0 < batch[e].M; m0 += GM)
-      for (int n0 = 0; n0 < batch[e].N; n0 += GN) tiles.push_back({e, m0, n0});
-  if (tiles.empty()) return;
+  DLaunch L;
+  L.v = v;
+  for (int e = 0; e < (int)batch.size(); ++e) {
+    L.flops += 2.0 * batch[e].M * batch[e].N * batch[e].K;
+    for (int m0 = 0; m0 < batch[e].M; m0 += BM)
+      for (int n0 = 0; n0 < batch[e].N; n0 += BN) tiles.push_back({e, m0, n0});
+  }
+  if (tiles.empty()) return L;
   const size_t b1 = batch.size() * sizeof(DGemm), off2 = (b1 + 255) / 256 * 256, b2 = tiles.size() * sizeof(DTile);
   std::vector<char> host(off2 + b2);
   std::memcpy(host.data(), batch.data(), b1);
   std::memcpy(host.data() + off2, tiles.data(), b2);
   h.ensure(args, off2 + b2);
   LR_CUDA(cudaMemcpyAsync(args.p, host.data(), off2 + b2, cudaMemcpyHostToDevice, s));
-  double flops = 0;
-  for (const DGemm &g : batch) flops += 2.0 * g.M * g.N * g.K;
-  Handle::Timed t{nullptr, nullptr, flops, 0};
-  LR_CUDA(cudaEventCreate(&t.a));
-  LR_CUDA(cudaEventCreate(&t.b));
-  LR_CUDA(cudaEventRecord(t.a, s));
-  k_dgemm_nt<<<(unsigned)tiles.size(), GT, 0, s>>>((const DGemm *)args.p,
-                                                   (const DTile *)((const char *)args.p + off2));
-  LR_CUDA(cudaEventRecord(t.b, s));
-  h.timed.push_back(t);
-  ++launch_counter();
-  LR_CUDA(cudaGetLastError());
+  LR_CUDA(cudaStreamSynchronize(s));   // the host staging goes out of scope
+  L.g = (const DGemm *)args.p;
+  L.t = (const DTile *)((const char *)args.p + off2);
+  L.ntiles = (unsigned)tiles.size();
+  return L;
 }
 
+void dgemm_launch(Handle &h, const DLaunch &L, cudaStream_t s, bool timed) {
+  if (!L.ntiles) return;
+  Handle::Timed t{nullptr, nullptr, L.flops, 0};
+  if (timed) {
+    LR_CUDA(cudaEventCreate(&t.a));
+    LR_CUDA(cudaEventCreate(&t.b));
+    LR_CUDA(cudaEventRecord(t.a, s));
+  }
+  launch_dgemm_variant(L.v, L.ntiles, L.g, L.t, s);
+  ++launch_counter();
+  LR_CUDA(cudaGetLastError());
+  if (timed) {
+    LR_CUDA(cudaEventRecord(t.b, s));
+    h.timed.push_back(t);
+  }
+}
+
+int dgemm_autotune(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, DevBuf &args) {
+  for (const DGemm &g : batch)
+    if (g.beta != 0.0) return 0;   // repeated runs would accumulate into C
+  int best = 0;
+  float best_ms = 1e30f;
+  cudaEvent_t a, b;
+  LR_CUDA(cudaEventCreate(&a));
+  LR_CUDA(cudaEventCreate(&b));
+  for (int v = 0; v < kNumVariants; ++v) {
+    const DLaunch L = dgemm_prepare(h, batch, v, s, args);
+    LR_CUDA(cudaEventRecord(a, s));
+    dgemm_launch(h, L, s, false);
+    LR_CUDA(cudaEventRecord(b, s));
+    LR_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    LR_CUDA(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+void dgemm_batched(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, DevBuf &args, int *var) {
+  if (*var < 0) *var = dgemm_autotune(h, batch, s, args);
+  dgemm_launch(h, dgemm_prepare(h, batch, *var, s, args), s, true);
+}
 
 }  // namespace
 
@@ -425,6 +504,8 @@ void chi0_shape(const Handle &h, Chi0Plan &P) {
 void chi0_plan(Handle &h) {
   Chi0Plan &P = h.plan;
   chi0_shape(h, P);
+  P.var_nx = P.var_fin = -1;
+  ++P.gen;
   const int nat = h.natoms;
   std::vector<double> cp(P.cp_total, 0.0);
   for (int U = 0; U < nat; ++U) {
@@ -624,6 +705,78 @@ void timed_grouped(Handle &h, const oz::Sliced &a, const oz::Sliced &b, const st
   h.timed.push_back(t);
 }
 
+// FP64 route, one batch of np points whose workspace starts at P.ws: gathered G operands Bg, Ag,
+// the N- and X-step results, and O.
+struct Fp64Ws {
+  double *Bg, *Ag, *Nw, *Xw, *Ow;
+};
+
+Fp64Ws fp64_ws(Handle &h, long long npb) {
+  const Chi0Plan &P = h.plan;
+  Fp64Ws w;
+  w.Bg = (double *)P.ws.p;
+  w.Ag = w.Bg + npb * 2 * P.bg_sz;
+  w.Nw = w.Ag + npb * 2 * P.ag_sz;
+  w.Xw = w.Nw + npb * 2 * P.n_sz;
+  w.Ow = w.Xw + npb * 2 * P.x_sz;
+  return w;
+}
+
+void fp64_gather(Handle &h, const Point *dpts, int np, const Fp64Ws &w) {
+  const Chi0Plan &P = h.plan;
+  const int nat = h.natoms, nR = h.mesh.size(), nao = h.nao;
+  const size_t g_gstride = (size_t)h.ntau * nR * nao * nao;
+  int max_m = 0;
+  for (int a = 0; a < nat; ++a) max_m = std::max(max_m, P.m[a]);
+  dim3 grid((unsigned)(((long long)P.m_all * max_m + 255) / 256), (unsigned)(np * 2 * nat));
+  k_gather_bg<<<grid, 256, 0, h.stream>>>((const double *)h.d_g.p, g_gstride, dpts, (const int *)P.d_uni.p,
+                                          (const int *)P.d_lam.p, (const long long *)P.t_lam_off.p,
+                                          (const int *)P.t_m.p, (const long long *)P.t_bg_off.p, nat, P.m_all, nR,
+                                          nao, h.mesh.n1, h.mesh.n2, h.mesh.n3, P.bg_sz, 2 * P.bg_sz, w.Bg);
+  dim3 grid2((unsigned)(((long long)nao * max_m + 255) / 256), (unsigned)(np * 2 * nat));
+  k_gather_ag<<<grid2, 256, 0, h.stream>>>((const double *)h.d_g.p, g_gstride, dpts, (const int *)P.d_lam.p,
+                                           (const long long *)P.t_lam_off.p, (const int *)P.t_m.p,
+                                           (const long long *)P.t_ag_off.p, nat, nR, nao, h.mesh.n1, h.mesh.n2,
+                                           h.mesh.n3, P.ag_sz, 2 * P.ag_sz, w.Ag);
+  launch_counter() += 2;
+  LR_CUDA(cudaGetLastError());
+}
+
+// N- and X-step descriptors of np points (appended to b)
+void fp64_nx(Handle &h, int np, const Fp64Ws &w, std::vector<DGemm> &b) {
+  const Chi0Plan &P = h.plan;
+  const double *Cp = (const double *)h.d_cpack.p;
+  for (int q = 0; q < np; ++q)
+    for (int g = 0; g < 2; ++g)
+      for (int V = 0; V < h.natoms; ++V) {
+        const int rowsV = h.n_aux[V] * h.n_ao[V], mV = P.m[V];
+        DGemm dn{Cp + P.cp_off[V], w.Bg + (size_t)q * 2 * P.bg_sz + g * P.bg_sz + P.bg_off[V],
+                 w.Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V], rowsV, P.m_all, mV, mV, mV, P.m_all,
+                 1.0, 0.0};
+        b.push_back(dn);
+        DGemm dx{w.Ag + (size_t)q * 2 * P.ag_sz + g * P.ag_sz + P.ag_off[V], Cp + P.cp_off[V],
+                 w.Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V], h.nao, rowsV, mV, mV, mV, rowsV, 1.0, 0.0};
+        b.push_back(dx);
+      }
+}
+
+// final contraction chi0(R, tau)[U rows] = -s Cpack_U O_U^T of the points (appended to b)
+void fp64_final(Handle &h, const std::vector<Point> &pts, const Fp64Ws &w, std::vector<DGemm> &b) {
+  const Chi0Plan &P = h.plan;
+  const double *Cp = (const double *)h.d_cpack.p;
+  const int naux = h.naux, nR = h.mesh.size();
+  const double spin = 2.0;
+  for (size_t q = 0; q < pts.size(); ++q) {
+    double *chi = (double *)h.d_chi_tau.p + ((size_t)pts[q].itau * nR + pts[q].iR) * naux * naux;
+    for (int U = 0; U < h.natoms; ++U) {
+      const int K = h.n_ao[U] * P.m[U];
+      DGemm df{Cp + P.cp_off[U], w.Ow + q * P.o_sz + P.o_off[U], chi + (size_t)h.aux_off[U] * naux, h.n_aux[U],
+               naux, K, K, K, naux, -spin, 0.0};
+      b.push_back(df);
+    }
+  }
+}
+
 // Workspace of the tensor-core route for a batch of npb points: FP64 N, X, O and the digit planes
 // of Bg, Ag and O (bounded by 2 GiB, at least one point).
 struct TcWs {
@@ -804,78 +957,133 @@ void chi0_run(Handle &h, double *ms_gemm) {
     return;
   }
   Chi0Plan &P = h.plan;
-  const int nat = h.natoms, nR = h.mesh.size(), ntau = h.ntau, naux = h.naux, nao = h.nao;
+  const int nR = h.mesh.size(), ntau = h.ntau, naux = h.naux;
   cudaStream_t s = h.stream;
-  const size_t n2 = (size_t)nao * nao;
-  const size_t g_gstride = (size_t)ntau * nR * n2;
   h.ensure(h.d_chi_tau, (size_t)ntau * nR * naux * naux * sizeof(double));
   const std::vector<int> rl = chi0_r_list(h.mesh);
   const long long total_pts = (long long)ntau * rl.size();
   const DpWs dw = dp_ws(h, P);
   const long long npb = dw.npb;
-  DevBuf &ws = P.ws;
-  h.ensure(ws, dw.total);
-  double *Bg = (double *)ws.p;
-  double *Ag = Bg + npb * 2 * P.bg_sz;
-  double *Nw = Ag + npb * 2 * P.ag_sz;
-  double *Xw = Nw + npb * 2 * P.n_sz;
-  double *Ow = Xw + npb * 2 * P.x_sz;
-  const double *Cp = (const double *)h.d_cpack.p;
-  const double spin = 2.0;
-  int max_m = 0;
-  for (int a = 0; a < nat; ++a) max_m = std::max(max_m, P.m[a]);
+  h.ensure(P.ws, dw.total);
+  const Fp64Ws w = fp64_ws(h, npb);
   for (long long p0 = 0; p0 < total_pts; p0 += npb) {
     const int np = (int)std::min(npb, total_pts - p0);
     std::vector<Point> pts = make_points(h, rl, p0, np);
     h.ensure(P.t_pts, np * sizeof(Point));
     LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
     const Point *dpts = (const Point *)P.t_pts.p;
-    {
-      dim3 grid((unsigned)(((long long)P.m_all * max_m + 255) / 256), (unsigned)(np * 2 * nat));
-      k_gather_bg<<<grid, 256, 0, s>>>((const double *)h.d_g.p, g_gstride, dpts, (const int *)P.d_uni.p,
-                                       (const int *)P.d_lam.p, (const long long *)P.t_lam_off.p, (const int *)P.t_m.p,
-                                       (const long long *)P.t_bg_off.p, nat, P.m_all, nR, nao, h.mesh.n1, h.mesh.n2,
-                                       h.mesh.n3, P.bg_sz, 2 * P.bg_sz, Bg);
-      dim3 grid2((unsigned)(((long long)nao * max_m + 255) / 256), (unsigned)(np * 2 * nat));
-      k_gather_ag<<<grid2, 256, 0, s>>>((const double *)h.d_g.p, g_gstride, dpts, (const int *)P.d_lam.p,
-                                        (const long long *)P.t_lam_off.p, (const int *)P.t_m.p,
-                                        (const long long *)P.t_ag_off.p, nat, nR, nao, h.mesh.n1, h.mesh.n2,
-                                        h.mesh.n3, P.ag_sz, 2 * P.ag_sz, Ag);
-      launch_counter() += 2;
-      LR_CUDA(cudaGetLastError());
-    }
-    // N- and X-steps
-    std::vector<DGemm> b1;
-    for (int q = 0; q < np; ++q)
-      for (int g = 0; g < 2; ++g)
-        for (int V = 0; V < nat; ++V) {
-          const int rowsV = h.n_aux[V] * h.n_ao[V], mV = P.m[V];
-          DGemm dn{Cp + P.cp_off[V], Bg + (size_t)q * 2 * P.bg_sz + g * P.bg_sz + P.bg_off[V],
-                   Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V], rowsV, P.m_all, mV, mV, mV, P.m_all,
-                   1.0, 0.0};
-          b1.push_back(dn);
-          DGemm dx{Ag + (size_t)q * 2 * P.ag_sz + g * P.ag_sz + P.ag_off[V], Cp + P.cp_off[V],
-                   Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V], nao, rowsV, mV, mV, mV, rowsV, 1.0, 0.0};
-          b1.push_back(dx);
-        }
-    dgemm_batched(h, b1, s, P.gargs1);
-    run_oassemble(h, dpts, np, Nw, Xw, Ow);
-    // final contraction into chi0(R, tau)
-    std::vector<DGemm> b2;
-    for (int q = 0; q < np; ++q) {
-      double *chi = (double *)h.d_chi_tau.p + ((size_t)pts[q].itau * nR + pts[q].iR) * naux * naux;
-      for (int U = 0; U < nat; ++U) {
-        const int K = h.n_ao[U] * P.m[U];
-        DGemm df{Cp + P.cp_off[U], Ow + (size_t)q * P.o_sz + P.o_off[U], chi + (size_t)h.aux_off[U] * naux,
-                 h.n_aux[U], naux, K, K, K, naux, -spin, 0.0};
-        b2.push_back(df);
-      }
-    }
-    dgemm_batched(h, b2, s, P.gargs2);
+    fp64_gather(h, dpts, np, w);
+    std::vector<DGemm> b1, b2;
+    fp64_nx(h, np, w, b1);
+    dgemm_batched(h, b1, s, P.gargs1, &P.var_nx);
+    run_oassemble(h, dpts, np, w.Nw, w.Xw, w.Ow);
+    fp64_final(h, pts, w, b2);
+    dgemm_batched(h, b2, s, P.gargs2, &P.var_fin);
   }
   fill_partners(h);
   LR_CUDA(cudaStreamSynchronize(s));
   if (ms_gemm) *ms_gemm = 0;
+}
+
+bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
+  if (hs.empty()) return false;
+  Handle &h0 = *hs[0];
+  cudaStream_t s = h0.stream;
+  bool fresh = m.gens.size() != hs.size();
+  for (size_t i = 0; i < hs.size() && !fresh; ++i) fresh = m.gens[i] != hs[i]->plan.gen || m.hs[i] != hs[i];
+  if (fresh) {
+    m.reset();
+    m.hs = hs;
+    m.gens.clear();
+    for (Handle *h : hs) m.gens.push_back(h->plan.gen);
+  }
+  // workspaces, chi0(R, tau) and the point list of every handle (all its points in one batch)
+  std::vector<Fp64Ws> ws(hs.size());
+  std::vector<std::vector<Point>> pts(hs.size());
+  for (size_t i = 0; i < hs.size(); ++i) {
+    Handle &h = *hs[i];
+    Chi0Plan &P = h.plan;
+    h.ensure(h.d_chi_tau, (size_t)h.ntau * h.mesh.size() * h.naux * h.naux * sizeof(double));
+    const DpWs dw = dp_ws(h, P);
+    h.ensure(P.ws, dw.total);
+    ws[i] = fp64_ws(h, dw.npb);
+    const std::vector<int> rl = chi0_r_list(h.mesh);
+    pts[i] = make_points(h, rl, 0, (int)(h.ntau * rl.size()));
+    if (fresh) {
+      h.ensure(P.t_pts, pts[i].size() * sizeof(Point));
+      LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts[i].data(), pts[i].size() * sizeof(Point), cudaMemcpyHostToDevice, s));
+    }
+  }
+  if (m.exec) {   // replay the captured sequence
+    LR_CUDA(cudaGraphLaunch(m.exec, s));
+    launch_counter() += m.nodes;
+    LR_CUDA(cudaStreamSynchronize(s));
+    return true;
+  }
+  std::vector<DGemm> b1, b2;
+  for (size_t i = 0; i < hs.size(); ++i) {
+    fp64_nx(*hs[i], (int)pts[i].size(), ws[i], b1);
+    fp64_final(*hs[i], pts[i], ws[i], b2);
+  }
+  // the whole sequence; tile variants are tuned on the first pass (eagerly), then the same
+  // launches are captured into a graph for the next calls
+  auto sequence = [&](bool tune, DLaunch &L1, DLaunch &L2) {
+    for (size_t i = 0; i < hs.size(); ++i)
+      fp64_gather(*hs[i], (const Point *)hs[i]->plan.t_pts.p, (int)pts[i].size(), ws[i]);
+    if (tune) {
+      if (m.var_nx < 0) m.var_nx = dgemm_autotune(h0, b1, s, m.nx_args);
+      L1 = dgemm_prepare(h0, b1, m.var_nx, s, m.nx_args);
+    }
+    dgemm_launch(h0, L1, s, tune);
+    for (size_t i = 0; i < hs.size(); ++i)
+      run_oassemble(*hs[i], (const Point *)hs[i]->plan.t_pts.p, (int)pts[i].size(), ws[i].Nw, ws[i].Xw, ws[i].Ow);
+    if (tune) {
+      if (m.var_fin < 0) m.var_fin = dgemm_autotune(h0, b2, s, m.fin_args);
+      L2 = dgemm_prepare(h0, b2, m.var_fin, s, m.fin_args);
+    }
+    dgemm_launch(h0, L2, s, tune);
+    for (Handle *h : hs) fill_partners(*h);
+  };
+  DLaunch L1, L2;
+  const long long c0 = launch_counter();
+  sequence(true, L1, L2);
+  LR_CUDA(cudaStreamSynchronize(s));
+  if (m.graph_failed) return false;
+  const long long c1 = launch_counter();
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    m.graph_failed = true;
+    return false;
+  }
+  bool ok = true;
+  try {
+    sequence(false, L1, L2);
+  } catch (const Error &) {
+    ok = false;
+  }
+  if (cudaStreamEndCapture(s, &g) != cudaSuccess || !ok || !g ||
+      cudaGraphInstantiate(&m.exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    m.exec = nullptr;
+    m.graph_failed = true;
+  }
+  if (g) cudaGraphDestroy(g);
+  m.nodes = launch_counter() - c1;
+  launch_counter() = c1;   // captured launches did not run
+  (void)c0;
+  return false;
+}
+
+bool chi0_fits_one_batch(const Handle &h) {
+  return h.chi0_S < 0 && dp_ws(h, h.plan).npb == (long long)h.ntau * (long long)chi0_r_list(h.mesh).size();
+}
+
+void MergedChi0::reset() {
+  if (exec) cudaGraphExecDestroy(exec);
+  exec = nullptr;
+  graph_failed = false;
+  nodes = 0;
 }
 
 size_t chi0_device_bytes(const Handle &h, const Chi0Plan &P) {

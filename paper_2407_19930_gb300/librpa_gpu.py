@@ -74,6 +74,13 @@ class librpa_gpu_server_stats(ctypes.Structure):
                 ("peak_reserved", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t)]
 
 
+class librpa_gpu_batch_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("n_merged", ctypes.c_int), ("graph", ctypes.c_int), ("var_nx", ctypes.c_int),
+                ("var_fin", ctypes.c_int), ("failed_index", ctypes.c_int), ("ms_green", ctypes.c_double),
+                ("ms_chi0", ctypes.c_double), ("ms_freq", ctypes.c_double), ("ms_ec", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("launches", ctypes.c_longlong)]
+
+
 class LibrpaError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s (%d): %s" % (_CODES.get(code, "?"), code, msg))
@@ -114,6 +121,10 @@ _SIGS = {
                                               ctypes.POINTER(librpa_gpu_result)]),
     "librpa_gpu_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(librpa_gpu_server_stats)]),
     "librpa_gpu_server_destroy": (None, [ctypes.c_void_p]),
+    "librpa_gpu_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_H), ctypes.c_int]),
+    "librpa_gpu_batch_run": (ctypes.c_int, [ctypes.c_void_p, _D]),
+    "librpa_gpu_batch_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(librpa_gpu_batch_stats)]),
+    "librpa_gpu_batch_destroy": (None, [ctypes.c_void_p]),
     "librpa_gpu_ec_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "librpa_gpu_destroy": (None, [_H]),
@@ -325,6 +336,41 @@ def librpa_gpu_ec_noalloc(naux, nomega, V, chi, out, stream=None):
     rc = load().librpa_gpu_ec_noalloc(int(naux), int(nomega), V, chi, out, stream, msg, len(msg))
     if rc != LIBRPA_OK:
         raise LibrpaError(rc, msg.value.decode())
+
+
+def librpa_gpu_batch_create(handles):
+    arr = (_H * len(handles))(*[h.value if hasattr(h, "value") else h for h in handles])
+    b = ctypes.c_void_p()
+    rc = load().librpa_gpu_batch_create(ctypes.byref(b), arr, len(handles))
+    if rc != LIBRPA_OK:
+        raise LibrpaError(rc, "batch_create")
+    b._handles = list(handles)
+    return b
+
+
+def librpa_gpu_batch_run(b):
+    """E_c of every handle of the batch (numpy array)."""
+    ec = np.zeros(len(b._handles))
+    rc = load().librpa_gpu_batch_run(b, _dp(ec))
+    if rc != LIBRPA_OK:
+        st = librpa_gpu_batch_get_stats(b)
+        i = st["failed_index"]
+        msg = librpa_gpu_last_error(b._handles[i]) if i >= 0 else ""
+        raise LibrpaError(rc, "batch handle %d: %s" % (i, msg))
+    return ec
+
+
+def librpa_gpu_batch_get_stats(b):
+    st = librpa_gpu_batch_stats()
+    rc = load().librpa_gpu_batch_get_stats(b, ctypes.byref(st))
+    if rc != LIBRPA_OK:
+        raise LibrpaError(rc, "batch_get_stats")
+    return {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def librpa_gpu_batch_destroy(b):
+    if b:
+        load().librpa_gpu_batch_destroy(b)
 
 
 def librpa_gpu_estimate_bytes(h):
