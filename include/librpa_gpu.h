@@ -260,11 +260,12 @@ int librpa_gpu_get_stats(librpa_gpu_t h, librpa_gpu_stats *s);
  * Many independent structures in one pass (not in the paper, which computes one system
  * per call).  Every handle must be filled (set_* calls) before librpa_gpu_batch_run.
  * All handles run on the first handle's stream.  In the FP64 mode, the chi0 contraction
- * of every handle whose points fit one workspace batch runs as single grouped GEMM launches
- * over all handles' tiles, which have uneven shapes.  The GEMM tile shape is picked by
+ * of all handles runs in rounds: round r takes the r-th batch of (R, tau) points of every
+ * handle, and runs its GEMMs as single grouped launches over all those tiles, which have
+ * uneven shapes.  The GEMM tile shape is picked by
  * timing the variants on the first run; from the second run on, that launch sequence is
- * replayed from a CUDA graph.  The other handles (tensor-core modes, structures too
- * large for one batch) run their own chi0 path in the same pass.  G, the transforms and
+ * replayed from a CUDA graph.  Handles in the tensor-core modes run their own chi0 path
+ * in the same pass.  G, the transforms and
  * the ln det stage run per handle.  While a batch exists, run its handles only through
  * the batch.  After changing a handle's LRI blocks or structure, the next run re-plans
  * and captures again.  Destroy the batch before its handles. */

@@ -1,8 +1,8 @@
 // Batched energies: many independent structures (handles) in one pass on one stream.  The FP64
-// chi0 contraction of every handle whose points fit one workspace batch runs as single grouped
-// launches over all handles' tiles (uneven block shapes), with tile variants tuned on the first
-// run and the launch sequence replayed from a CUDA graph afterwards; other handles (tensor-core
-// modes, large structures) run their own chi0 path in the same pass.  G, the transforms and the
+// chi0 contraction of all handles runs in rounds of point batches, each round's GEMMs as single
+// grouped launches over all handles' tiles (uneven block shapes), with tile variants tuned on the
+// first run and the launch sequence replayed from a CUDA graph afterwards; handles in the
+// tensor-core modes run their own chi0 path in the same pass.  G, the transforms and the
 // ln det stage run per handle.
 #include <string>
 #include <vector>
@@ -165,8 +165,8 @@ void librpa_gpu_batch_destroy(librpa_gpu_batch_t b) {
   cudaSetDevice(b->hs[0]->opts.device);
   cudaStreamSynchronize(b->hs[0]->stream);
   b->m.reset();
-  b->hs[0]->release(b->m.nx_args);
-  b->hs[0]->release(b->m.fin_args);
+  for (DevBuf &d : b->m.nx_args) b->hs[0]->release(d);
+  for (DevBuf &d : b->m.fin_args) b->hs[0]->release(d);
   delete b;
 }
 

@@ -182,13 +182,14 @@ void chi0_shape(const Handle &h, Chi0Plan &P);
 // device bytes the chi0 stage holds for this shape (packed C and its digit planes, chi0(R, tau),
 // batch workspace, tables)
 size_t chi0_device_bytes(const Handle &h, const Chi0Plan &P);
-// Batched chi0 of several handles (FP64 route, all points of each handle in one batch): the
-// N/X and final GEMMs of all handles as single grouped launches on hs[0]'s stream; the launch
-// sequence is captured in a CUDA graph on the first call and replayed while no plan changes.
+// Batched chi0 of several handles (FP64 route) on hs[0]'s stream, in rounds: round r takes the
+// r-th point batch of every handle, and the N/X and final GEMMs of a round are single grouped
+// launches over all those handles' tiles.  The launch sequence is captured in a CUDA graph on
+// the first call and replayed while no plan changes.
 struct MergedChi0 {
   std::vector<Handle *> hs;
   std::vector<long long> gens;
-  DevBuf nx_args, fin_args;   // allocated through hs[0]
+  std::vector<DevBuf> nx_args, fin_args;   // descriptors of every round, allocated through hs[0]
   int var_nx = -1, var_fin = -1;
   cudaGraphExec_t exec = nullptr;
   long long nodes = 0;
@@ -197,7 +198,7 @@ struct MergedChi0 {
 };
 // returns true when the launches were replayed from the captured graph
 bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m);
-// whether h's FP64 route holds all its points in one batch (a condition of chi0_run_merged)
+// whether h takes part in chi0_run_merged (its chi0 runs on the FP64 route)
 bool chi0_fits_one_batch(const Handle &h);
 
 // lattice vectors R whose chi0(R, tau) is computed (R <= -R in the flat BvK order); the others

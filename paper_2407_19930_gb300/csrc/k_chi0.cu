@@ -811,11 +811,11 @@ struct DpWs {
   size_t total;
 };
 
-DpWs dp_ws(const Handle &h, const Chi0Plan &P) {
+DpWs dp_ws(const Handle &h, const Chi0Plan &P, long long cap_doubles = 1LL << 27) {
   DpWs w;
   w.per_point = 2 * (P.bg_sz + P.ag_sz + P.n_sz + P.x_sz) + P.o_sz;
   const long long total_pts = (long long)h.ntau * chi0_r_list(h.mesh).size();
-  w.npb = std::min(std::max<long long>(1, (1LL << 27) / std::max<long long>(1, w.per_point)), total_pts);
+  w.npb = std::min(std::max<long long>(1, cap_doubles / std::max<long long>(1, w.per_point)), total_pts);
   w.total = (size_t)w.npb * w.per_point * sizeof(double);
   return w;
 }
@@ -989,26 +989,33 @@ bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
   if (hs.empty()) return false;
   Handle &h0 = *hs[0];
   cudaStream_t s = h0.stream;
-  bool fresh = m.gens.size() != hs.size();
-  for (size_t i = 0; i < hs.size() && !fresh; ++i) fresh = m.gens[i] != hs[i]->plan.gen || m.hs[i] != hs[i];
+  const size_t nh = hs.size();
+  bool fresh = m.gens.size() != nh;
+  for (size_t i = 0; i < nh && !fresh; ++i) fresh = m.gens[i] != hs[i]->plan.gen || m.hs[i] != hs[i];
   if (fresh) {
     m.reset();
     m.hs = hs;
     m.gens.clear();
     for (Handle *h : hs) m.gens.push_back(h->plan.gen);
   }
-  // workspaces, chi0(R, tau) and the point list of every handle (all its points in one batch)
-  std::vector<Fp64Ws> ws(hs.size());
-  std::vector<std::vector<Point>> pts(hs.size());
-  for (size_t i = 0; i < hs.size(); ++i) {
+  // per handle: chi0(R, tau), a workspace for npb points (at most 16 GiB over the batch), all its
+  // points resident, and the number of rounds it takes
+  const long long cap = std::max<long long>(1LL << 24, std::min<long long>(1LL << 27, (2LL << 30) / (long long)nh));
+  std::vector<Fp64Ws> ws(nh);
+  std::vector<std::vector<Point>> pts(nh);
+  std::vector<long long> npb(nh);
+  int rounds = 0;
+  for (size_t i = 0; i < nh; ++i) {
     Handle &h = *hs[i];
     Chi0Plan &P = h.plan;
     h.ensure(h.d_chi_tau, (size_t)h.ntau * h.mesh.size() * h.naux * h.naux * sizeof(double));
-    const DpWs dw = dp_ws(h, P);
+    const DpWs dw = dp_ws(h, P, cap);
     h.ensure(P.ws, dw.total);
     ws[i] = fp64_ws(h, dw.npb);
+    npb[i] = dw.npb;
     const std::vector<int> rl = chi0_r_list(h.mesh);
     pts[i] = make_points(h, rl, 0, (int)(h.ntau * rl.size()));
+    rounds = std::max(rounds, (int)((pts[i].size() + npb[i] - 1) / npb[i]));
     if (fresh) {
       h.ensure(P.t_pts, pts[i].size() * sizeof(Point));
       LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts[i].data(), pts[i].size() * sizeof(Point), cudaMemcpyHostToDevice, s));
@@ -1020,33 +1027,54 @@ bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
     LR_CUDA(cudaStreamSynchronize(s));
     return true;
   }
-  std::vector<DGemm> b1, b2;
-  for (size_t i = 0; i < hs.size(); ++i) {
-    fp64_nx(*hs[i], (int)pts[i].size(), ws[i], b1);
-    fp64_final(*hs[i], pts[i], ws[i], b2);
-  }
+  // descriptors of every round: round r takes points [r npb_i, (r + 1) npb_i) of handle i
+  auto slice = [&](size_t i, int r, long long &p0, int &np) {
+    p0 = (long long)r * npb[i];
+    np = (int)std::max<long long>(0, std::min<long long>(npb[i], (long long)pts[i].size() - p0));
+  };
+  std::vector<std::vector<DGemm>> b1(rounds), b2(rounds);
+  for (int r = 0; r < rounds; ++r)
+    for (size_t i = 0; i < nh; ++i) {
+      long long p0;
+      int np;
+      slice(i, r, p0, np);
+      if (!np) continue;
+      fp64_nx(*hs[i], np, ws[i], b1[r]);
+      fp64_final(*hs[i], std::vector<Point>(pts[i].begin() + p0, pts[i].begin() + p0 + np), ws[i], b2[r]);
+    }
+  m.nx_args.resize(rounds);
+  m.fin_args.resize(rounds);
+  std::vector<DLaunch> L1(rounds), L2(rounds);
   // the whole sequence; tile variants are tuned on the first pass (eagerly), then the same
   // launches are captured into a graph for the next calls
-  auto sequence = [&](bool tune, DLaunch &L1, DLaunch &L2) {
-    for (size_t i = 0; i < hs.size(); ++i)
-      fp64_gather(*hs[i], (const Point *)hs[i]->plan.t_pts.p, (int)pts[i].size(), ws[i]);
-    if (tune) {
-      if (m.var_nx < 0) m.var_nx = dgemm_autotune(h0, b1, s, m.nx_args);
-      L1 = dgemm_prepare(h0, b1, m.var_nx, s, m.nx_args);
+  auto sequence = [&](bool first) {
+    for (int r = 0; r < rounds; ++r) {
+      for (size_t i = 0; i < nh; ++i) {
+        long long p0;
+        int np;
+        slice(i, r, p0, np);
+        if (np) fp64_gather(*hs[i], (const Point *)hs[i]->plan.t_pts.p + p0, np, ws[i]);
+      }
+      if (first) {
+        if (m.var_nx < 0) m.var_nx = dgemm_autotune(h0, b1[r], s, m.nx_args[r]);
+        L1[r] = dgemm_prepare(h0, b1[r], m.var_nx, s, m.nx_args[r]);
+      }
+      dgemm_launch(h0, L1[r], s, first);
+      for (size_t i = 0; i < nh; ++i) {
+        long long p0;
+        int np;
+        slice(i, r, p0, np);
+        if (np) run_oassemble(*hs[i], (const Point *)hs[i]->plan.t_pts.p + p0, np, ws[i].Nw, ws[i].Xw, ws[i].Ow);
+      }
+      if (first) {
+        if (m.var_fin < 0) m.var_fin = dgemm_autotune(h0, b2[r], s, m.fin_args[r]);
+        L2[r] = dgemm_prepare(h0, b2[r], m.var_fin, s, m.fin_args[r]);
+      }
+      dgemm_launch(h0, L2[r], s, first);
     }
-    dgemm_launch(h0, L1, s, tune);
-    for (size_t i = 0; i < hs.size(); ++i)
-      run_oassemble(*hs[i], (const Point *)hs[i]->plan.t_pts.p, (int)pts[i].size(), ws[i].Nw, ws[i].Xw, ws[i].Ow);
-    if (tune) {
-      if (m.var_fin < 0) m.var_fin = dgemm_autotune(h0, b2, s, m.fin_args);
-      L2 = dgemm_prepare(h0, b2, m.var_fin, s, m.fin_args);
-    }
-    dgemm_launch(h0, L2, s, tune);
     for (Handle *h : hs) fill_partners(*h);
   };
-  DLaunch L1, L2;
-  const long long c0 = launch_counter();
-  sequence(true, L1, L2);
+  sequence(true);
   LR_CUDA(cudaStreamSynchronize(s));
   if (m.graph_failed) return false;
   const long long c1 = launch_counter();
@@ -1058,7 +1086,7 @@ bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
   }
   bool ok = true;
   try {
-    sequence(false, L1, L2);
+    sequence(false);
   } catch (const Error &) {
     ok = false;
   }
@@ -1071,13 +1099,10 @@ bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
   if (g) cudaGraphDestroy(g);
   m.nodes = launch_counter() - c1;
   launch_counter() = c1;   // captured launches did not run
-  (void)c0;
   return false;
 }
 
-bool chi0_fits_one_batch(const Handle &h) {
-  return h.chi0_S < 0 && dp_ws(h, h.plan).npb == (long long)h.ntau * (long long)chi0_r_list(h.mesh).size();
-}
+bool chi0_fits_one_batch(const Handle &h) { return h.chi0_S < 0; }
 
 void MergedChi0::reset() {
   if (exec) cudaGraphExecDestroy(exec);
