@@ -163,6 +163,18 @@ __global__ void k_plain(Src src, int rows, int K, int kpad, int row0, __nv_bfloa
   dig[(long long)row0 * kpad + x] = __double2bfloat16(k < K ? src.get(r, k) : 0.0);
 }
 
+// plain TF32: the FP32 value rounded to the 10-bit TF32 mantissa (round to nearest, ties away)
+template <class Src>
+__global__ void k_plain_tf32(Src src, int rows, int K, int kpad, int row0, float *dig) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (long long)rows * kpad) return;
+  const int r = (int)(x / kpad), k = (int)(x % kpad);
+  const float f = (float)(k < K ? src.get(r, k) : 0.0);
+  uint32_t t;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(f));
+  dig[(long long)row0 * kpad + x] = __uint_as_float(t);
+}
+
 template <class Src>
 void split_any(const Src &src, int rows, int K, int row0, Sliced &o, cudaStream_t s) {
   if (row0 < 0 || row0 + rows > o.rows || K > o.kpad) throw Error{LIBRPA_E_ARG, "split: rows or K exceed the operand"};
@@ -170,19 +182,23 @@ void split_any(const Src &src, int rows, int K, int row0, Sliced &o, cudaStream_
   const long long plane = (long long)o.rows * kpad;
   const long long n = (long long)rows * kpad;
   const unsigned g = (unsigned)((n + 255) / 256);
-  if (o.S == 0) {
-    k_plain<Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, o.digits);
+  if (o.S == 0 || o.S == S_TF32) {
+    if (o.S == 0)
+      k_plain<Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, (__nv_bfloat16 *)o.digits);
+    else
+      k_plain_tf32<Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, (float *)o.digits);
     ++launch_counter();
     LR_CUDA(cudaGetLastError());
     return;
   }
+  __nv_bfloat16 *dig = (__nv_bfloat16 *)o.digits;
   k_row_expo<Src><<<(unsigned)(((long long)rows * 32 + 255) / 256), 256, 0, s>>>(src, rows, K, row0, o.expo);
   switch (o.S) {
-    case 1: k_digits<1, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, o.digits); break;
-    case 2: k_digits<2, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, o.digits); break;
-    case 3: k_digits<3, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, o.digits); break;
-    case 4: k_digits<4, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, o.digits); break;
-    default: k_digits<5, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, o.digits); break;
+    case 1: k_digits<1, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, dig); break;
+    case 2: k_digits<2, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, dig); break;
+    case 3: k_digits<3, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, dig); break;
+    case 4: k_digits<4, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, dig); break;
+    default: k_digits<5, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, dig); break;
   }
   launch_counter() += 2;
   LR_CUDA(cudaGetLastError());
@@ -243,14 +259,23 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 }
 
 
-// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = BN
+// instruction descriptors: D = F32, A and B K-major, M = 128, N = BN; A/B format 1 = BF16
+// (kind::f16) or 2 = TF32 (kind::tf32)
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                ((uint32_t)(BM >> 4) << 24);
 
 __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
       ::"r"(d), "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d), "l"(a), "l"(b), "r"(IDESC_TF32), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
@@ -284,7 +309,7 @@ constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s
 //   warps 0-3: epilogue; warp w owns TMEM lanes 32w..32w+31 (= tile rows); after each flush
 //     group they move the diagonal accumulators into exact int64 register sums and hand the
 //     TMEM columns back to the issuer.
-constexpr int PBK = 32;   // K per stage: one 64-byte swizzle row of BF16
+constexpr int PBK = 32;   // K per stage: one 64-byte swizzle row of BF16 (16 TF32 values)
 constexpr int NST = 3;    // pipeline depth
 
 // shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart
@@ -307,12 +332,15 @@ __global__ void __launch_bounds__(192, 1)
     k_ozgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const Entry *__restrict__ entries, const Tile *__restrict__ tiles, const int *__restrict__ expoA,
              const int *__restrict__ expoB, int *err) {
-  constexpr int NP = S > 0 ? S : 1;                   // digit planes (S = 0: one plane of plain BF16)
-  constexpr uint32_t A_BYTES = BM * PBK * 2, B_BYTES = BN * PBK * 2;
+  constexpr bool TF = S == S_TF32;                     // plain TF32 (kind::tf32)
+  constexpr bool PLAIN = S == 0 || TF;                 // one plane, FP32 accumulation over all K
+  constexpr int NP = PLAIN ? 1 : S;                    // digit planes
+  constexpr int KS = TF ? PBK / 2 : PBK;               // K elements per stage (64 bytes per row)
+  constexpr uint32_t A_BYTES = BM * 64, B_BYTES = BN * 64;
   constexpr uint32_t STAGE = NP * (A_BYTES + B_BYTES);
   // K steps per flush group: NP pairs x (32 G) x 2^14 <= 2^24 keeps the FP32 sums exact; plain
   // BF16 accumulates over the whole K in FP32
-  constexpr int G = S == 0 ? (1 << 30) : 32 / NP;
+  constexpr int G = PLAIN ? (1 << 30) : 32 / NP;
   constexpr uint32_t TMEM_COLS = tmem_cols<NP>();
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[NST], empty[NST], tfull, tempty;
@@ -340,8 +368,8 @@ __global__ void __launch_bounds__(192, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   int kbeg = m0 * en.km + n0 * en.kn;
-  kbeg = kbeg / PBK * PBK;
-  const int nsteps = en.K > kbeg ? (en.K - kbeg + PBK - 1) / PBK : 0;
+  kbeg = kbeg / KS * KS;
+  const int nsteps = en.K > kbeg ? (en.K - kbeg + KS - 1) / KS : 0;
   const int ngroups = (nsteps + G - 1) / G;
   const int arow = en.a_row0 + m0, brow = en.b_row0 + n0;
   long long acc[BN];
@@ -358,7 +386,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         mbar_expect_tx(&full[st], STAGE);
         uint8_t *sa = smem + st * STAGE, *sb = sa + NP * A_BYTES;
-        const int k0 = kbeg + i * PBK;
+        const int k0 = kbeg + i * KS;
 #pragma unroll
         for (int p = 0; p < NP; ++p) tma_load_3d(sa + p * A_BYTES, &tmA, &full[st], k0, arow, p);
 #pragma unroll
@@ -384,9 +412,15 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
           for (int t = 1; t + s <= NP + 1; ++t)
 #pragma unroll
-            for (int j = 0; j < PBK / 16; ++j)
-              umma(tmem + (uint32_t)(s + t - 2) * BN, smem_desc64(sa + (s - 1) * A_BYTES + 32 * j),
-                   smem_desc64(sb + (t - 1) * B_BYTES + 32 * j), (c == 0 && j == 0 && s == 1) ? 0u : 1u);
+            for (int j = 0; j < 2; ++j) {   // two MMAs of 32 bytes of K per 64-byte row
+              const uint64_t da = smem_desc64(sa + (s - 1) * A_BYTES + 32 * j);
+              const uint64_t db = smem_desc64(sb + (t - 1) * B_BYTES + 32 * j);
+              const uint32_t accum = (c == 0 && j == 0 && s == 1) ? 0u : 1u;
+              if constexpr (TF)
+                umma_tf32(tmem + (uint32_t)(s + t - 2) * BN, da, db, accum);
+              else
+                umma(tmem + (uint32_t)(s + t - 2) * BN, da, db, accum);
+            }
         umma_commit(&empty[st]);
         if (c == G - 1 || i == nsteps - 1) umma_commit(&tfull);
       }
@@ -401,7 +435,7 @@ __global__ void __launch_bounds__(192, 1)
         break;
       }
       tc_fence_after();
-      if constexpr (S > 0) {
+      if constexpr (!PLAIN) {
 #pragma unroll
         for (int d = 2; d <= S + 1; ++d) {
           const long long mul = 1LL << (8 * (S + 1 - d));
@@ -420,18 +454,18 @@ __global__ void __launch_bounds__(192, 1)
     }
     if (!failed) {
       const int row = m0 + 32 * warp + lane;
-      const int ea = (S > 0 && row < en.M) ? expoA[en.a_row0 + row] : 0;
+      const int ea = (!PLAIN && row < en.M) ? expoA[en.a_row0 + row] : 0;
 #pragma unroll
       for (int cb = 0; cb < BN / 16; ++cb) {
         uint32_t r[16];
-        if constexpr (S == 0) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + cb * 16, r);
+        if constexpr (PLAIN) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + cb * 16, r);
         if (row >= en.M) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int col = n0 + cb * 16 + j;
           if (col >= en.N) break;
           double v;
-          if constexpr (S == 0)
+          if constexpr (PLAIN)
             v = nsteps > 0 ? en.alpha * (double)__uint_as_float(r[j]) : 0.0;
           else
             v = en.alpha * ldexp((double)acc[cb * 16 + j], ea + expoB[en.b_row0 + col] - 14 - 8 * (S - 1));
@@ -465,11 +499,13 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 CUtensorMap make_map(const Sliced &o, int box_rows) {
   CUtensorMap m;
-  const cuuint64_t dims[3] = {(cuuint64_t)o.kpad, (cuuint64_t)o.rows, (cuuint64_t)(o.S > 0 ? o.S : 1)};
-  const cuuint64_t strides[2] = {(cuuint64_t)o.kpad * 2, (cuuint64_t)o.kpad * 2 * (cuuint64_t)o.rows};
-  const cuuint32_t box[3] = {(cuuint32_t)PBK, (cuuint32_t)box_rows, 1};
+  const cuuint64_t eb = (cuuint64_t)elem_bytes(o.S);
+  const cuuint64_t dims[3] = {(cuuint64_t)o.kpad, (cuuint64_t)o.rows, (cuuint64_t)planes(o.S)};
+  const cuuint64_t strides[2] = {(cuuint64_t)o.kpad * eb, (cuuint64_t)o.kpad * eb * (cuuint64_t)o.rows};
+  const cuuint32_t box[3] = {(cuuint32_t)(64 / eb), (cuuint32_t)box_rows, 1};   // 64-byte rows
   const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = g_encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)o.digits, dims, strides, box, estr,
+  const CUtensorMapDataType dt = o.S == S_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUresult r = g_encode(&m, dt, 3, o.digits, dims, strides, box, estr,
                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error{LIBRPA_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r)};
@@ -479,7 +515,7 @@ CUtensorMap make_map(const Sliced &o, int box_rows) {
 template <int S>
 void launch(const CUtensorMap &ma, const CUtensorMap &mb, const Entry *e, const Tile *t, unsigned ntiles,
             const int *ea, const int *eb, int *err, cudaStream_t s) {
-  const int smem = NST * (S > 0 ? S : 1) * (BM + BN) * PBK * 2 + 1024;
+  const int smem = NST * planes(S) * (BM + BN) * 64 + 1024;
   LR_CUDA(cudaFuncSetAttribute(k_ozgemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   k_ozgemm<S><<<ntiles, 192, smem, s>>>(ma, mb, e, t, ea, eb, err);
 }
@@ -499,7 +535,7 @@ void init() {
 
 size_t sliced_bytes(int rows, int K, int S) {
   const size_t kpad = ((size_t)K + 7) / 8 * 8;
-  const size_t dig = ((size_t)(S > 0 ? S : 1) * rows * kpad * 2 + 255) / 256 * 256;
+  const size_t dig = ((size_t)planes(S) * rows * kpad * elem_bytes(S) + 255) / 256 * 256;
   return dig + ((size_t)rows * 4 + 255) / 256 * 256;
 }
 
@@ -508,8 +544,8 @@ void sliced_bind(Sliced &o, void *mem, int rows, int K, int S) {
   o.K = K;
   o.kpad = (K + 7) / 8 * 8;
   o.S = S;
-  o.digits = (__nv_bfloat16 *)mem;
-  const size_t dig = ((size_t)(S > 0 ? S : 1) * rows * o.kpad * 2 + 255) / 256 * 256;
+  o.digits = mem;
+  const size_t dig = ((size_t)planes(S) * rows * o.kpad * elem_bytes(S) + 255) / 256 * 256;
   o.expo = (int *)((char *)mem + dig);
 }
 
@@ -539,11 +575,12 @@ void split_ragged(const double *base, const long long *off, const int *Ke, int r
 
 long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry> &entries, int *err,
                        cudaStream_t s, Handle &h, DevBuf &args) {
-  if (a.S != b.S || a.S < 0 || a.S > SMAX) throw Error{LIBRPA_E_ARG, "oz::gemm: operand mismatch"};
+  if (a.S != b.S || a.S < 0 || (a.S > SMAX && a.S != S_TF32)) throw Error{LIBRPA_E_ARG, "oz::gemm: operand mismatch"};
   init();
   std::vector<Tile> tiles;
   // MMA flops issued: per tile BM x BN x (K rounded up to the K step) per digit-plane product
-  const double prods = a.S == 0 ? 1.0 : a.S * (a.S + 1) / 2.0;
+  const double prods = (a.S == 0 || a.S == S_TF32) ? 1.0 : a.S * (a.S + 1) / 2.0;
+  const int ks = a.S == S_TF32 ? PBK / 2 : PBK;   // K elements per pipeline stage
   double exec = 0;
   h.oz_exec_flops = 0;
   for (int e = 0; e < (int)entries.size(); ++e) {
@@ -556,8 +593,8 @@ long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry
       for (int n0 = 0; n0 < en.N; n0 += BN) {
         if (en.lower_div > 0 && n0 > m0 / en.lower_div) continue;
         tiles.push_back({e, m0, n0});
-        const int kbeg = (m0 * en.km + n0 * en.kn) / PBK * PBK;   // as in the kernel
-        if (en.K > kbeg) exec += 2.0 * BM * BN * (double)((en.K - kbeg + PBK - 1) / PBK * PBK) * prods;
+        const int kbeg = (m0 * en.km + n0 * en.kn) / ks * ks;   // as in the kernel
+        if (en.K > kbeg) exec += 2.0 * BM * BN * (double)((en.K - kbeg + ks - 1) / ks * ks) * prods;
       }
   }
   if (tiles.empty()) return 0;
@@ -577,6 +614,7 @@ long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry
     case 2: launch<2>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
     case 3: launch<3>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
     case 4: launch<4>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
+    case S_TF32: launch<S_TF32>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
     default: launch<5>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
   }
   ++launch_counter();

@@ -6,7 +6,9 @@
 // diagonal accumulates in its own FP32 TMEM accumulator, which is exact while |sum| < 2^24
 // (<= 1024 / (pairs of the diagonal) products of K).  Accumulators are flushed into exact int64
 // register sums and scaled to FP64 once at the end.  S = 5 keeps 39 bits per operand (relative
-// product error ~1e-12); S = 1..3 give the BF16 / split-precision ladder.
+// product error ~1e-12); S = 1..3 give the BF16 / split-precision ladder.  Two plain forms
+// take one plane of values rounded per element and accumulate in FP32 over all K: S = 0 (BF16,
+// kind::f16) and S = S_TF32 (TF32 in FP32 containers, kind::tf32).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -20,17 +22,20 @@ struct Handle;
 struct DevBuf;
 namespace oz {
 
-constexpr int BM = 128, BN = 64, BK = 64, SMAX = 5;
+constexpr int BM = 128, BN = 64, BK = 64, SMAX = 5, S_TF32 = 6;
+inline int planes(int S) { return S >= 1 && S <= SMAX ? S : 1; }
+inline int elem_bytes(int S) { return S == S_TF32 ? 4 : 2; }
 
-// K-major sliced operand: digit planes [S][rows][kpad] (BF16) and row exponents [rows].
+// K-major sliced operand: digit planes [S][rows][kpad] (BF16; FP32 for S_TF32) and row exponents
+// [rows].
 struct Sliced {
-  __nv_bfloat16 *digits = nullptr;
+  void *digits = nullptr;
   int *expo = nullptr;
   int rows = 0;     // total rows
   int K = 0;        // logical K (columns beyond K and up to kpad hold zero digits)
   int kpad = 0;     // row pitch in elements (K rounded up to a multiple of 8)
-  int S = 0;        // digit planes; S = 0 means one plane of plain BF16 values (own exponent per
-                    // element, rounded to nearest) multiplied with FP32 accumulation over all K
+  int S = 0;        // digit planes 1..SMAX; 0 = one plane of plain BF16 values, S_TF32 = one plane
+                    // of plain TF32 values (own exponent per element, rounded to nearest)
 };
 size_t sliced_bytes(int rows, int K, int S);   // bytes for digits + exponents (256-byte aligned parts)
 void sliced_bind(Sliced &o, void *mem, int rows, int K, int S);

@@ -172,6 +172,24 @@ def test_bf16_mode_energy(name):
     assert gpu["ec"] < 0 and abs(gpu["ec"] - ref["ec"]) < 1e-2 * abs(ref["ec"]), err
 
 
+@pytest.mark.parametrize("name", ["cubic", "mixed"])
+def test_tf32_mode(name):
+    """Plain TF32 chi0 GEMMs (11-bit significands, FP32 accumulation): stated, not bounded by
+    0.1 meV/atom.  Three more bits than BF16, so the error must fall below the BF16 mode's on the
+    same input and below 1e-3 of |E_c|; chi0(R, tau) within 5e-3 normwise."""
+    inp = CONFIGS[name]()
+    grid = ogrid.make_grid(8, *inp.delta_range)
+    ref = pipeline.rpa_energy(inp, grid)
+    tf = _run(inp, grid, opts=_opts(L.LIBRPA_TF32))
+    bf = _run(inp, grid, opts=_opts(L.LIBRPA_BF16))
+    e_tf = abs(tf["ec"] - ref["ec"])
+    e_bf = abs(bf["ec"] - ref["ec"])
+    print("tf32 mode E_c error %.4f meV/atom, bf16 %.4f (%s); chi0(R,tau) rel %.2e" % (
+        e_tf * MEV / inp.st.natoms, e_bf * MEV / inp.st.natoms, name, _rel(tf["chi_tau"], ref["chi_tau"])))
+    assert tf["ec"] < 0 and e_tf < 1e-3 * abs(ref["ec"]) and e_tf < e_bf
+    assert _rel(tf["chi_tau"], ref["chi_tau"]) < 5e-3
+
+
 def test_tc_mode_energy(tc_case):
     name, inp, grid, ref, gpu = tc_case
     assert abs(gpu["ec"] - ref["ec"]) < TOL_EC
