@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "RPA energies/s"
 UNIT = "energies/s"
 WORKLOAD = ("graphene 4x4 supercell + H2O-shaped molecule: 35 atoms, n_ao 431, N_aux 2010, "
-            "4x4x1 k-mesh, 16 tau/omega points, FP64")
+            "4x4x1 k-mesh, 16 tau/omega points")
 
 # FP64 tensor-core peak: measured BF16 dense peak x the nominal FP64/BF16 ratio of GB300
 # (1.25 TFLOP/s / 2250 TFLOP/s); no FP64 figure is in the measured-peaks file.
@@ -342,6 +342,11 @@ def run_gpu(args):
         line["roofline"] = tc_roofline(s, peaks, src)
     if modes:
         line["modes"] = modes
+    if ws == 1 and args.serve_sample > 0:
+        torch.cuda.empty_cache()   # the headline's blocks cached by torch go back to the device
+        m = serve_measure(L, _serve_inputs(args.serve_sample), args.rate, args.slots, args.ntau, local)
+        line["serving"] = {k: m[k] for k in ("value", "unit", "workload", "slots", "latency_ms", "completed",
+                                             "failed", "errors", "peak_running")}
     if ws == 1 and not args.no_cpu:
         from oracle import build as obuild, grid as ogrid
         obuild.build()
@@ -405,33 +410,29 @@ def time_mode(L, inp, stream, device, ntau, mode, ec_ref, torch):
             "roofline": tc_roofline(s, peaks, src), "steps": 1, "warmup": 1}
 
 
-def run_serve(args):
-    """Serving workload: a Poisson stream of RPA energy requests (random cells of 2-64 atoms,
-    mixed species, 1x1x1 to 3x3x1 k) into the library's serving loop; precision per request
+def _serve_inputs(n):
+    """The serving workload's requests, drawn in parallel (spawned workers)."""
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+    from paper_2407_19930_gb300 import synthetic as syn
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                             mp_context=multiprocessing.get_context("spawn")) as ex:
+        return list(ex.map(syn.config_request, range(n)))
+
+
+def serve_measure(L, reqs_in, rate, slots, ntau, device):
+    """Poisson arrivals of the requests into the library's serving loop; precision per request
     alternates between the FP64-accurate tensor-core mode and the mixed mode."""
     import numpy as np
-    import torch
-    from paper_2407_19930_gb300 import build as lbuild
-    from paper_2407_19930_gb300 import librpa_gpu as L
-    from paper_2407_19930_gb300 import synthetic as syn
-    ws, rank, local = dist_init()
-    if ws > 1:
-        print(json.dumps({"metric": METRIC, "unavailable": "the serving run is one process on one GPU"}))
-        return 0
-    torch.cuda.set_device(local)
-    lbuild.build()
-    L.load(build_if_missing=False)
-    n = args.serve_requests
-    reqs_in = [syn.config_request(i) for i in range(n)]
     modes = ["fp64_tc", "split"]
-    rng = np.random.default_rng(4004)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n))
-    s = L.librpa_gpu_server_create(device=local, slots=args.slots)
+    n = len(reqs_in)
+    arrivals = np.cumsum(np.random.default_rng(4004).exponential(1.0 / rate, size=n))
+    s = L.librpa_gpu_server_create(device=device, slots=slots)
     handles = []
     try:
         for i, inp in enumerate(reqs_in):
             o = L.librpa_gpu_default_opts()
-            o.n_tau = args.ntau
+            o.n_tau = ntau
             o.precision = PRECISIONS[modes[i % 2]][0]
             r = L.librpa_gpu_server_request(s, o)
             handles.append(r)
@@ -449,32 +450,60 @@ def run_serve(args):
         t_all = time.perf_counter() - t0
         clk = clocks.stop()
         st = L.librpa_gpu_server_get_stats(s)
+        errors = [{"request": i, "status": r["status"] if r else None,
+                   "message": L.librpa_gpu_last_error(handles[i])}
+                  for i, r in enumerate(res) if not r or r["status"] != 0]
     finally:
         L.librpa_gpu_server_destroy(s)
         for r in handles:
             L.librpa_gpu_destroy(r)
-    ok = [r for r in res if r and r["status"] == 0]
     sizes = [inp.st.natoms for inp in reqs_in]
-    line = {
-        "metric": METRIC, "value": st["energies_per_s"], "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": 0,
-        "ms_per_step": 1e3 * t_all / max(1, len(ok)), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "per request: " + ", ".join(PRECISIONS[m][1] for m in modes),
-        "data": "synthetic (seeded random cells, tight-binding KS data, LRI coefficients, Coulomb matrices)",
-        "config": {"workload": "serving: %d requests, Poisson arrivals at %.1f req/s, random cells of %d-%d atoms "
-                               "(5/9/13 NAO, 20/40/60 ABF), k-mesh 1x1x1..3x3x1, %d tau"
-                               % (n, args.rate, min(sizes), max(sizes), args.ntau),
-                   "slots": args.slots, "hbm_budget_bytes": st["hbm_budget"]},
+    return {
+        "value": st["energies_per_s"], "unit": UNIT, "seconds": t_all,
+        "workload": "serving: %d requests, Poisson arrivals at %.1f req/s, random cells of %d-%d atoms "
+                    "(5/9/13 NAO, 20/40/60 ABF), k-mesh 1x1x1..3x3x1, %d tau; precision per request alternating "
+                    "fp64_tc / split" % (n, rate, min(sizes), max(sizes), ntau),
+        "slots": slots, "hbm_budget_bytes": st["hbm_budget"],
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean_queue": st["mean_queue_ms"]},
         "completed": st["completed"], "failed": st["failed"], "peak_running": st["peak_running"],
-        "peak_reserved_bytes": st["peak_reserved"],
+        "peak_reserved_bytes": st["peak_reserved"], "errors": errors,
         "requests": [{"atoms": inp.st.natoms, "kmesh": "x".join(map(str, inp.st.kmesh)), "n_aux": inp.st.naux,
-                      "mode": modes[i % 2], "status": r["status"], "ec_ha": r["ec"], "ms_queue": r["ms_queue"],
-                      "ms_run": r["ms_run"], "ms_total": r["ms_total"], "slot": r["slot"]}
+                      "mode": modes[i % 2], "status": r["status"] if r else None, "ec_ha": r["ec"] if r else None,
+                      "ms_queue": r["ms_queue"] if r else None, "ms_run": r["ms_run"] if r else None,
+                      "ms_total": r["ms_total"] if r else None, "slot": r["slot"] if r else None}
                      for i, (inp, r) in enumerate(zip(reqs_in, res))],
         "clocks": clk,
     }
+
+
+def run_serve(args):
+    """Serving workload: a Poisson stream of RPA energy requests (random cells of 2-64 atoms,
+    mixed species, 1x1x1 to 3x3x1 k) into the library's serving loop."""
+    ws, rank, local = dist_init()
+    if ws > 1:
+        print(json.dumps({"metric": METRIC, "unavailable": "the serving run is one process on one GPU"}))
+        return 0
+    reqs_in = _serve_inputs(args.serve_requests)
+    import torch
+    from paper_2407_19930_gb300 import build as lbuild
+    from paper_2407_19930_gb300 import librpa_gpu as L
+    torch.cuda.set_device(local)
+    lbuild.build()
+    L.load(build_if_missing=False)
+    m = serve_measure(L, reqs_in, args.rate, args.slots, args.ntau, local)
+    n = len(reqs_in)
+    line = {
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": 0,
+        "ms_per_step": 1e3 * m["seconds"] / max(1, m["completed"]), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "per request: " + PRECISIONS["fp64_tc"][1] + "; " + PRECISIONS["split"][1],
+        "data": "synthetic (seeded random cells, tight-binding KS data, LRI coefficients, Coulomb matrices)",
+        "config": {"workload": m["workload"], "slots": m["slots"], "hbm_budget_bytes": m["hbm_budget_bytes"]},
+        "latency_ms": m["latency_ms"], "completed": m["completed"], "failed": m["failed"],
+        "peak_running": m["peak_running"], "peak_reserved_bytes": m["peak_reserved_bytes"],
+        "requests": m["requests"], "clocks": m["clocks"],
+    }
     print(json.dumps(line), flush=True)
-    return 0 if len(ok) == n else 1
+    return 0 if m["completed"] == n else 1
 
 
 def _batch_inputs(n):
@@ -588,6 +617,8 @@ def main():
     ap.add_argument("--batch", action="store_true", help="batched workload instead of the headline")
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-sample", type=int, default=8,
+                    help="requests of the serving sample added to the headline line (0: none)")
     ap.add_argument("--rate", type=float, default=20.0, help="request arrival rate (Poisson), per second")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--modes", default="fp64_tc,split,tf32,bf16",

@@ -222,13 +222,16 @@ struct ArF {
   __device__ static T mad(T a, T b, T c) { return fmaf(a, b, c); }
 };
 struct ArDF {
-  using T = float2;   // value x + y with |y| <= ulp(x) / 2
+  using T = float2;   // value x + y; operands normalised (|y| <= ulp(x) / 2), accumulators not
   __device__ static T from(double v) {
     const float h = __double2float_rn(v);
     return make_float2(h, __double2float_rn(v - (double)h));
   }
   __device__ static double to(T v) { return (double)v.x + (double)v.y; }
   __device__ static T zero() { return make_float2(0.f, 0.f); }
+  // c + a b: the high parts' rounded product joins c.x by an exact two-sum; the product's
+  // rounding error, the cross terms and the two-sum error collect in c.y, which is never
+  // renormalised (its own rounding is ~2^-24 of terms of size ulp(c.x): ~n 2^-48 overall)
   __device__ static T mad(T a, T b, T c) {
     const float p = a.x * b.x;
     float e = fmaf(a.x, b.x, -p);   // a.x b.x = p + e exactly
@@ -237,9 +240,7 @@ struct ArDF {
     const float s = c.x + p;        // s + t = c.x + p exactly
     const float bv = s - c.x;
     const float t = (c.x - (s - bv)) + (p - bv);
-    const float lo = t + e + c.y;
-    const float hi = s + lo;
-    return make_float2(hi, lo - (hi - s));
+    return make_float2(s, c.y + (t + e));
   }
 };
 

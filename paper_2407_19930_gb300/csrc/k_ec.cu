@@ -283,24 +283,34 @@ size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 // Workspace of the ln det stage: L[nq], W[nw], A[nw] (complex n x n), pointer tables,
 // lndet/trace/info, output, and for the tensor-core route the digit planes.
 struct EcLayout {
-  size_t o_L, o_W, o_A, o_ptr, o_ld, o_tr, o_inf, o_out, o_wo, o_err;
+  size_t o_L, o_W, o_A, o_ptr, o_ld, o_tr, o_ldc, o_trc, o_inf, o_out, o_wo, o_err;
   size_t o_sx = 0, o_sw = 0, o_sl = 0, o_slh = 0, o_pa = 0, o_pb = 0;
   size_t total = 0;
 };
 
+// q points factorised together: the q <= -q of the mesh (all q are computed in chunks of this
+// size when V(q) turns out not to pair)
+int ec_chunk(const Handle &h) {
+  int c = 0;
+  for (int q = 0; q < h.mesh.size(); ++q) c += q <= h.mesh.neg(q);
+  return c;
+}
+
 EcLayout ec_layout(const Handle &h) {
-  const int n = h.naux, nq = h.mesh.size(), nw = h.ntau, S = h.ec_S;
+  const int n = h.naux, nq = h.mesh.size(), nw = h.ntau, S = h.ec_S, nc = ec_chunk(h);
   const size_t n2 = (size_t)n * n, mat = n2 * sizeof(double2);
-  const int bmax = std::max(nq, nw);
+  const int bmax = std::max(nq, nc * nw);
   EcLayout l;
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off += al256(bytes); return o; };
   l.o_L = take(nq * mat);
   l.o_W = take(nw * mat);
-  l.o_A = take(nw * mat);
-  l.o_ptr = take(((size_t)nq + nw + 8) * 8);
+  l.o_A = take((size_t)nc * nw * mat);   // the (q, omega) of a chunk are factorised in one batch
+  l.o_ptr = take(((size_t)nq + (size_t)nc * nw + 8) * 8);
   l.o_ld = take(((size_t)nq * nw + nq) * 8);
   l.o_tr = take((size_t)nq * nw * 8);
+  l.o_ldc = take((size_t)nq * nw * 8);
+  l.o_trc = take((size_t)nq * nw * 8);
   l.o_inf = take((size_t)(nq + nq * nw) * 4);
   l.o_out = take((size_t)(1 + nq + nw) * 8);
   l.o_wo = take((size_t)nw * 8);
@@ -326,7 +336,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   const size_t n2 = (size_t)n * n;
   cudaStream_t s = h.stream;
   const size_t mat = n2 * sizeof(double2);
-  const int bmax = std::max(nq, nw);
+  const int nc = ec_chunk(h), bmax = std::max(nq, nc * nw);
   const EcLayout lay = ec_layout(h);
   const size_t o_L = lay.o_L, o_W = lay.o_W, o_A = lay.o_A, o_ptr = lay.o_ptr, o_ld = lay.o_ld, o_tr = lay.o_tr,
                o_inf = lay.o_inf, o_out = lay.o_out, o_wo = lay.o_wo, o_err = lay.o_err, o_sx = lay.o_sx,
@@ -393,86 +403,100 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     ++launch_counter();
   }
   const double2 *chi = (const double2 *)h.d_chi_qw.p;
+  // A(q, omega) of the q of a chunk, packed: A[(qi - c0) * nw + k]; each chunk is factorised in
+  // one lockstep batch
   double2 **aptr = ptrs + nq;
-  std::vector<double2 *> ap(nw);
-  for (int k = 0; k < nw; ++k) ap[k] = Am + k * n2;
-  LR_CUDA(cudaMemcpyAsync(aptr, ap.data(), nw * 8, cudaMemcpyHostToDevice, s));
+  double *lndet_c = (double *)(w + lay.o_ldc), *trace_c = (double *)(w + lay.o_trc);
+  LR_CUDA(cudaMemsetAsync(lndet_c, 0, (size_t)nql * nw * 8, s));
   // algorithmic work (8 flops per complex MAC): W = chi0 L with L lower triangular,
   // sum_j (n - j) = n (n + 1) / 2 MACs per row; A = -L^H W on the lower triangle,
   // sum_{i >= j} (n - i) MACs per matrix
   const double dn = n;
   const double fl_w = 8.0 * nw * dn * (dn * (dn + 1) / 2), fl_a = 8.0 * nw * (dn * (dn + 1) * (dn + 2) / 6);
-  for (int qi = 0; qi < nql; ++qi) {
-    const int q = qlist[qi];
-    if (S >= 0) {
-      const double2 *L = Lq + (size_t)qi * n2;
-      oz::split_complex(L, n, oz::OP_N, false, n, n, 1, 0, sl, s);     // B'^T of W = chi0 L
-      oz::split_complex(L, n, oz::OP_H, true, n, n, 1, 0, slh, s);     // A' of L^H W
-      oz::split_complex(chi + (size_t)q * nw * n2, n, oz::OP_N, true, n, n, nw, (long long)n2, sx, s);
-      oz::Out o1;   // W^T, so that the second GEMM reads W column by column as rows
-      o1.C = (double *)Wm;
-      o1.ldc = n;
-      o1.batch_stride = (long long)n2;
-      o1.mode = 2;
-      Handle::Timed t1{nullptr, nullptr, fl_w, 1};
-      LR_CUDA(cudaEventCreate(&t1.a));
-      LR_CUDA(cudaEventCreate(&t1.b));
-      LR_CUDA(cudaEventRecord(t1.a, s));
-      oz::gemm(sx, sl, 2 * n, n, nw, o1, 0, 2, 0, err, s, h);
-      LR_CUDA(cudaEventRecord(t1.b, s));
-      t1.exec_flops = h.oz_exec_flops;
-      h.timed.push_back(t1);
-      oz::split_complex(Wm, n, oz::OP_T, false, n, n, nw, (long long)n2, sw, s);   // B'^T rows j: W[k][j]
-      oz::Out o2;
-      o2.C = (double *)Am;
-      o2.ldc = n;
-      o2.batch_stride = (long long)n2;
-      o2.mode = 1;
-      o2.alpha = -1.0;
-      Handle::Timed t2{nullptr, nullptr, fl_a, 1};
-      LR_CUDA(cudaEventCreate(&t2.a));
-      LR_CUDA(cudaEventCreate(&t2.b));
-      LR_CUDA(cudaEventRecord(t2.a, s));
-      oz::gemm(slh, sw, 2 * n, n, nw, o2, 1, 0, 2, err, s, h);
-      LR_CUDA(cudaEventRecord(t2.b, s));
-      t2.exec_flops = h.oz_exec_flops;
-      h.timed.push_back(t2);
-    } else {
-      // W = chi0(q, omega) L_q  (L lower triangular: k >= j)
-      std::vector<ZGemm> b1, b2;
-      for (int k = 0; k < nw; ++k) {
-        ZGemm z{};
-        z.A = chi + ((size_t)q * nw + k) * n2;
-        z.B = Lq + (size_t)qi * n2;
-        z.C = Wm + k * n2;
-        z.M = z.N = z.K = n;
-        z.lda = z.ldb = z.ldc = n;
-        z.alpha = make_double2(1.0, 0.0);
-        z.beta = make_double2(0.0, 0.0);
-        b1.push_back(z);
-        ZGemm y{};
-        y.A = Lq + (size_t)qi * n2;     // op(A) = L^H: stored [K][M], conjugated
-        y.B = Wm + k * n2;
-        y.C = Am + k * n2;
-        y.M = y.N = y.K = n;
-        y.lda = y.ldb = y.ldc = n;
-        y.alpha = make_double2(-1.0, 0.0);
-        y.beta = make_double2(0.0, 0.0);
-        b2.push_back(y);
+  for (int c0 = 0; c0 < nql; c0 += nc) {
+    const int c1 = std::min(nql, c0 + nc);
+    std::vector<double2 *> ap((size_t)(c1 - c0) * nw);
+    for (size_t b = 0; b < ap.size(); ++b) ap[b] = Am + b * n2;
+    LR_CUDA(cudaMemcpyAsync(aptr, ap.data(), ap.size() * 8, cudaMemcpyHostToDevice, s));
+    for (int qi = c0; qi < c1; ++qi) {
+      const int q = qlist[qi];
+      double2 *Aq = Am + (size_t)(qi - c0) * nw * n2;
+      if (S >= 0) {
+        const double2 *L = Lq + (size_t)qi * n2;
+        oz::split_complex(L, n, oz::OP_N, false, n, n, 1, 0, sl, s);     // B'^T of W = chi0 L
+        oz::split_complex(L, n, oz::OP_H, true, n, n, 1, 0, slh, s);     // A' of L^H W
+        oz::split_complex(chi + (size_t)q * nw * n2, n, oz::OP_N, true, n, n, nw, (long long)n2, sx, s);
+        oz::Out o1;   // W^T, so that the second GEMM reads W column by column as rows
+        o1.C = (double *)Wm;
+        o1.ldc = n;
+        o1.batch_stride = (long long)n2;
+        o1.mode = 2;
+        Handle::Timed t1{nullptr, nullptr, fl_w, 1};
+        LR_CUDA(cudaEventCreate(&t1.a));
+        LR_CUDA(cudaEventCreate(&t1.b));
+        LR_CUDA(cudaEventRecord(t1.a, s));
+        oz::gemm(sx, sl, 2 * n, n, nw, o1, 0, 2, 0, err, s, h);
+        LR_CUDA(cudaEventRecord(t1.b, s));
+        t1.exec_flops = h.oz_exec_flops;
+        h.timed.push_back(t1);
+        oz::split_complex(Wm, n, oz::OP_T, false, n, n, nw, (long long)n2, sw, s);   // B'^T rows j: W[k][j]
+        oz::Out o2;
+        o2.C = (double *)Aq;
+        o2.ldc = n;
+        o2.batch_stride = (long long)n2;
+        o2.mode = 1;
+        o2.alpha = -1.0;
+        Handle::Timed t2{nullptr, nullptr, fl_a, 1};
+        LR_CUDA(cudaEventCreate(&t2.a));
+        LR_CUDA(cudaEventCreate(&t2.b));
+        LR_CUDA(cudaEventRecord(t2.a, s));
+        oz::gemm(slh, sw, 2 * n, n, nw, o2, 1, 0, 2, err, s, h);
+        LR_CUDA(cudaEventRecord(t2.b, s));
+        t2.exec_flops = h.oz_exec_flops;
+        h.timed.push_back(t2);
+      } else {
+        // W = chi0(q, omega) L_q  (L lower triangular: k >= j)
+        std::vector<ZGemm> b1, b2;
+        for (int k = 0; k < nw; ++k) {
+          ZGemm z{};
+          z.A = chi + ((size_t)q * nw + k) * n2;
+          z.B = Lq + (size_t)qi * n2;
+          z.C = Wm + k * n2;
+          z.M = z.N = z.K = n;
+          z.lda = z.ldb = z.ldc = n;
+          z.alpha = make_double2(1.0, 0.0);
+          z.beta = make_double2(0.0, 0.0);
+          b1.push_back(z);
+          ZGemm y{};
+          y.A = Lq + (size_t)qi * n2;     // op(A) = L^H: stored [K][M], conjugated
+          y.B = Wm + k * n2;
+          y.C = Aq + k * n2;
+          y.M = y.N = y.K = n;
+          y.lda = y.ldb = y.ldc = n;
+          y.alpha = make_double2(-1.0, 0.0);
+          y.beta = make_double2(0.0, 0.0);
+          b2.push_back(y);
+        }
+        ZGemmFlags f1;
+        f1.kfrom = 2;
+        zgemm_batched(b1, f1, s, h, 1, fl_w);
+        ZGemmFlags f2;
+        f2.transA = true;
+        f2.conjA = true;
+        f2.kfrom = 1;
+        f2.lower_only = true;
+        zgemm_batched(b2, f2, s, h, 1, fl_a);
       }
-      ZGemmFlags f1;
-      f1.kfrom = 2;
-      zgemm_batched(b1, f1, s, h, 1, fl_w);
-      ZGemmFlags f2;
-      f2.transA = true;
-      f2.conjA = true;
-      f2.kfrom = 1;
-      f2.lower_only = true;
-      zgemm_batched(b2, f2, s, h, 1, fl_a);
     }
-    k_diag_shift<<<nw, 256, 0, s>>>(aptr, n, n, trace + (size_t)q * nw);
+    // A = I - L^H chi0 L of the chunk's (q, omega): trace, then one lockstep Cholesky of all
+    k_diag_shift<<<(unsigned)ap.size(), 256, 0, s>>>(aptr, n, n, trace_c + (size_t)c0 * nw);
     ++launch_counter();
-    potrf_batched(h, aptr, ap, n, n, lndet + (size_t)q * nw, info + nq + (size_t)q * nw, tc);
+    potrf_batched(h, aptr, ap, n, n, lndet_c + (size_t)c0 * nw, info + nq + (size_t)c0 * nw, tc);
+  }
+  for (int qi = 0; qi < nql; ++qi) {   // to the flat (q, omega) order
+    const int q = qlist[qi];
+    LR_CUDA(cudaMemcpyAsync(lndet + (size_t)q * nw, lndet_c + (size_t)qi * nw, nw * 8, cudaMemcpyDeviceToDevice, s));
+    LR_CUDA(cudaMemcpyAsync(trace + (size_t)q * nw, trace_c + (size_t)qi * nw, nw * 8, cudaMemcpyDeviceToDevice, s));
   }
   for (int q : qlist) {   // the integrands of -q
     const int p = h.mesh.neg(q);
