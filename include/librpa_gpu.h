@@ -307,7 +307,10 @@ void librpa_gpu_batch_destroy(librpa_gpu_batch_t b);
  * workers is free and its device-memory estimate (librpa_gpu_estimate_bytes) fits in
  * what is left of the server's HBM budget.  Each worker runs its request on its own
  * stream, from a stream-ordered memory pool, so admitted requests overlap on the device.
- * Once the request is complete, the worker releases its device memory. */
+ * Once the request is complete, the worker releases its device memory.  A request that
+ * fails with E_NOMEM (the device ran out although the estimates fit the budget: memory
+ * held outside the server, or pool fragmentation) is queued again at the head and runs
+ * once more, alone. */
 typedef struct librpa_gpu_server *librpa_gpu_server_t;
 
 typedef struct {

@@ -38,6 +38,7 @@ struct Ticket {
   Clock::time_point t_submit, t_admit, t_done;
   size_t est = 0, peak = 0;
   int slot = -1;
+  bool exclusive = false;   // re-queued after a failed device allocation: runs alone
 };
 
 struct SlotCtx {
@@ -88,6 +89,7 @@ struct librpa_gpu_server {
     if (queue.empty()) return nullptr;
     const size_t avail = budget - in_use;
     Ticket *head = queue.front();
+    if (head->exclusive) return running == 0 ? head : nullptr;   // no backfill past it
     if (head->est <= avail) return head;
     if (ms_between(head->t_submit, Clock::now()) > kAgingMs) return nullptr;
     for (Ticket *t : queue)
@@ -142,6 +144,16 @@ struct librpa_gpu_server {
         std::lock_guard<std::mutex> lk(mu);
         in_use -= t->est;
         --running;
+        if (t->rc == LIBRPA_E_NOMEM && !t->exclusive && !stop) {
+          // the device ran out although the estimates fit the budget (memory held outside the
+          // server, pool fragmentation): run it again once, alone, at the head of the queue
+          t->exclusive = true;
+          t->state = 0;
+          t->slot = -1;
+          queue.push_front(t);
+          cv.notify_all();
+          continue;
+        }
         t->t_done = Clock::now();
         t->state = 2;
         requests[t->h] = 0;
