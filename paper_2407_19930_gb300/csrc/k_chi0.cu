@@ -210,6 +210,7 @@ struct OArgs {
 struct ArD {
   using T = double;
   __device__ static T from(double x) { return x; }
+  __device__ static T load(const double *p) { return *p; }
   __device__ static double to(T x) { return x; }
   __device__ static T zero() { return 0.0; }
   __device__ static T mad(T a, T b, T c) { return fma(a, b, c); }
@@ -217,6 +218,7 @@ struct ArD {
 struct ArF {
   using T = float;
   __device__ static T from(double x) { return (float)x; }
+  __device__ static T load(const double *p) { return (float)*p; }
   __device__ static double to(T x) { return (double)x; }
   __device__ static T zero() { return 0.f; }
   __device__ static T mad(T a, T b, T c) { return fmaf(a, b, c); }
@@ -229,6 +231,8 @@ struct ArDF {
   }
   __device__ static double to(T v) { return (double)v.x + (double)v.y; }
   __device__ static T zero() { return make_float2(0.f, 0.f); }
+  // N and X arrive from their GEMMs already as (hi, lo) pairs in 8-byte slots
+  __device__ static T load(const double *p) { return *reinterpret_cast<const float2 *>(p); }
   // c + a b: the high parts' rounded product joins c.x by an exact two-sum; the product's
   // rounding error, the cross terms and the two-sum error collect in c.y, which is never
   // renormalised (its own rounding is ~2^-24 of terms of size ulp(c.x): ~n 2^-48 overall)
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(256) k_oassemble(OArgs a, int NL) {
     for (int e = tid; e < NL * nU * two; e += nthr) {
       const int q = e / (nU * two), r = e % (nU * two), i = r / two, t = r % two;
       const int nu = nu0 + q;
-      LX[e] = nu < nauxV ? Ar::from((t < nV ? XA : XB)[(size_t)(aoU + i) * ldx + nu * nV + (t % nV)]) : Ar::zero();
+      LX[e] = nu < nauxV ? Ar::load((t < nV ? XA : XB) + (size_t)(aoU + i) * ldx + nu * nV + (t % nV)) : Ar::zero();
     }
     __syncthreads();
     const int nu = nu0 + nl;
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(256) k_oassemble(OArgs a, int NL) {
       for (int r = 0; r < 16; ++r) acc[r] = Ar::zero();
 #pragma unroll 2
       for (int t = 0; t < two; ++t) {
-        const T rn = Ar::from((t < nV ? NB : NA)[(size_t)(nu * nV + (t % nV)) * a.m_all + ucol]);
+        const T rn = Ar::load((t < nV ? NB : NA) + (size_t)(nu * nV + (t % nV)) * a.m_all + ucol);
         const T rgv = RG[t * 64 + col];
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
@@ -878,7 +882,9 @@ void chi0_run_tc(Handle &h) {
     gs.kind = 1;
     gs.rows_per_entry = nao;
     oz::split_gather(gs, np * rows_ag, P.max_m, sag, s);
-    // N-step: N_V = Cpack_V Bg_V^T;  X-step: X_V = Ag_V Cpack_V^T
+    // N-step: N_V = Cpack_V Bg_V^T;  X-step: X_V = Ag_V Cpack_V^T (as FP32 pairs when the O
+    // assembly runs in FP32 pairs)
+    const bool pairs = S >= 4 && S <= oz::SMAX;
     std::vector<oz::Entry> en, ex;
     for (int q = 0; q < np; ++q)
       for (int g = 0; g < 2; ++g)
@@ -893,6 +899,7 @@ void chi0_run_tc(Handle &h) {
           a.C = Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V];
           a.ldc = P.m_all;
           a.alpha = 1.0;
+          a.mode = pairs ? 3 : 0;
           en.push_back(a);
           oz::Entry b{};
           b.a_row0 = e * nao;
@@ -901,6 +908,7 @@ void chi0_run_tc(Handle &h) {
           b.N = rowsV;
           b.K = P.m[V];
           b.C = Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V];
+          b.mode = pairs ? 3 : 0;
           b.ldc = rowsV;
           b.alpha = 1.0;
           ex.push_back(b);

@@ -470,6 +470,12 @@ __global__ void __launch_bounds__(192, 1)
           else
             v = en.alpha * ldexp((double)acc[cb * 16 + j], ea + expoB[en.b_row0 + col] - 14 - 8 * (S - 1));
           double *p;
+          if (en.mode == 3) {   // real, as an unevaluated pair of FP32 numbers (hi, lo)
+            const float hi = __double2float_rn(v);
+            reinterpret_cast<float2 *>(en.C)[(long long)row * en.ldc + col] =
+                make_float2(hi, __double2float_rn(v - (double)hi));
+            continue;
+          }
           if (en.mode == 0)
             p = en.C + (long long)row * en.ldc + col;
           else if (en.mode == 1)

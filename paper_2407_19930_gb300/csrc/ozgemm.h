@@ -74,6 +74,8 @@ void split_ragged(const double *base, const long long *off, const int *Ke, int r
 
 // Output of a GEMM entry.
 //  mode 0: real C[m][n] (ldc);
+//  mode 3: real C[m][n] stored as a pair of FP32 numbers (hi, lo) in the 8 bytes of the double
+//          (beta must be 0);
 //  mode 1: complex C[i][j] (interleaved) from rows m = 2i + c: component c of C[i][j];
 //  mode 2: complex transposed: component c of C[j][i].
 struct Out {
