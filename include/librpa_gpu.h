@@ -256,6 +256,22 @@ int librpa_gpu_get_green(librpa_gpu_t h, int itau, int iR, double *go, double *g
 int librpa_gpu_get_chi0_tau(librpa_gpu_t h, int itau, int iR, double *out);
 int librpa_gpu_get_chi0_freq(librpa_gpu_t h, int iq, int iomega, double *re, double *im);
 
+/* Device-pointer variants (for data already on the GPU, e.g. torch tensors): the same as
+ * set_green / set_coulomb / get_chi0_freq, with the complex matrices as device arrays of
+ * interleaved (re, im) pairs, 16-byte aligned, on the handle's device:
+ *   set_green_dev:     wfc [nbands][n_ao_total] complex (eig and occ stay host arrays: they set
+ *                      the grid range);
+ *   set_coulomb_dev:   V [N_aux][N_aux] complex;
+ *   get_chi0_freq_dev: out [N_aux][N_aux] complex = chi0(q, i omega) at (iq, iomega).
+ * The copies are enqueued on the handle's stream and the calls return without waiting: a
+ * device input must stay valid, and a device output must not be read, until that stream has
+ * reached the copy (work the caller enqueues on the same stream is ordered after it).  Not
+ * accepted on request handles of the serving loop (E_STATE).  Errors: as the host versions. */
+int librpa_gpu_set_green_dev(librpa_gpu_t h, int ispin, int ik, int nbands, const double *eig, const double *occ,
+                             const double *wfc, double efermi);
+int librpa_gpu_set_coulomb_dev(librpa_gpu_t h, int iq, const double *V);
+int librpa_gpu_get_chi0_freq_dev(librpa_gpu_t h, int iq, int iomega, double *out);
+
 /* Stage timings and counters of the last chi0 / ec calls. Errors: E_ARG. */
 int librpa_gpu_get_stats(librpa_gpu_t h, librpa_gpu_stats *s);
 

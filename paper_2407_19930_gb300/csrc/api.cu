@@ -576,6 +576,67 @@ int librpa_gpu_get_chi0_freq(librpa_gpu_t h, int iq, int iw, double *re, double 
   });
 }
 
+int librpa_gpu_set_green_dev(librpa_gpu_t h, int ispin, int ik, int nbands, const double *eig, const double *occ,
+                             const double *wfc, double efermi) {
+  return guarded(h, [&]() -> int {
+    if (!h->have_structure) return fail(h, LIBRPA_E_STATE, "set_green_dev before set_structure");
+    if (h->deferred) return fail(h, LIBRPA_E_STATE, "set_green_dev on a request handle (inputs stay on the host)");
+    if (ispin != 0 || ik < 0 || ik >= h->mesh.size() || nbands != h->nao || !eig || !occ || !wfc ||
+        (uintptr_t)wfc % 16)
+      return fail(h, LIBRPA_E_ARG, "set_green_dev: bad spin/k index, nbands != n_ao total, NULL or misaligned");
+    const int nb = h->nao;
+    for (int n = 0; n < nb; ++n) {
+      if (!(occ[n] >= 0.0 && occ[n] <= 1.0) || !std::isfinite(eig[n]))
+        return fail(h, LIBRPA_E_ARG, "set_green_dev: occupations must be in [0, 1] and energies finite");
+      h->eig[(size_t)ik * nb + n] = eig[n];
+      h->occ[(size_t)ik * nb + n] = occ[n];
+    }
+    cudaSetDevice(h->opts.device);
+    const size_t nk = h->mesh.size(), per_k = (size_t)nb * h->nao;
+    h->ensure(h->d_wfc, nk * per_k * 16);
+    h->ensure(h->d_eig, nk * nb * 8);
+    h->ensure(h->d_occ, nk * nb * 8);
+    LR_CUDA(cudaMemcpyAsync((char *)h->d_wfc.p + ik * per_k * 16, wfc, per_k * 16, cudaMemcpyDeviceToDevice,
+                            h->stream));
+    LR_CUDA(cudaMemcpyAsync((double *)h->d_eig.p + ik * nb, h->eig.data() + ik * nb, nb * 8,
+                            cudaMemcpyHostToDevice, h->stream));
+    LR_CUDA(cudaMemcpyAsync((double *)h->d_occ.p + ik * nb, h->occ.data() + ik * nb, nb * 8,
+                            cudaMemcpyHostToDevice, h->stream));
+    h->efermi_k[ik] = efermi;
+    h->have_k[ik] = 1;
+    h->chi0_done = false;
+    return LIBRPA_OK;
+  });
+}
+
+int librpa_gpu_set_coulomb_dev(librpa_gpu_t h, int iq, const double *V) {
+  return guarded(h, [&]() -> int {
+    if (!h->have_structure) return fail(h, LIBRPA_E_STATE, "set_coulomb_dev before set_structure");
+    if (h->deferred) return fail(h, LIBRPA_E_STATE, "set_coulomb_dev on a request handle (inputs stay on the host)");
+    if (iq < 0 || iq >= h->mesh.size() || !V || (uintptr_t)V % 16)
+      return fail(h, LIBRPA_E_ARG, "set_coulomb_dev: bad q, NULL or misaligned");
+    cudaSetDevice(h->opts.device);
+    const size_t n2 = (size_t)h->naux * h->naux;
+    h->ensure(h->d_vq, n2 * 16 * h->mesh.size());
+    LR_CUDA(cudaMemcpyAsync((char *)h->d_vq.p + n2 * 16 * iq, V, n2 * 16, cudaMemcpyDeviceToDevice, h->stream));
+    h->have_q[iq] = 1;
+    h->vq_sym = -1;
+    return LIBRPA_OK;
+  });
+}
+
+int librpa_gpu_get_chi0_freq_dev(librpa_gpu_t h, int iq, int iw, double *out) {
+  return guarded(h, [&]() -> int {
+    if (!h->chi0_done) return fail(h, LIBRPA_E_STATE, "get_chi0_freq_dev: chi0 not computed");
+    if (iq < 0 || iq >= h->mesh.size() || iw < 0 || iw >= h->ntau || !out || (uintptr_t)out % 16)
+      return fail(h, LIBRPA_E_ARG, "get_chi0_freq_dev: index out of range, NULL or misaligned output");
+    const size_t n2 = (size_t)h->naux * h->naux;
+    LR_CUDA(cudaMemcpyAsync(out, (const char *)h->d_chi_qw.p + ((size_t)iq * h->ntau + iw) * n2 * 16, n2 * 16,
+                            cudaMemcpyDeviceToDevice, h->stream));
+    return LIBRPA_OK;
+  });
+}
+
 int librpa_gpu_get_stats(librpa_gpu_t h, librpa_gpu_stats *s) {
   if (!h || !s) return LIBRPA_E_ARG;
   *s = h->stats;

@@ -302,15 +302,19 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s
 
 // Pipelined, warp-specialised kernel (one CTA = one 128 x 64 output tile of one GEMM entry):
-//   warp 4 (one lane): TMA producer over a ring of NST shared-memory stages, each holding the
+//   warp EW (one lane): TMA producer over a ring of NST shared-memory stages, each holding the
 //     NP digit planes of a 128 x 32 A slice and a 64 x 32 B slice (SWIZZLE_64B, K-major);
-//   warp 5 (one lane): tcgen05.mma issuer; commits free a stage when its MMAs complete and,
-//     at the end of a flush group, signal the epilogue;
-//   warps 0-3: epilogue; warp w owns TMEM lanes 32w..32w+31 (= tile rows); after each flush
-//     group they move the diagonal accumulators into exact int64 register sums and hand the
-//     TMEM columns back to the issuer.
+//   warp EW + 1 (one lane): tcgen05.mma issuer; commits free a stage when its MMAs complete
+//     and, at the end of a flush group, signal the epilogue;
+//   warps 0..EW-1: epilogue; warp w owns TMEM lanes 32 (w % 4) .. + 31 (= tile rows).  With
+//     EW = 8 (digit planes) warp w takes columns 32 (w / 4) .. + 31: after each flush group it
+//     moves the diagonal accumulators into exact int64 register sums (32 per thread) and hands
+//     the TMEM columns back to the issuer.  With EW = 4 (plain BF16 / TF32, one drain at the
+//     end) each warp takes all 64 columns.
 constexpr int PBK = 32;   // K per stage: one 64-byte swizzle row of BF16 (16 TF32 values)
 constexpr int NST = 3;    // pipeline depth
+// epilogue warps of the S variant
+__host__ __device__ constexpr int epi_warps(int S) { return (S == 0 || S == S_TF32) ? 4 : 8; }
 
 // shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart
 __device__ __forceinline__ uint64_t smem_desc64(uint32_t saddr) {
@@ -328,7 +332,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 }
 
 template <int S>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
     k_ozgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const Entry *__restrict__ entries, const Tile *__restrict__ tiles, const int *__restrict__ expoA,
              const int *__restrict__ expoB, int *err) {
@@ -341,6 +345,7 @@ __global__ void __launch_bounds__(192, 1)
   // K steps per flush group: NP pairs x (32 G) x 2^14 <= 2^24 keeps the FP32 sums exact; plain
   // BF16 accumulates over the whole K in FP32
   constexpr int G = PLAIN ? (1 << 30) : 32 / NP;
+  constexpr int EPI_WARPS = epi_warps(S), HALF = BN * 4 / EPI_WARPS;   // HALF: columns per epilogue warp
   constexpr uint32_t TMEM_COLS = tmem_cols<NP>();
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[NST], empty[NST], tfull, tempty;
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(&tfull, 1);
-    mbar_init(&tempty, 4);
+    mbar_init(&tempty, EPI_WARPS);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -372,11 +377,12 @@ __global__ void __launch_bounds__(192, 1)
   const int nsteps = en.K > kbeg ? (en.K - kbeg + KS - 1) / KS : 0;
   const int ngroups = (nsteps + G - 1) / G;
   const int arow = en.a_row0 + m0, brow = en.b_row0 + n0;
-  long long acc[BN];
+  long long acc[HALF];
 #pragma unroll
-  for (int j = 0; j < BN; ++j) acc[j] = 0;
+  for (int j = 0; j < HALF; ++j) acc[j] = 0;
   bool failed = false;
-  if (warp == 4) {
+  const int quad = warp & 3, half = warp >> 2;   // epilogue: TMEM lane quadrant, column half
+  if (warp == EPI_WARPS) {
     if (lane == 0) {
       for (int i = 0; i < nsteps; ++i) {
         const int st = i % NST;
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(192, 1)
         for (int p = 0; p < NP; ++p) tma_load_3d(sb + p * B_BYTES, &tmB, &full[st], k0, brow, p);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == EPI_WARPS + 1) {
     if (lane == 0) {
       for (int i = 0; i < nsteps; ++i) {
         const int st = i % NST, gi = i / G, c = i % G;
@@ -436,13 +442,13 @@ __global__ void __launch_bounds__(192, 1)
       }
       tc_fence_after();
       if constexpr (!PLAIN) {
-#pragma unroll
+#pragma unroll 1
         for (int d = 2; d <= S + 1; ++d) {
           const long long mul = 1LL << (8 * (S + 1 - d));
 #pragma unroll
-          for (int cb = 0; cb < BN / 16; ++cb) {
+          for (int cb = 0; cb < HALF / 16; ++cb) {
             uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d - 2) * BN + cb * 16, r);
+            tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d - 2) * BN + half * HALF + cb * 16, r);
 #pragma unroll
             for (int j = 0; j < 16; ++j) acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) * mul;
           }
@@ -453,16 +459,16 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
     if (!failed) {
-      const int row = m0 + 32 * warp + lane;
+      const int row = m0 + 32 * quad + lane;
       const int ea = (!PLAIN && row < en.M) ? expoA[en.a_row0 + row] : 0;
 #pragma unroll
-      for (int cb = 0; cb < BN / 16; ++cb) {
+      for (int cb = 0; cb < HALF / 16; ++cb) {
         uint32_t r[16];
-        if constexpr (PLAIN) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + cb * 16, r);
+        if constexpr (PLAIN) tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + half * HALF + cb * 16, r);
         if (row >= en.M) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int col = n0 + cb * 16 + j;
+          const int col = n0 + half * HALF + cb * 16 + j;
           if (col >= en.N) break;
           double v;
           if constexpr (PLAIN)
@@ -523,7 +529,7 @@ void launch(const CUtensorMap &ma, const CUtensorMap &mb, const Entry *e, const 
             const int *ea, const int *eb, int *err, cudaStream_t s) {
   const int smem = NST * planes(S) * (BM + BN) * 64 + 1024;
   LR_CUDA(cudaFuncSetAttribute(k_ozgemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k_ozgemm<S><<<ntiles, 192, smem, s>>>(ma, mb, e, t, ea, eb, err);
+  k_ozgemm<S><<<ntiles, 32 * (epi_warps(S) + 2), smem, s>>>(ma, mb, e, t, ea, eb, err);
 }
 
 }  // namespace

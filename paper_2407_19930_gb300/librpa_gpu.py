@@ -126,6 +126,10 @@ _SIGS = {
     "librpa_gpu_batch_run": (ctypes.c_int, [ctypes.c_void_p, _D]),
     "librpa_gpu_batch_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(librpa_gpu_batch_stats)]),
     "librpa_gpu_batch_destroy": (None, [ctypes.c_void_p]),
+    "librpa_gpu_set_green_dev": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
+                                                ctypes.c_void_p, ctypes.c_double]),
+    "librpa_gpu_set_coulomb_dev": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p]),
+    "librpa_gpu_get_chi0_freq_dev": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "librpa_gpu_ec_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "librpa_gpu_destroy": (None, [_H]),
@@ -317,6 +321,21 @@ def librpa_gpu_get_chi0_freq(h, iq, iw, naux):
     re, im = np.zeros((naux, naux)), np.zeros((naux, naux))
     _check(h, load().librpa_gpu_get_chi0_freq(h, int(iq), int(iw), _dp(re), _dp(im)))
     return re + 1j * im
+
+
+def librpa_gpu_set_green_dev(h, ispin, ik, eig, occ, wfc_ptr, efermi):
+    """wfc_ptr: device address of [nbands][n_ao] complex128 (e.g. tensor.data_ptr())."""
+    eig, occ = _f64(eig), _f64(occ)
+    _check(h, load().librpa_gpu_set_green_dev(h, int(ispin), int(ik), len(eig), _dp(eig), _dp(occ), wfc_ptr,
+                                              float(efermi)))
+
+
+def librpa_gpu_set_coulomb_dev(h, iq, v_ptr):
+    _check(h, load().librpa_gpu_set_coulomb_dev(h, int(iq), v_ptr))
+
+
+def librpa_gpu_get_chi0_freq_dev(h, iq, iw, out_ptr):
+    _check(h, load().librpa_gpu_get_chi0_freq_dev(h, int(iq), int(iw), out_ptr))
 
 
 def librpa_gpu_get_stats(h):

@@ -247,6 +247,44 @@ def test_torch_memory_and_stream():
     assert np.array_equal(a["chi_tau"], b["chi_tau"])
 
 
+def test_device_pointer_inputs_and_outputs():
+    """set_green_dev / set_coulomb_dev / get_chi0_freq_dev with torch tensors give the host
+    path's results bit for bit."""
+    torch = pytest.importorskip("torch")
+    inp = syn.config_cubic()
+    st = inp.st
+    grid = ogrid.make_grid(8, *inp.delta_range)
+    ref = _run(inp, grid)
+    dev = torch.device("cuda:0")
+    s = torch.cuda.Stream()
+    h = L.librpa_gpu_create(torch_stream=s)
+    try:
+        L.librpa_gpu_set_structure(h, st.lat, st.pos, st.n_ao, st.n_aux, st.kmesh, st.nspins, st.r_cut)
+        for I, K, R, C in inp.lri:
+            L.librpa_gpu_set_lri_coeffs(h, I, K, R, C)
+        keep = []
+        with torch.cuda.stream(s):
+            for ik in range(st.nk):
+                w = torch.view_as_real(torch.from_numpy(np.ascontiguousarray(inp.wfc[ik]))).contiguous().to(dev)
+                keep.append(w)
+                L.librpa_gpu_set_green_dev(h, 0, ik, inp.eig[ik], inp.occ[ik], w.data_ptr(), inp.efermi)
+            for iq in range(st.nk):
+                v = torch.view_as_real(torch.from_numpy(np.ascontiguousarray(inp.vq[iq]))).contiguous().to(dev)
+                keep.append(v)
+                L.librpa_gpu_set_coulomb_dev(h, iq, v.data_ptr())
+        L.librpa_gpu_set_grid(h, grid["tau"], grid["omega"], grid["w_omega"], grid["gamma"])
+        L.librpa_gpu_chi0(h)
+        ec, ecq, _ = L.librpa_gpu_ec(h, st.nk, None)
+        out = torch.empty((st.naux, st.naux, 2), dtype=torch.float64, device=dev)
+        L.librpa_gpu_get_chi0_freq_dev(h, 1, 3, out.data_ptr())
+        s.synchronize()
+        chi = torch.view_as_complex(out).cpu().numpy()
+    finally:
+        L.librpa_gpu_destroy(h)
+    assert ec == ref["ec"] and np.array_equal(ecq, ref["ec_q"])
+    assert np.array_equal(chi, ref["chi_qw"][1, 3])
+
+
 # ------------------------------------------------------------------ error paths
 
 
