@@ -16,26 +16,40 @@ from .chi0_definition import chi0_definition
 
 
 def spin_factor(nspins: int) -> float:
-    """Spin factor s of chi0: 2 for a spin-unpolarised calculation."""
-    if nspins != 1:
-        raise ValueError("only nspins = 1 is covered")
-    return 2.0
+    """Spin factor s of chi0 per channel: 2 for a spin-unpolarised calculation (one channel
+    standing for both spins), 1 per channel for a spin-polarised one (chi0 = sum over spins)."""
+    if nspins == 1:
+        return 2.0
+    if nspins == 2:
+        return 1.0
+    raise ValueError("nspins must be 1 or 2")
+
+
+def greens(inp, grid):
+    """[(G^occ, G^vir)] per spin channel."""
+    st = inp.st
+    return [green.green(st.kmesh, inp.kfrac, e, o, w, inp.efermi, grid["tau"]) for e, o, w in inp.channels()]
 
 
 def chi0_tau(inp, grid, route="alg1", go=None, gv=None):
-    """chi0(R, tau) as [ntau][nR][N][N]."""
+    """chi0(R, tau) as [ntau][nR][N][N]: the contraction of each spin channel with its own
+    Green's functions, summed.  go / gv: one channel's arrays, or [nspins] of them."""
     st = inp.st
     if go is None:
-        go, gv = green.green(st.kmesh, inp.kfrac, inp.eig, inp.occ, inp.wfc, inp.efermi, grid["tau"])
+        gs = greens(inp, grid)
+    else:
+        gs = [(go, gv)] if st.nspins == 1 else list(zip(go, gv))
     ntau = len(grid["tau"])
     pts = [(iR, it) for it in range(ntau) for iR in range(st.nk)]
     s = spin_factor(st.nspins)
-    if route == "alg1":
-        c = chi0_alg1(st, inp.lri, go, gv, pts, spin=s)
-    elif route == "definition":
-        c = chi0_definition(st, inp.lri, go, gv, pts, spin=s)
-    else:
-        raise ValueError(route)
+    c = 0.0
+    for g_o, g_v in gs:
+        if route == "alg1":
+            c = c + chi0_alg1(st, inp.lri, g_o, g_v, pts, spin=s)
+        elif route == "definition":
+            c = c + chi0_definition(st, inp.lri, g_o, g_v, pts, spin=s)
+        else:
+            raise ValueError(route)
     return c.reshape(ntau, st.nk, st.naux, st.naux)
 
 
@@ -50,9 +64,14 @@ def chi0_q_omega(inp, grid, chi_tau):
 
 
 def rpa_energy(inp, grid, route="alg1", vq=None):
-    """Dict with G, chi0 in every representation and E_c (Ha per cell)."""
+    """Dict with G ([nspins] leading axis when nspins = 2), chi0 in every representation and
+    E_c (Ha per cell)."""
     st = inp.st
-    go, gv = green.green(st.kmesh, inp.kfrac, inp.eig, inp.occ, inp.wfc, inp.efermi, grid["tau"])
+    gs = greens(inp, grid)
+    if st.nspins == 1:
+        go, gv = gs[0]
+    else:
+        go, gv = np.stack([g[0] for g in gs]), np.stack([g[1] for g in gs])
     ct = chi0_tau(inp, grid, route=route, go=go, gv=gv)
     cq = chi0_q_omega(inp, grid, ct)
     v = inp.vq if vq is None else vq

@@ -87,6 +87,17 @@ class Inputs:
     vq: np.ndarray           # (nq, naux, naux) complex Hermitian positive definite
     seed: int = 0
     hr: dict = None          # real-space tight-binding H(R) the KS data came from
+    # spin-polarised requests (st.nspins = 2): KS data per channel, [spin][k][...]; eig, occ and
+    # wfc above then hold channel 0
+    eig_s: np.ndarray = None
+    occ_s: np.ndarray = None
+    wfc_s: np.ndarray = None
+
+    def channels(self) -> list:
+        """[(eig, occ, wfc)] per spin channel."""
+        if self.st.nspins == 1:
+            return [(self.eig, self.occ, self.wfc)]
+        return [(self.eig_s[c], self.occ_s[c], self.wfc_s[c]) for c in range(self.st.nspins)]
 
     @property
     def gap(self) -> float:
@@ -95,10 +106,14 @@ class Inputs:
 
     @property
     def delta_range(self) -> tuple:
-        """(smallest, largest) occupied->virtual transition energy, Ha."""
-        nocc = self.st.nocc
-        return (float(self.eig[:, nocc].min() - self.eig[:, nocc - 1].max()),
-                float(self.eig[:, -1].max() - self.eig[:, 0].min()))
+        """(smallest, largest) occupied->virtual transition energy within a spin channel, Ha."""
+        lo, hi = np.inf, -np.inf
+        for eig, occ, _ in self.channels():
+            o, v = occ > 0, occ < 1
+            if o.any() and v.any():
+                lo = min(lo, float(eig[v].min() - eig[o].max()))
+                hi = max(hi, float(eig[v].max() - eig[o].min()))
+        return (lo, hi)
 
 
 # ----------------------------------------------------------------------------
@@ -334,6 +349,41 @@ def make_inputs(st: Structure, seed: int, vscale=1.0, t0=0.1, min_gap=0.1) -> In
                   lri=lri, vq=vq, seed=seed, hr=hr)
 
 
+def make_inputs_spin(st: Structure, seed: int, vscale=1.0, t0=0.1, min_gap=0.1, identical=False) -> Inputs:
+    """Spin-polarised request (st.nspins = 2): both channels from one H(R), except that the up
+    channel has one more low orbital on atom 0 (its first high on-site level moved to the low
+    one), so it holds one more occupied band.  ``identical`` keeps both channels equal to the
+    spin-unpolarised problem drawn by ``make_inputs`` with the same seed (same random draws)."""
+    assert st.nspins == 2 and st.n_ao[0] > st.n_low[0]
+    s = seed
+    while True:
+        rng = np.random.default_rng(s)
+        hr = tight_binding_hr(st, rng, t0=t0)
+        hr_up = {R: b.copy() for R, b in hr.items()}
+        nocc_up = st.nocc
+        if not identical:
+            i = int(st.n_low[0])   # first high orbital of atom 0
+            hr_up[(0, 0, 0)][i, i] -= 1.0
+            nocc_up += 1
+        chans, ok = [], True
+        for h_c, nocc in ((hr_up, nocc_up), (hr, st.nocc)):
+            kf, eig, wfc = solve_ks(st, h_c)
+            if eig[:, nocc].min() - eig[:, nocc - 1].max() < min_gap:
+                ok = False
+            occ = np.zeros_like(eig)
+            occ[:, :nocc] = 1.0
+            chans.append((eig, occ, wfc, 0.5 * (eig[:, nocc].min() + eig[:, nocc - 1].max())))
+        if ok:
+            break
+        s += 1
+    efermi = float(np.mean([c[3] for c in chans]))   # any common level: it cancels within a channel
+    lri = lri_coefficients(st, rng)
+    vq = coulomb_q(st, rng, scale=vscale)
+    return Inputs(st=st, kfrac=kf, eig=chans[0][0], occ=chans[0][1], wfc=chans[0][2], efermi=efermi,
+                  lri=lri, vq=vq, seed=seed, hr=hr, eig_s=np.stack([c[0] for c in chans]),
+                  occ_s=np.stack([c[1] for c in chans]), wfc_s=np.stack([c[2] for c in chans]))
+
+
 # ----------------------------------------------------------------------------
 # named workloads
 #
@@ -364,6 +414,13 @@ def config_mixed(seed=11, kmesh=(2, 2, 1), vscale=6e-4) -> Inputs:
     rng = np.random.default_rng(seed)
     st = random_cell(rng, 4, kmesh)
     return make_inputs(st, seed, vscale=vscale)
+
+
+def config_spin(seed=1001, vscale=1e-3, kmesh=(2, 2, 2), identical=False) -> Inputs:
+    """The cubic two-atom cell, spin-polarised (nspins = 2)."""
+    st = cubic_two_atom(kmesh=kmesh)
+    st.nspins = 2
+    return make_inputs_spin(st, seed, vscale=vscale, identical=identical)
 
 
 def config_request(index, natoms_range=(2, 64), seed_base=4004, vscale=2e-4) -> Inputs:

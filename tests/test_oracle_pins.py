@@ -322,3 +322,57 @@ def test_pair_transpose_symmetry(cubic, cubic_run):
     for it in range(ct.shape[0]):
         for iR in range(st.nk):
             assert np.abs(ct[it, mi[iR]] - ct[it, iR].T).max() < 1e-13 * scale
+
+
+# ---------------------------------------------------------------- spin-polarised requests (nspins = 2)
+
+
+def test_spin_identical_channels_equal_unpolarised():
+    """Two equal spin channels with s = 1 each are the unpolarised problem with s = 2."""
+    a = syn.config_cubic()
+    b = syn.config_spin(identical=True)
+    g = ogrid.make_grid(6, *a.delta_range)
+    ra, rb = pipeline.rpa_energy(a, g), pipeline.rpa_energy(b, g)
+    assert np.abs(ra["chi_tau"] - rb["chi_tau"]).max() <= 1e-14 * np.abs(ra["chi_tau"]).max()
+    assert abs(ra["ec"] - rb["ec"]) <= 1e-14 * abs(ra["ec"])
+
+
+def test_spin_routes_agree_in_tau():
+    """Polarised channels (one more occupied band spin up): Algorithm 1 on each channel's Green's
+    functions, summed with s = 1, equals the sum over states of both channels in q space."""
+    inp = syn.config_spin()
+    st = inp.st
+    tau = np.array([0.25, 1.3])
+    ct = pipeline.chi0_tau(inp, {"tau": tau})
+    scale = np.abs(ct).max()
+    assert scale > 1.0
+    for iq in range(st.nk):
+        s = sum(chi0_sos(st, inp.lri, inp.kfrac, e, o, w, iq, tau=tau, spin=1.0) for e, o, w in inp.channels())
+        for it in range(len(tau)):
+            q = freq.r_to_q(ct[it], st.kmesh, inp.kfrac, [iq])[0]
+            assert np.abs(q - s[it]).max() < 1e-13 * scale
+    # and the channels really differ: the up channel alone is not half of the sum
+    up = pipeline.chi0_tau(syn.Inputs(st=syn.Structure(**{**st.__dict__, "nspins": 1}), kfrac=inp.kfrac,
+                                      eig=inp.eig_s[0], occ=inp.occ_s[0], wfc=inp.wfc_s[0], efermi=inp.efermi,
+                                      lri=inp.lri, vq=inp.vq), {"tau": tau})
+    assert np.abs(ct - 0.5 * up).max() > 1e-3 * scale
+
+
+@pytest.mark.parametrize("delta,c01,v", [(0.6, 0.7, 1.3), (1.1, 0.2, 0.5)])
+def test_spin_two_level_closed_form(delta, c01, v):
+    """One spin channel with the two-level transition, the other without occupied states:
+    E_c = (1/2)(sqrt(D^2 + 2aD) - D - a) with a = 1 rho^2 V (spin factor 1 per channel)."""
+    st = syn.Structure(lat=np.eye(3) * 50.0, pos=np.zeros((1, 3)), n_ao=np.array([2]), n_aux=np.array([1]),
+                       n_low=np.array([1]), kmesh=(1, 1, 1), nspins=2)
+    eig = np.array([[-delta / 2, delta / 2]])
+    wfc = np.eye(2, dtype=np.complex128)[None]
+    occ_up, occ_dn = np.array([[1.0, 0.0]]), np.array([[0.0, 0.0]])
+    C = np.array([[[0.0, c01], [c01, 0.0]]])
+    inp = syn.Inputs(st=st, kfrac=np.zeros((1, 3)), eig=eig, occ=occ_up, wfc=wfc, efermi=0.0,
+                     lri=[(0, 0, (0, 0, 0), C)], vq=np.array([[[v + 0j]]]),
+                     eig_s=np.stack([eig, eig]), occ_s=np.stack([occ_up, occ_dn]), wfc_s=np.stack([wfc, wfc]))
+    g = ogrid.make_grid(16, delta, delta)
+    out = pipeline.rpa_energy(inp, g)
+    a = 1.0 * (2 * c01) ** 2 * v
+    exact = 0.5 * (math.sqrt(delta ** 2 + 2 * a * delta) - delta - a)
+    assert abs(out["ec"] - exact) < 1e-6 * abs(exact)
