@@ -131,7 +131,8 @@ int librpa_gpu_create(librpa_gpu_t *h, const librpa_gpu_opts *o);
  *   lat[9]   lattice vectors as rows a1, a2, a3 (bohr);
  *   pos      [natoms][3] Cartesian positions (bohr);
  *   n_ao     [natoms] NAOs per atom (1..64); n_aux [natoms] ABFs per atom (1..256);
- *   nk1..nk3 Gamma-centred k-mesh (each >= 1); nspins must be 1 (spin factor s = 2);
+ *   nk1..nk3 Gamma-centred k-mesh (each >= 1); nspins = 1 (one channel standing for both
+ *   spins, spin factor s = 2) or 2 (two channels, s = 1 each, chi0 = sum over channels);
  *   r_cut    LRI cutoff (bohr): set_lri_coeffs rejects blocks whose atoms are farther apart.
  * Resets every other input of the handle.
  * Errors: E_ARG. */
@@ -147,11 +148,11 @@ int librpa_gpu_set_structure(librpa_gpu_t h, int natoms, const double lat[9], co
  * Errors: E_STATE (no structure), E_ARG (indices, |tau_K + R - tau_I| > r_cut, C NULL). */
 int librpa_gpu_set_lri_coeffs(librpa_gpu_t h, int I, int K, const int R[3], const double *C);
 
-/* KS eigen-data of one k point (paper: set_wg_ekb_efermi + set_ao_basis_wfc;
- * Sec. 2, Eq. green_mat).
+/* KS eigen-data of one k point of spin channel ispin (0 .. nspins-1) (paper:
+ * set_wg_ekb_efermi + set_ao_basis_wfc; Sec. 2, Eq. green_mat).
  *   eig [nbands] (Ha), occ [nbands] occupation per spin-orbital in [0, 1];
  *   wfc_re, wfc_im [nbands][n_ao_total]: wfc[n][i] = c_{i,n}(k);
- *   efermi: the chemical potential mu (Ha).
+ *   efermi: the chemical potential mu (Ha), the same for every k point and channel.
  * nbands must equal the total number of NAOs.  The path assumes time-reversal
  * symmetry (real H(R)), which makes G(R, tau) real; with check_level >= 1 librpa_gpu_chi0
  * returns E_NUMERIC if G has an imaginary part above 1e-10 relative.
@@ -248,7 +249,7 @@ int librpa_gpu_ec_noalloc(int naux, int nomega, const double *V, const double *c
                           void *stream, char *msg, size_t msg_len);
 
 /* Inspection of intermediates kept on the device (host copies of one slice):
- *   get_green:      go, gv  [n_ao_total][n_ao_total] at (itau, iR);
+ *   get_green:      go, gv  [n_ao_total][n_ao_total] at (itau, iR), spin channel 0;
  *   get_chi0_tau:   out     [N_aux][N_aux] = chi0(R, tau) at (itau, iR);
  *   get_chi0_freq:  re, im  [N_aux][N_aux] = chi0(q, i omega) at (iq, iomega).
  * Errors: E_STATE (not computed yet), E_ARG, E_CUDA. */

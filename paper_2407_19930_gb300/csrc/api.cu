@@ -136,7 +136,8 @@ void release_device(Handle &h) { free_device_state(h); }
 
 void materialize(Handle &h) {
   if (!h.deferred) return;
-  const size_t nk = h.mesh.size(), nb = h.nao, per_k = nb * h.nao, n2 = (size_t)h.naux * h.naux;
+  const size_t nq = h.mesh.size(), nk = (size_t)h.nspins * nq, nb = h.nao, per_k = nb * h.nao,
+               n2 = (size_t)h.naux * h.naux;
   if (!h.d_wfc.p && !h.stage_wfc.empty()) {
     h.ensure(h.d_wfc, nk * per_k * 16);
     h.ensure(h.d_eig, nk * nb * 8);
@@ -146,8 +147,8 @@ void materialize(Handle &h) {
     LR_CUDA(cudaMemcpyAsync(h.d_occ.p, h.occ.data(), nk * nb * 8, cudaMemcpyHostToDevice, h.stream));
   }
   if (!h.d_vq.p && !h.stage_vq.empty()) {
-    h.ensure(h.d_vq, n2 * 16 * nk);
-    LR_CUDA(cudaMemcpyAsync(h.d_vq.p, h.stage_vq.data(), n2 * 16 * nk, cudaMemcpyHostToDevice, h.stream));
+    h.ensure(h.d_vq, n2 * 16 * nq);
+    LR_CUDA(cudaMemcpyAsync(h.d_vq.p, h.stage_vq.data(), n2 * 16 * nq, cudaMemcpyHostToDevice, h.stream));
   }
   LR_CUDA(cudaStreamSynchronize(h.stream));
 }
@@ -155,10 +156,11 @@ void materialize(Handle &h) {
 size_t estimate_device_bytes(Handle &h) {
   const int ntau_saved = h.ntau;
   if (!h.have_grid) h.ntau = h.opts.n_tau;
-  const size_t nk = h.mesh.size(), nb = h.nao, n2ao = (size_t)h.nao * h.nao, n2 = (size_t)h.naux * h.naux;
-  size_t b = nk * nb * h.nao * 16 + 2 * nk * nb * 8;            // KS data
+  const size_t nk = h.mesh.size(), ns = h.nspins, nb = h.nao, n2ao = (size_t)h.nao * h.nao,
+               n2 = (size_t)h.naux * h.naux;
+  size_t b = ns * (nk * nb * h.nao * 16 + 2 * nk * nb * 8);       // KS data
   b += nk * n2 * 16;                                              // V(q)
-  b += 2 * (size_t)h.ntau * nk * n2ao * 8;                        // G^occ, G^vir
+  b += ns * 2 * (size_t)h.ntau * nk * n2ao * 8;                   // G^occ, G^vir per spin
   b += nk * (size_t)h.ntau * n2 * 16;                             // chi0(q, i omega)
   Chi0Plan P;
   chi0_shape(h, P);
@@ -171,30 +173,40 @@ size_t estimate_device_bytes(Handle &h) {
 
 int chi0_prepare(Handle &h) {
   if (!h.have_structure) return fail(&h, LIBRPA_E_STATE, "chi0 before set_structure");
-  for (int k = 0; k < h.mesh.size(); ++k)
-    if (!h.have_k[k]) return fail(&h, LIBRPA_E_STATE, "chi0: set_green missing for k index " + std::to_string(k));
+  for (size_t k = 0; k < h.have_k.size(); ++k)
+    if (!h.have_k[k])
+      return fail(&h, LIBRPA_E_STATE, "chi0: set_green missing for spin " + std::to_string(k / h.mesh.size()) +
+                                          ", k index " + std::to_string(k % h.mesh.size()));
   {
     std::vector<char> seen(h.natoms, 0);
     for (auto &kv : h.lri) seen[std::get<0>(kv.first)] = 1;
     for (int a = 0; a < h.natoms; ++a)
       if (!seen[a]) return fail(&h, LIBRPA_E_STATE, "chi0: no LRI block for atom " + std::to_string(a));
   }
-  for (int k = 1; k < h.mesh.size(); ++k)
-    if (h.efermi_k[k] != h.efermi_k[0]) return fail(&h, LIBRPA_E_ARG, "chi0: efermi differs between k points");
+  for (size_t k = 1; k < h.efermi_k.size(); ++k)
+    if (h.efermi_k[k] != h.efermi_k[0])
+      return fail(&h, LIBRPA_E_ARG, "chi0: efermi differs between k points or spins");
   cudaSetDevice(h.opts.device);
   if (!h.have_grid) {
-    // transition-energy range of the KS spectrum: smallest virtual minus largest
-    // occupied energy, and largest virtual minus smallest occupied energy
+    // transition-energy range of the KS spectrum, within each spin channel: smallest virtual
+    // minus largest occupied energy, and largest virtual minus smallest occupied energy
     const int nb = h.nao, nk = h.mesh.size();
-    double eo_max = -1e300, eo_min = 1e300, ev_min = 1e300, ev_max = -1e300;
-    for (int k = 0; k < nk; ++k)
-      for (int n = 0; n < nb; ++n) {
-        double e = h.eig[(size_t)k * nb + n], f = h.occ[(size_t)k * nb + n];
-        if (f > 0) { eo_max = std::fmax(eo_max, e); eo_min = std::fmin(eo_min, e); }
-        if (f < 1) { ev_min = std::fmin(ev_min, e); ev_max = std::fmax(ev_max, e); }
-      }
-    double dmin = ev_min - eo_max, dmax = ev_max - eo_min;
-    if (!(dmin > 0)) return fail(&h, LIBRPA_E_ARG, "chi0: no gap between occupied and virtual states");
+    double dmin = 1e300, dmax = -1e300;
+    for (int sp = 0; sp < h.nspins; ++sp) {
+      double eo_max = -1e300, eo_min = 1e300, ev_min = 1e300, ev_max = -1e300;
+      for (int k = 0; k < nk; ++k)
+        for (int n = 0; n < nb; ++n) {
+          const size_t x = ((size_t)sp * nk + k) * nb + n;
+          const double e = h.eig[x], f = h.occ[x];
+          if (f > 0) { eo_max = std::fmax(eo_max, e); eo_min = std::fmin(eo_min, e); }
+          if (f < 1) { ev_min = std::fmin(ev_min, e); ev_max = std::fmax(ev_max, e); }
+        }
+      if (eo_max < -1e299 || ev_min > 1e299) continue;   // no transitions in this channel
+      dmin = std::fmin(dmin, ev_min - eo_max);
+      dmax = std::fmax(dmax, ev_max - eo_min);
+    }
+    if (!(dmin > 0) || dmin > 1e299)
+      return fail(&h, LIBRPA_E_ARG, "chi0: no gap between occupied and virtual states");
     int n = h.opts.n_tau;
     h.tau.resize(n);
     h.omega.resize(n);
@@ -269,7 +281,7 @@ int librpa_gpu_set_structure(librpa_gpu_t h, int natoms, const double lat[9], co
   return guarded(h, [&]() -> int {
     if (natoms < 1 || !lat || !pos || !n_ao || !n_aux || nk1 < 1 || nk2 < 1 || nk3 < 1 || !(r_cut > 0))
       return fail(h, LIBRPA_E_ARG, "set_structure: bad dimensions or NULL arrays");
-    if (nspins != 1) return fail(h, LIBRPA_E_ARG, "set_structure: only nspins = 1 is supported");
+    if (nspins != 1 && nspins != 2) return fail(h, LIBRPA_E_ARG, "set_structure: nspins must be 1 or 2");
     for (int a = 0; a < natoms; ++a)
       if (n_ao[a] < 1 || n_ao[a] > 64 || n_aux[a] < 1 || n_aux[a] > 256)
         return fail(h, LIBRPA_E_ARG, "set_structure: n_ao must be 1..64 and n_aux 1..256 per atom");
@@ -295,10 +307,10 @@ int librpa_gpu_set_structure(librpa_gpu_t h, int natoms, const double lat[9], co
     h->lri.clear();
     h->stage_wfc.clear();
     h->stage_vq.clear();
-    h->eig.assign((size_t)nk * h->nao, 0.0);
-    h->occ.assign((size_t)nk * h->nao, 0.0);
-    h->have_k.assign(nk, 0);
-    h->efermi_k.assign(nk, 0.0);
+    h->eig.assign((size_t)nspins * nk * h->nao, 0.0);
+    h->occ.assign((size_t)nspins * nk * h->nao, 0.0);
+    h->have_k.assign((size_t)nspins * nk, 0);
+    h->efermi_k.assign((size_t)nspins * nk, 0.0);
     h->have_q.assign(nk, 0);
     h->have_grid = h->grid_user = false;
     h->chi0_done = false;
@@ -333,25 +345,27 @@ int librpa_gpu_set_green(librpa_gpu_t h, int ispin, int ik, int nbands, const do
                          const double *wfc_re, const double *wfc_im, double efermi) {
   return guarded(h, [&]() -> int {
     if (!h->have_structure) return fail(h, LIBRPA_E_STATE, "set_green before set_structure");
-    if (ispin != 0 || ik < 0 || ik >= h->mesh.size() || nbands != h->nao || !eig || !occ || !wfc_re || !wfc_im)
+    if (ispin < 0 || ispin >= h->nspins || ik < 0 || ik >= h->mesh.size() || nbands != h->nao || !eig || !occ ||
+        !wfc_re || !wfc_im)
       return fail(h, LIBRPA_E_ARG, "set_green: bad spin/k index, nbands != n_ao total, or NULL");
     const int nb = h->nao;
+    const size_t sk = (size_t)ispin * h->mesh.size() + ik;   // (spin, k) slot
     for (int n = 0; n < nb; ++n) {
       if (!(occ[n] >= 0.0 && occ[n] <= 1.0) || !std::isfinite(eig[n]))
         return fail(h, LIBRPA_E_ARG, "set_green: occupations must be in [0, 1] and energies finite");
-      h->eig[(size_t)ik * nb + n] = eig[n];
-      h->occ[(size_t)ik * nb + n] = occ[n];
+      h->eig[sk * nb + n] = eig[n];
+      h->occ[sk * nb + n] = occ[n];
     }
-    const size_t nk = h->mesh.size(), per_k = (size_t)nb * h->nao;
+    const size_t nk = (size_t)h->nspins * h->mesh.size(), per_k = (size_t)nb * h->nao;
     if (h->deferred) {   // kept on the host until the request is admitted
       h->stage_wfc.resize(nk * per_k * 2);
-      double *w = h->stage_wfc.data() + (size_t)ik * per_k * 2;
+      double *w = h->stage_wfc.data() + sk * per_k * 2;
       for (size_t x = 0; x < per_k; ++x) {
         w[2 * x] = wfc_re[x];
         w[2 * x + 1] = wfc_im[x];
       }
-      h->efermi_k[ik] = efermi;
-      h->have_k[ik] = 1;
+      h->efermi_k[sk] = efermi;
+      h->have_k[sk] = 1;
       h->chi0_done = false;
       return LIBRPA_OK;
     }
@@ -364,15 +378,15 @@ int librpa_gpu_set_green(librpa_gpu_t h, int ispin, int ik, int nbands, const do
       w[2 * x] = wfc_re[x];
       w[2 * x + 1] = wfc_im[x];
     }
-    LR_CUDA(cudaMemcpyAsync((char *)h->d_wfc.p + ik * per_k * 16, w.data(), per_k * 16, cudaMemcpyHostToDevice,
+    LR_CUDA(cudaMemcpyAsync((char *)h->d_wfc.p + sk * per_k * 16, w.data(), per_k * 16, cudaMemcpyHostToDevice,
                             h->stream));
-    LR_CUDA(cudaMemcpyAsync((double *)h->d_eig.p + ik * nb, h->eig.data() + ik * nb, nb * 8,
+    LR_CUDA(cudaMemcpyAsync((double *)h->d_eig.p + sk * nb, h->eig.data() + sk * nb, nb * 8,
                             cudaMemcpyHostToDevice, h->stream));
-    LR_CUDA(cudaMemcpyAsync((double *)h->d_occ.p + ik * nb, h->occ.data() + ik * nb, nb * 8,
+    LR_CUDA(cudaMemcpyAsync((double *)h->d_occ.p + sk * nb, h->occ.data() + sk * nb, nb * 8,
                             cudaMemcpyHostToDevice, h->stream));
     LR_CUDA(cudaStreamSynchronize(h->stream));
-    h->efermi_k[ik] = efermi;
-    h->have_k[ik] = 1;
+    h->efermi_k[sk] = efermi;
+    h->have_k[sk] = 1;
     h->chi0_done = false;
     return LIBRPA_OK;
   });
@@ -479,7 +493,7 @@ int librpa_gpu_chi0(librpa_gpu_t h, double *out_re, double *out_im) {
     h->stats.ms_freq = t;
     for (auto &e : ev) cudaEventDestroy(e);
     h->resolve_timers();
-    h->stats.flop_chi0 = h->plan.flop_per_point * h->ntau * (double)chi0_r_list(h->mesh).size();
+    h->stats.flop_chi0 = h->plan.flop_per_point * h->ntau * (double)chi0_r_list(h->mesh).size() * h->nspins;
     h->stats.launches = launch_counter() - l0;
     h->stats.bytes_device = h->bytes_held;
     h->stats.bytes_device_peak = h->bytes_peak;
@@ -581,29 +595,30 @@ int librpa_gpu_set_green_dev(librpa_gpu_t h, int ispin, int ik, int nbands, cons
   return guarded(h, [&]() -> int {
     if (!h->have_structure) return fail(h, LIBRPA_E_STATE, "set_green_dev before set_structure");
     if (h->deferred) return fail(h, LIBRPA_E_STATE, "set_green_dev on a request handle (inputs stay on the host)");
-    if (ispin != 0 || ik < 0 || ik >= h->mesh.size() || nbands != h->nao || !eig || !occ || !wfc ||
-        (uintptr_t)wfc % 16)
+    if (ispin < 0 || ispin >= h->nspins || ik < 0 || ik >= h->mesh.size() || nbands != h->nao || !eig || !occ ||
+        !wfc || (uintptr_t)wfc % 16)
       return fail(h, LIBRPA_E_ARG, "set_green_dev: bad spin/k index, nbands != n_ao total, NULL or misaligned");
     const int nb = h->nao;
+    const size_t sk = (size_t)ispin * h->mesh.size() + ik;
     for (int n = 0; n < nb; ++n) {
       if (!(occ[n] >= 0.0 && occ[n] <= 1.0) || !std::isfinite(eig[n]))
         return fail(h, LIBRPA_E_ARG, "set_green_dev: occupations must be in [0, 1] and energies finite");
-      h->eig[(size_t)ik * nb + n] = eig[n];
-      h->occ[(size_t)ik * nb + n] = occ[n];
+      h->eig[sk * nb + n] = eig[n];
+      h->occ[sk * nb + n] = occ[n];
     }
     cudaSetDevice(h->opts.device);
-    const size_t nk = h->mesh.size(), per_k = (size_t)nb * h->nao;
+    const size_t nk = (size_t)h->nspins * h->mesh.size(), per_k = (size_t)nb * h->nao;
     h->ensure(h->d_wfc, nk * per_k * 16);
     h->ensure(h->d_eig, nk * nb * 8);
     h->ensure(h->d_occ, nk * nb * 8);
-    LR_CUDA(cudaMemcpyAsync((char *)h->d_wfc.p + ik * per_k * 16, wfc, per_k * 16, cudaMemcpyDeviceToDevice,
+    LR_CUDA(cudaMemcpyAsync((char *)h->d_wfc.p + sk * per_k * 16, wfc, per_k * 16, cudaMemcpyDeviceToDevice,
                             h->stream));
-    LR_CUDA(cudaMemcpyAsync((double *)h->d_eig.p + ik * nb, h->eig.data() + ik * nb, nb * 8,
+    LR_CUDA(cudaMemcpyAsync((double *)h->d_eig.p + sk * nb, h->eig.data() + sk * nb, nb * 8,
                             cudaMemcpyHostToDevice, h->stream));
-    LR_CUDA(cudaMemcpyAsync((double *)h->d_occ.p + ik * nb, h->occ.data() + ik * nb, nb * 8,
+    LR_CUDA(cudaMemcpyAsync((double *)h->d_occ.p + sk * nb, h->occ.data() + sk * nb, nb * 8,
                             cudaMemcpyHostToDevice, h->stream));
-    h->efermi_k[ik] = efermi;
-    h->have_k[ik] = 1;
+    h->efermi_k[sk] = efermi;
+    h->have_k[sk] = 1;
     h->chi0_done = false;
     return LIBRPA_OK;
   });

@@ -113,6 +113,7 @@ struct Handle {
   // structure
   bool have_structure = false;
   int natoms = 0, nao = 0, naux = 0, nspins = 1;
+  int cur_spin = 0;   // spin channel the chi0 contraction is working on
   double lat[9]{};
   std::vector<double> pos;
   std::vector<int> n_ao, n_aux, ao_off, aux_off;
@@ -198,7 +199,7 @@ struct MergedChi0 {
 };
 // returns true when the launches were replayed from the captured graph
 bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m);
-// whether h takes part in chi0_run_merged (its chi0 runs on the FP64 route)
+// whether h takes part in chi0_run_merged (FP64 route, one spin channel)
 bool chi0_fits_one_batch(const Handle &h);
 
 // lattice vectors R whose chi0(R, tau) is computed (R <= -R in the flat BvK order); the others

@@ -136,6 +136,14 @@ struct Point {
   int R[3];
 };
 
+// G of the spin channel being contracted ([spin][g][tau][R][i][j]) and the spin factor of chi0 per
+// channel: 2 for the single unpolarised channel, 1 per channel when nspins = 2 (chi0 = sum over
+// channels; the second channel's final GEMM accumulates, beta = 1)
+const double *g_spin(const Handle &h) {
+  return (const double *)h.d_g.p + (size_t)h.cur_spin * 2 * h.ntau * h.mesh.size() * h.nao * h.nao;
+}
+double spin_factor(const Handle &h) { return h.nspins == 1 ? 2.0 : 1.0; }
+
 // Bg[p][g][V][kappa][lambda] = G^g(tau_p)[bvk(R1_kappa - R_p - R2'_lambda)][ao_lambda][ao_kappa]
 __global__ void k_gather_bg(const double *__restrict__ G, size_t g_gstride, const Point *__restrict__ pts,
                             const int *__restrict__ uni, const int *__restrict__ lam, const long long *lam_off,
@@ -609,7 +617,7 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
   LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
   LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
   OArgs oa;
-  oa.G = (const double *)h.d_g.p;
+  oa.G = g_spin(h);
   oa.g_gstride = (size_t)h.ntau * h.mesh.size() * h.nao * h.nao;
   oa.nR_stride = h.mesh.size();
   oa.nao = h.nao;
@@ -734,12 +742,12 @@ void fp64_gather(Handle &h, const Point *dpts, int np, const Fp64Ws &w) {
   int max_m = 0;
   for (int a = 0; a < nat; ++a) max_m = std::max(max_m, P.m[a]);
   dim3 grid((unsigned)(((long long)P.m_all * max_m + 255) / 256), (unsigned)(np * 2 * nat));
-  k_gather_bg<<<grid, 256, 0, h.stream>>>((const double *)h.d_g.p, g_gstride, dpts, (const int *)P.d_uni.p,
+  k_gather_bg<<<grid, 256, 0, h.stream>>>(g_spin(h), g_gstride, dpts, (const int *)P.d_uni.p,
                                           (const int *)P.d_lam.p, (const long long *)P.t_lam_off.p,
                                           (const int *)P.t_m.p, (const long long *)P.t_bg_off.p, nat, P.m_all, nR,
                                           nao, h.mesh.n1, h.mesh.n2, h.mesh.n3, P.bg_sz, 2 * P.bg_sz, w.Bg);
   dim3 grid2((unsigned)(((long long)nao * max_m + 255) / 256), (unsigned)(np * 2 * nat));
-  k_gather_ag<<<grid2, 256, 0, h.stream>>>((const double *)h.d_g.p, g_gstride, dpts, (const int *)P.d_lam.p,
+  k_gather_ag<<<grid2, 256, 0, h.stream>>>(g_spin(h), g_gstride, dpts, (const int *)P.d_lam.p,
                                            (const long long *)P.t_lam_off.p, (const int *)P.t_m.p,
                                            (const long long *)P.t_ag_off.p, nat, nR, nao, h.mesh.n1, h.mesh.n2,
                                            h.mesh.n3, P.ag_sz, 2 * P.ag_sz, w.Ag);
@@ -770,13 +778,13 @@ void fp64_final(Handle &h, const std::vector<Point> &pts, const Fp64Ws &w, std::
   const Chi0Plan &P = h.plan;
   const double *Cp = (const double *)h.d_cpack.p;
   const int naux = h.naux, nR = h.mesh.size();
-  const double spin = 2.0;
+  const double spin = spin_factor(h), beta = h.cur_spin > 0 ? 1.0 : 0.0;
   for (size_t q = 0; q < pts.size(); ++q) {
     double *chi = (double *)h.d_chi_tau.p + ((size_t)pts[q].itau * nR + pts[q].iR) * naux * naux;
     for (int U = 0; U < h.natoms; ++U) {
       const int K = h.n_ao[U] * P.m[U];
       DGemm df{Cp + P.cp_off[U], w.Ow + q * P.o_sz + P.o_off[U], chi + (size_t)h.aux_off[U] * naux, h.n_aux[U],
-               naux, K, K, K, naux, -spin, 0.0};
+               naux, K, K, K, naux, -spin, beta};
       b.push_back(df);
     }
   }
@@ -850,8 +858,9 @@ void chi0_run_tc(Handle &h) {
   oz::Sliced cpnx, cpf;
   oz::sliced_bind(cpnx, P.cp_nx.p, P.cpnx_rows, P.max_m, S);
   oz::sliced_bind(cpf, P.cp_f.p, naux, P.max_nm, S);
-  const double spin = 2.0;
+  const double spin = spin_factor(h);
   const size_t g_gstride = (size_t)ntau * nR * nao * nao;
+  for (h.cur_spin = 0; h.cur_spin < h.nspins; ++h.cur_spin)
   for (long long p0 = 0; p0 < total_pts; p0 += npb) {
     const int np = (int)std::min(npb, total_pts - p0);
     std::vector<Point> pts = make_points(h, rl, p0, np);
@@ -860,7 +869,7 @@ void chi0_run_tc(Handle &h) {
     // digit planes of the gathered Green's-function operands, straight from G
     oz::GatherSrc gs;
     gs.kind = 0;
-    gs.G = (const double *)h.d_g.p;
+    gs.G = g_spin(h);
     gs.g_gstride = (long long)g_gstride;
     gs.nR = nR;
     gs.nao = nao;
@@ -945,11 +954,13 @@ void chi0_run_tc(Handle &h) {
         f.C = chi + (size_t)h.aux_off[U] * naux;
         f.ldc = naux;
         f.alpha = -spin;
+        f.beta = h.cur_spin > 0 ? 1.0 : 0.0;
         ef.push_back(f);
       }
     }
     timed_grouped(h, cpf, sod, ef, err, P.gargs3);
   }
+  h.cur_spin = 0;
   fill_partners(h);
   int e_host = 0;
   LR_CUDA(cudaMemcpyAsync(&e_host, err, 4, cudaMemcpyDeviceToHost, s));
@@ -975,6 +986,7 @@ void chi0_run(Handle &h, double *ms_gemm) {
   const long long npb = dw.npb;
   h.ensure(P.ws, dw.total);
   const Fp64Ws w = fp64_ws(h, npb);
+  for (h.cur_spin = 0; h.cur_spin < h.nspins; ++h.cur_spin)
   for (long long p0 = 0; p0 < total_pts; p0 += npb) {
     const int np = (int)std::min(npb, total_pts - p0);
     std::vector<Point> pts = make_points(h, rl, p0, np);
@@ -989,6 +1001,7 @@ void chi0_run(Handle &h, double *ms_gemm) {
     fp64_final(h, pts, w, b2);
     dgemm_batched(h, b2, s, P.gargs2, &P.var_fin);
   }
+  h.cur_spin = 0;
   fill_partners(h);
   LR_CUDA(cudaStreamSynchronize(s));
   if (ms_gemm) *ms_gemm = 0;
@@ -1001,6 +1014,7 @@ bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
   const size_t nh = hs.size();
   bool fresh = m.gens.size() != nh;
   for (size_t i = 0; i < nh && !fresh; ++i) fresh = m.gens[i] != hs[i]->plan.gen || m.hs[i] != hs[i];
+  for (Handle *h : hs) h->cur_spin = 0;   // one channel (nspins = 1 handles only)
   if (fresh) {
     m.reset();
     m.hs = hs;
@@ -1111,7 +1125,7 @@ bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
   return false;
 }
 
-bool chi0_fits_one_batch(const Handle &h) { return h.chi0_S < 0; }
+bool chi0_fits_one_batch(const Handle &h) { return h.chi0_S < 0 && h.nspins == 1; }
 
 void MergedChi0::reset() {
   if (exec) cudaGraphExecDestroy(exec);

@@ -76,7 +76,7 @@ double green_build(Handle &h) {
   const size_t n2 = (size_t)nao * nao;
   const double mu = h.efermi_k[0];
   cudaStream_t s = h.stream;
-  h.ensure(h.d_g, 2 * (size_t)ntau * nR * n2 * sizeof(double));
+  h.ensure(h.d_g, (size_t)h.nspins * 2 * ntau * nR * n2 * sizeof(double));   // [spin][g][tau][R][i][j]
   // workspace: weights, P, twiddles, max; the KS data is already on the device
   const size_t b_e = (size_t)nk * nb * 8, b_w = 2 * b_e, b_p = 2 * (size_t)nk * n2 * 16,
                b_t = (size_t)nk * nR * 16;
@@ -84,8 +84,8 @@ double green_build(Handle &h) {
   const size_t o_w = 0, o_p = o_w + al(b_w), o_t = o_p + al(b_p), o_m = o_t + al(b_t);
   h.ensure(h.work, green_work_bytes(h));
   char *wk = (char *)h.work.p;
-  const double2 *d_wfc = (const double2 *)h.d_wfc.p;
-  const double *d_eig = (const double *)h.d_eig.p, *d_occ = (const double *)h.d_occ.p;
+  const double2 *d_wfc0 = (const double2 *)h.d_wfc.p;
+  const double *d_eig0 = (const double *)h.d_eig.p, *d_occ0 = (const double *)h.d_occ.p;
   double *d_w = (double *)(wk + o_w);
   double2 *d_P = (double2 *)(wk + o_p), *d_tw = (double2 *)(wk + o_t);
   unsigned long long *d_max = (unsigned long long *)(wk + o_m);
@@ -107,51 +107,55 @@ double green_build(Handle &h) {
   LR_CUDA(cudaMemcpyAsync(d_tw, tw.data(), b_t, cudaMemcpyHostToDevice, s));
   LR_CUDA(cudaStreamSynchronize(s));   // tw is a host temporary
   LR_CUDA(cudaMemsetAsync(d_max, 0, 16, s));
-  // band ranges with non-zero occupied / virtual weight per k
-  std::vector<int> olo(nk, nb), ohi(nk, 0), vlo(nk, nb), vhi(nk, 0);
-  for (int k = 0; k < nk; ++k)
-    for (int n = 0; n < nb; ++n) {
-      const double f = h.occ[(size_t)k * nb + n];
-      if (f > 0) { olo[k] = std::min(olo[k], n); ohi[k] = n + 1; }
-      if (f < 1) { vlo[k] = std::min(vlo[k], n); vhi[k] = n + 1; }
-    }
   const size_t g_stride = (size_t)ntau * nR * n2;
-  for (int it = 0; it < ntau; ++it) {
-    k_weights<<<(nk * nb + 255) / 256, 256, 0, s>>>(d_eig, d_occ, mu, h.tau[it], nk * nb, d_w);
-    ++launch_counter();
-    std::vector<ZGemm> batch;
-    for (int g = 0; g < 2; ++g)
-      for (int k = 0; k < nk; ++k) {
-        const int lo = g == 0 ? olo[k] : vlo[k], hi = g == 0 ? ohi[k] : vhi[k];
-        ZGemm z{};
-        z.A = d_wfc + ((size_t)k * nb + lo) * nao;
-        z.B = z.A;
-        z.C = d_P + ((size_t)g * nk + k) * n2;
-        z.kscale = d_w + (size_t)g * nk * nb + (size_t)k * nb + lo;
-        z.M = nao;
-        z.N = nao;
-        z.K = hi > lo ? hi - lo : 0;
-        z.lda = z.ldb = nao;
-        z.ldc = nao;
-        z.alpha = make_double2(1.0, 0.0);
-        z.beta = make_double2(0.0, 0.0);
-        if (z.K == 0) {
-          LR_CUDA(cudaMemsetAsync(z.C, 0, n2 * 16, s));
-          continue;
-        }
-        batch.push_back(z);
+  for (int sp = 0; sp < h.nspins; ++sp) {   // one spin channel at a time, own KS data, own G
+    const double2 *d_wfc = d_wfc0 + (size_t)sp * nk * nb * nao;
+    const double *d_eig = d_eig0 + (size_t)sp * nk * nb, *d_occ = d_occ0 + (size_t)sp * nk * nb;
+    double *d_gs = (double *)h.d_g.p + (size_t)sp * 2 * g_stride;
+    // band ranges with non-zero occupied / virtual weight per k
+    std::vector<int> olo(nk, nb), ohi(nk, 0), vlo(nk, nb), vhi(nk, 0);
+    for (int k = 0; k < nk; ++k)
+      for (int n = 0; n < nb; ++n) {
+        const double f = h.occ[((size_t)sp * nk + k) * nb + n];
+        if (f > 0) { olo[k] = std::min(olo[k], n); ohi[k] = n + 1; }
+        if (f < 1) { vlo[k] = std::min(vlo[k], n); vhi[k] = n + 1; }
       }
-    ZGemmFlags f;
-    f.transA = true;   // A stored [band][i]
-    f.conjB = true;    // B = conj(wfc) stored [band][j]
-    f.lower_only = true;
-    zgemm_batched(batch, f, s, h);
-    const size_t nthr = 2 * n2;
-    k_phase_sum<<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(d_P, d_tw, nk, nR, nao, 1.0 / nk,
-                                                              (double *)h.d_g.p + (size_t)it * nR * n2, g_stride,
-                                                              d_max);
-    ++launch_counter();
-    LR_CUDA(cudaGetLastError());
+    for (int it = 0; it < ntau; ++it) {
+      k_weights<<<(nk * nb + 255) / 256, 256, 0, s>>>(d_eig, d_occ, mu, h.tau[it], nk * nb, d_w);
+      ++launch_counter();
+      std::vector<ZGemm> batch;
+      for (int g = 0; g < 2; ++g)
+        for (int k = 0; k < nk; ++k) {
+          const int lo = g == 0 ? olo[k] : vlo[k], hi = g == 0 ? ohi[k] : vhi[k];
+          ZGemm z{};
+          z.A = d_wfc + ((size_t)k * nb + lo) * nao;
+          z.B = z.A;
+          z.C = d_P + ((size_t)g * nk + k) * n2;
+          z.kscale = d_w + (size_t)g * nk * nb + (size_t)k * nb + lo;
+          z.M = nao;
+          z.N = nao;
+          z.K = hi > lo ? hi - lo : 0;
+          z.lda = z.ldb = nao;
+          z.ldc = nao;
+          z.alpha = make_double2(1.0, 0.0);
+          z.beta = make_double2(0.0, 0.0);
+          if (z.K == 0) {
+            LR_CUDA(cudaMemsetAsync(z.C, 0, n2 * 16, s));
+            continue;
+          }
+          batch.push_back(z);
+        }
+      ZGemmFlags f;
+      f.transA = true;   // A stored [band][i]
+      f.conjB = true;    // B = conj(wfc) stored [band][j]
+      f.lower_only = true;
+      zgemm_batched(batch, f, s, h);
+      const size_t nthr = 2 * n2;
+      k_phase_sum<<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(d_P, d_tw, nk, nR, nao, 1.0 / nk,
+                                                                d_gs + (size_t)it * nR * n2, g_stride, d_max);
+      ++launch_counter();
+      LR_CUDA(cudaGetLastError());
+    }
   }
   unsigned long long mx[2];
   LR_CUDA(cudaMemcpyAsync(mx, d_max, 16, cudaMemcpyDeviceToHost, s));

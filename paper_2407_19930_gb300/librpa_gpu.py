@@ -464,8 +464,9 @@ def set_inputs(h, inp, grid=None):
     librpa_gpu_set_structure(h, st.lat, st.pos, st.n_ao, st.n_aux, st.kmesh, st.nspins, st.r_cut)
     for I, K, R, C in inp.lri:
         librpa_gpu_set_lri_coeffs(h, I, K, R, C)
-    for ik in range(st.nk):
-        librpa_gpu_set_green(h, 0, ik, inp.eig[ik], inp.occ[ik], inp.wfc[ik], inp.efermi)
+    for isp, (eig, occ, wfc) in enumerate(inp.channels()):
+        for ik in range(st.nk):
+            librpa_gpu_set_green(h, isp, ik, eig[ik], occ[ik], wfc[ik], inp.efermi)
     for iq in range(st.nk):
         librpa_gpu_set_coulomb(h, iq, inp.vq[iq])
     if grid is not None:

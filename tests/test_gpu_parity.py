@@ -57,6 +57,8 @@ CONFIGS = {
                       n_low=np.array([2]), kmesh=(1, 1, 1)), 5, vscale=1e-2),
     "cubic_3x1x2": lambda: syn.make_inputs(
         syn.cubic_two_atom(nao=5, naux=33, nlow=2, kmesh=(3, 1, 2)), 31, vscale=2e-3),
+    # spin-polarised (nspins = 2): one more occupied band in the up channel
+    "cubic_spin": lambda: syn.config_spin(),
     # 9 cells of which 8 pair up as (R, -R): most chi0(R, tau) come from the pair symmetry
     "cubic_3x3x1": lambda: syn.make_inputs(
         syn.cubic_two_atom(nao=4, naux=16, nlow=2, kmesh=(3, 3, 1)), 41, vscale=2e-3),
@@ -75,8 +77,9 @@ def case(request):
 
 def test_green(case):
     name, inp, grid, ref, gpu = case
-    assert _rel(gpu["go"], ref["go"]) < TOL_G
-    assert _rel(gpu["gv"], ref["gv"]) < TOL_G
+    go, gv = (ref["go"], ref["gv"]) if inp.st.nspins == 1 else (ref["go"][0], ref["gv"][0])   # channel 0
+    assert _rel(gpu["go"], go) < TOL_G
+    assert _rel(gpu["gv"], gv) < TOL_G
 
 
 def test_chi0_tau(case):
@@ -115,7 +118,7 @@ def _opts(precision=L.LIBRPA_FP64, chi0_slices=0, ec_slices=0):
     return o
 
 
-@pytest.fixture(scope="module", params=["cubic", "mixed", "cubic_3x1x2", "cubic_3x3x1"])
+@pytest.fixture(scope="module", params=["cubic", "mixed", "cubic_3x1x2", "cubic_3x3x1", "cubic_spin"])
 def tc_case(request):
     """Same inputs as the FP64 parity cases, run with the FP64-accurate tensor-core mode
     (5 BF16 digit planes per operand in the chi0 and ln det GEMMs)."""
