@@ -63,7 +63,9 @@ extern "C" {
  * (row value = 2^E sum_s d_s 2^{-7-8(s-1)}, |d_s| <= 128), digit products accumulated exactly
  * and summed in FP64: S = 5 keeps 39 bits per operand (FP64-accurate to ~1e-12 relative),
  * S = 3 about 23 bits.  The plain forms round every element once, to BF16 (8 significant
- * bits) or to TF32 (11 bits, on the TF32 tensor cores), and accumulate in FP32.  The
+ * bits) or to TF32 (11 bits, on the TF32 tensor cores), and accumulate in FP32; the 3xTF32
+ * split writes x = hi + lo with hi = tf32(x), lo = tf32(x - hi) and sums hi hi + hi lo + lo hi
+ * in FP32 (about 21 bits).  The
  * exponentials of G(tau), the transform weights, the Cholesky factorisations' diagonal blocks
  * and the E_c sum always stay FP64. */
 #define LIBRPA_FP64 0     /* every step in FP64 on the FP64 pipes (DMMA / DFMA) */
@@ -71,6 +73,7 @@ extern "C" {
 #define LIBRPA_SPLIT 2    /* chi0 GEMMs with 3 digit planes (mixed), ln det GEMMs with 5 */
 #define LIBRPA_BF16 3     /* chi0 GEMMs in plain BF16 (FP32 accumulation), ln det GEMMs with 5 */
 #define LIBRPA_TF32 4     /* chi0 GEMMs in plain TF32 (FP32 accumulation), ln det GEMMs with 5 */
+#define LIBRPA_TF32X3 5   /* chi0 GEMMs as 3xTF32 split products (FP32 accumulation), ln det with 5 */
 
 typedef struct librpa_gpu *librpa_gpu_t;
 
@@ -87,7 +90,7 @@ typedef struct {
   librpa_gpu_free_fn dev_free;   /* NULL = cudaFree */
   void *alloc_ctx;               /* passed to dev_alloc / dev_free */
   int n_tau;                     /* grid size (tau = omega points) when the library builds the grid */
-  int precision;                 /* LIBRPA_FP64, LIBRPA_FP64_TC, LIBRPA_SPLIT, LIBRPA_BF16 or LIBRPA_TF32 */
+  int precision;                 /* LIBRPA_FP64, _FP64_TC, _SPLIT, _BF16, _TF32 or _TF32X3 */
   size_t hbm_budget;             /* bytes the handle may allocate; 0 = no limit */
   int check_level;               /* 0 = none; 1 = check G is real and the pivots finite */
   int chi0_slices;               /* 0 = from precision; 1..5 = digit planes of the chi0 GEMMs */

@@ -239,7 +239,7 @@ void librpa_gpu_default_opts(librpa_gpu_opts *o) {
 int librpa_gpu_create(librpa_gpu_t *hp, const librpa_gpu_opts *o) {
   if (!hp || !o) return LIBRPA_E_ARG;
   *hp = nullptr;
-  if (o->n_tau < 1 || o->n_tau > 64 || o->precision < LIBRPA_FP64 || o->precision > LIBRPA_TF32 ||
+  if (o->n_tau < 1 || o->n_tau > 64 || o->precision < LIBRPA_FP64 || o->precision > LIBRPA_TF32X3 ||
       o->chi0_slices < 0 || o->chi0_slices > 5 || o->ec_slices < 0 || o->ec_slices > 5)
     return LIBRPA_E_ARG;
   int ndev = 0;
@@ -253,8 +253,8 @@ int librpa_gpu_create(librpa_gpu_t *hp, const librpa_gpu_opts *o) {
   h->opts = *o;
   {
     // arithmetic per stage (-1 = FP64 pipes, 0 = plain BF16, 1..5 = digit planes, 6 = plain
-    // TF32): presets, then explicit overrides
-    static const int chi0_preset[5] = {-1, 5, 3, 0, 6}, ec_preset[5] = {-1, 5, 5, 5, 5};
+    // TF32, 7 = 3xTF32): presets, then explicit overrides
+    static const int chi0_preset[6] = {-1, 5, 3, 0, 6, 7}, ec_preset[6] = {-1, 5, 5, 5, 5, 5};
     h->chi0_S = o->chi0_slices ? o->chi0_slices : chi0_preset[o->precision];
     h->ec_S = o->ec_slices ? o->ec_slices : ec_preset[o->precision];
   }

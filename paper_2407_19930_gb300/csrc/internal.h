@@ -97,7 +97,8 @@ struct Chi0Plan {
 // ----------------------------------------------------------------- handle
 struct Handle {
   librpa_gpu_opts opts{};
-  int chi0_S = -1;  // chi0 GEMMs: -1 = FP64 pipes, 0 = plain BF16, 1..5 = BF16 digit planes, 6 = plain TF32
+  int chi0_S = -1;  // chi0 GEMMs: -1 = FP64 pipes, 0 = plain BF16, 1..5 = BF16 digit planes, 6 = plain TF32,
+                    // 7 = 3xTF32
   int ec_S = -1;    // ln det GEMMs: same encoding
   cudaStream_t stream = nullptr;
   bool own_stream = false;

@@ -607,7 +607,7 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
   }
   // arithmetic: FP64 pipes for the FP64 mode, FP32 for the mixed modes, FP32 pairs (~48 bits)
   // for the FP64-accurate tensor-core mode
-  const int ar = h.chi0_S < 0 ? 0 : (h.chi0_S <= 3 || h.chi0_S == oz::S_TF32) ? 1 : 2;
+  const int ar = h.chi0_S < 0 ? 0 : (h.chi0_S >= 4 && h.chi0_S <= oz::SMAX) ? 2 : 1;
   const size_t esz = ar == 1 ? sizeof(float) : 8;
   int NL = 4;
   auto smem_for = [&](int nl) { return (size_t)(maxn * 2 * maxn + 2 * maxn * 64 + nl * maxn * 2 * maxn) * esz; };

@@ -163,16 +163,32 @@ __global__ void k_plain(Src src, int rows, int K, int kpad, int row0, __nv_bfloa
   dig[(long long)row0 * kpad + x] = __double2bfloat16(k < K ? src.get(r, k) : 0.0);
 }
 
+__device__ __forceinline__ float to_tf32(float f) {   // round to nearest, ties away
+  uint32_t t;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(f));
+  return __uint_as_float(t);
+}
+
+// 3xTF32 split: plane 0 = tf32(x), plane 1 = tf32(x - plane 0)
+template <class Src>
+__global__ void k_split_tf32x3(Src src, int rows, int K, int kpad, int row0, long long plane, float *dig) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= (long long)rows * kpad) return;
+  const int r = (int)(x / kpad), k = (int)(x % kpad);
+  const double v = k < K ? src.get(r, k) : 0.0;
+  const float hi = to_tf32((float)v);
+  const long long o = (long long)row0 * kpad + x;
+  dig[o] = hi;
+  dig[plane + o] = to_tf32((float)(v - (double)hi));
+}
+
 // plain TF32: the FP32 value rounded to the 10-bit TF32 mantissa (round to nearest, ties away)
 template <class Src>
 __global__ void k_plain_tf32(Src src, int rows, int K, int kpad, int row0, float *dig) {
   const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= (long long)rows * kpad) return;
   const int r = (int)(x / kpad), k = (int)(x % kpad);
-  const float f = (float)(k < K ? src.get(r, k) : 0.0);
-  uint32_t t;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(f));
-  dig[(long long)row0 * kpad + x] = __uint_as_float(t);
+  dig[(long long)row0 * kpad + x] = to_tf32((float)(k < K ? src.get(r, k) : 0.0));
 }
 
 template <class Src>
@@ -182,6 +198,12 @@ void split_any(const Src &src, int rows, int K, int row0, Sliced &o, cudaStream_
   const long long plane = (long long)o.rows * kpad;
   const long long n = (long long)rows * kpad;
   const unsigned g = (unsigned)((n + 255) / 256);
+  if (o.S == S_TF32X3) {
+    k_split_tf32x3<Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, (float *)o.digits);
+    ++launch_counter();
+    LR_CUDA(cudaGetLastError());
+    return;
+  }
   if (o.S == 0 || o.S == S_TF32) {
     if (o.S == 0)
       k_plain<Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, (__nv_bfloat16 *)o.digits);
@@ -314,7 +336,7 @@ constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s
 constexpr int PBK = 32;   // K per stage: one 64-byte swizzle row of BF16 (16 TF32 values)
 constexpr int NST = 3;    // pipeline depth
 // epilogue warps of the S variant
-__host__ __device__ constexpr int epi_warps(int S) { return (S == 0 || S == S_TF32) ? 4 : 8; }
+__host__ __device__ constexpr int epi_warps(int S) { return (S == 0 || S == S_TF32 || S == S_TF32X3) ? 4 : 8; }
 
 // shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart
 __device__ __forceinline__ uint64_t smem_desc64(uint32_t saddr) {
@@ -336,9 +358,9 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
     k_ozgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const Entry *__restrict__ entries, const Tile *__restrict__ tiles, const int *__restrict__ expoA,
              const int *__restrict__ expoB, int *err) {
-  constexpr bool TF = S == S_TF32;                     // plain TF32 (kind::tf32)
-  constexpr bool PLAIN = S == 0 || TF;                 // one plane, FP32 accumulation over all K
-  constexpr int NP = PLAIN ? 1 : S;                    // digit planes
+  constexpr bool TF = S == S_TF32 || S == S_TF32X3;   // kind::tf32
+  constexpr bool PLAIN = S == 0 || TF;                 // one FP32 accumulator over all K
+  constexpr int NP = S == S_TF32X3 ? 2 : PLAIN ? 1 : S;   // planes per operand
   constexpr int KS = TF ? PBK / 2 : PBK;               // K elements per stage (64 bytes per row)
   constexpr uint32_t A_BYTES = BM * 64, B_BYTES = BN * 64;
   constexpr uint32_t STAGE = NP * (A_BYTES + B_BYTES);
@@ -346,7 +368,7 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
   // BF16 accumulates over the whole K in FP32
   constexpr int G = PLAIN ? (1 << 30) : 32 / NP;
   constexpr int EPI_WARPS = epi_warps(S), HALF = BN * 4 / EPI_WARPS;   // HALF: columns per epilogue warp
-  constexpr uint32_t TMEM_COLS = tmem_cols<NP>();
+  constexpr uint32_t TMEM_COLS = tmem_cols<PLAIN ? 1 : NP>();
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[NST], empty[NST], tfull, tempty;
   __shared__ uint32_t tmem_slot;
@@ -421,11 +443,13 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
             for (int j = 0; j < 2; ++j) {   // two MMAs of 32 bytes of K per 64-byte row
               const uint64_t da = smem_desc64(sa + (s - 1) * A_BYTES + 32 * j);
               const uint64_t db = smem_desc64(sb + (t - 1) * B_BYTES + 32 * j);
-              const uint32_t accum = (c == 0 && j == 0 && s == 1) ? 0u : 1u;
+              // digit planes: one accumulator per diagonal s + t; plain forms: one for all
+              const uint32_t col = PLAIN ? 0u : (uint32_t)(s + t - 2) * BN;
+              const uint32_t accum = (c == 0 && j == 0 && s == 1 && (!PLAIN || t == 1)) ? 0u : 1u;
               if constexpr (TF)
-                umma_tf32(tmem + (uint32_t)(s + t - 2) * BN, da, db, accum);
+                umma_tf32(tmem + col, da, db, accum);
               else
-                umma(tmem + (uint32_t)(s + t - 2) * BN, da, db, accum);
+                umma(tmem + col, da, db, accum);
             }
         umma_commit(&empty[st]);
         if (c == G - 1 || i == nsteps - 1) umma_commit(&tfull);
@@ -516,7 +540,7 @@ CUtensorMap make_map(const Sliced &o, int box_rows) {
   const cuuint64_t strides[2] = {(cuuint64_t)o.kpad * eb, (cuuint64_t)o.kpad * eb * (cuuint64_t)o.rows};
   const cuuint32_t box[3] = {(cuuint32_t)(64 / eb), (cuuint32_t)box_rows, 1};   // 64-byte rows
   const cuuint32_t estr[3] = {1, 1, 1};
-  const CUtensorMapDataType dt = o.S == S_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const CUresult r = g_encode(&m, dt, 3, o.digits, dims, strides, box, estr,
                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -587,12 +611,13 @@ void split_ragged(const double *base, const long long *off, const int *Ke, int r
 
 long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry> &entries, int *err,
                        cudaStream_t s, Handle &h, DevBuf &args) {
-  if (a.S != b.S || a.S < 0 || (a.S > SMAX && a.S != S_TF32)) throw Error{LIBRPA_E_ARG, "oz::gemm: operand mismatch"};
+  if (a.S != b.S || a.S < 0 || (a.S > SMAX && a.S != S_TF32 && a.S != S_TF32X3))
+    throw Error{LIBRPA_E_ARG, "oz::gemm: operand mismatch"};
   init();
   std::vector<Tile> tiles;
   // MMA flops issued: per tile BM x BN x (K rounded up to the K step) per digit-plane product
-  const double prods = (a.S == 0 || a.S == S_TF32) ? 1.0 : a.S * (a.S + 1) / 2.0;
-  const int ks = a.S == S_TF32 ? PBK / 2 : PBK;   // K elements per pipeline stage
+  const double prods = (a.S == 0 || a.S == S_TF32) ? 1.0 : a.S == S_TF32X3 ? 3.0 : a.S * (a.S + 1) / 2.0;
+  const int ks = elem_bytes(a.S) == 4 ? PBK / 2 : PBK;   // K elements per pipeline stage
   double exec = 0;
   h.oz_exec_flops = 0;
   for (int e = 0; e < (int)entries.size(); ++e) {
@@ -627,6 +652,7 @@ long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry
     case 3: launch<3>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
     case 4: launch<4>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
     case S_TF32: launch<S_TF32>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
+    case S_TF32X3: launch<S_TF32X3>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
     default: launch<5>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
   }
   ++launch_counter();

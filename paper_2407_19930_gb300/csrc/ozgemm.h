@@ -22,9 +22,11 @@ struct Handle;
 struct DevBuf;
 namespace oz {
 
-constexpr int BM = 128, BN = 64, BK = 64, SMAX = 5, S_TF32 = 6;
-inline int planes(int S) { return S >= 1 && S <= SMAX ? S : 1; }
-inline int elem_bytes(int S) { return S == S_TF32 ? 4 : 2; }
+// S_TF32: one plane of TF32 values; S_TF32X3: two planes hi = tf32(x), lo = tf32(x - hi) and the
+// three products hi hi + hi lo + lo hi summed in one FP32 accumulator (the "3xTF32" split)
+constexpr int BM = 128, BN = 64, BK = 64, SMAX = 5, S_TF32 = 6, S_TF32X3 = 7;
+inline int planes(int S) { return S >= 1 && S <= SMAX ? S : S == S_TF32X3 ? 2 : 1; }
+inline int elem_bytes(int S) { return S == S_TF32 || S == S_TF32X3 ? 4 : 2; }
 
 // K-major sliced operand: digit planes [S][rows][kpad] (BF16; FP32 for S_TF32) and row exponents
 // [rows].

@@ -31,6 +31,7 @@ LIBRPA_FP64_TC = 1
 LIBRPA_SPLIT = 2
 LIBRPA_BF16 = 3
 LIBRPA_TF32 = 4
+LIBRPA_TF32X3 = 5
 LIBRPA_NOALLOC_SCRATCH_BYTES = 16 << 20
 LIBRPA_NOALLOC_MAX_NAUX = 591
 
