@@ -51,7 +51,11 @@ MEV_PER_HA = 27211.386245988
 
 # DRAM traffic per launch of the dominant kernels from one ncu capture (see profiles/),
 # valid only while the kernel source is unchanged (sha256 of the file at capture time).
-TRAFFIC = {}
+TRAFFIC = {
+    # 98 launches of one FP64 step of the graphene workload (16 G-build GEMMs, the ln det GEMMs and
+    # Cholesky trailing updates): 92.5 GB read + 65.0 GB written (profiles/k_zgemm_dram_graphene_fp64.md)
+    "k_zgemm": {"bytes_per_launch": 1.6075e9, "src_sha": "02ef5086221f2c12"},
+}
 
 
 def _peaks():

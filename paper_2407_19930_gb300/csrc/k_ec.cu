@@ -413,6 +413,8 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   // sum_{i >= j} (n - i) MACs per matrix
   const double dn = n;
   const double fl_w = 8.0 * nw * dn * (dn * (dn + 1) / 2), fl_a = 8.0 * nw * (dn * (dn + 1) * (dn + 2) / 6);
+  // FP64 route: A needs W only on and below its diagonal tiles (j >= k), sum_k (n - k)^2 MACs
+  const double fl_w_lower = 8.0 * nw * (dn * (dn + 1) * (2 * dn + 1) / 6);
   for (int c0 = 0; c0 < nql; c0 += nc) {
     const int c1 = std::min(nql, c0 + nc);
     std::vector<double2 *> ap((size_t)(c1 - c0) * nw);
@@ -479,7 +481,8 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
         }
         ZGemmFlags f1;
         f1.kfrom = 2;
-        zgemm_batched(b1, f1, s, h, 1, fl_w);
+        f1.lower_only = true;   // the second GEMM reads W only on and below the diagonal tiles
+        zgemm_batched(b1, f1, s, h, 1, fl_w_lower);
         ZGemmFlags f2;
         f2.transA = true;
         f2.conjA = true;
@@ -525,7 +528,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   // flop count of this stage (complex MAC = 8 real flops): per q (4/3 n^3 real for the Cholesky of
   // V), per (q, omega): W = chi0 L (n^3/2 MAC), L^H W lower (n^3/6 MAC), Cholesky (n^3/6 MAC)
   const double n3 = (double)n * n * n;
-  h.stats.flop_ec = nql * (8.0 * n3 / 6.0) + (double)nql * nw * 8.0 * (n3 / 2 + n3 / 6 + n3 / 6);
+  h.stats.flop_ec = nql * (8.0 * n3 / 6.0) + (double)nql * nw * 8.0 * ((S >= 0 ? n3 / 2 : n3 / 3) + n3 / 6 + n3 / 6);
   return LIBRPA_OK;
 }
 
