@@ -30,7 +30,10 @@ def _alone(inp, grid, precision):
 
 
 def test_batch_equals_alone_and_oracle():
-    cases = [(n, L.LIBRPA_FP64) for n in NAMES] + [("cubic", L.LIBRPA_FP64_TC), ("mixed", L.LIBRPA_SPLIT)]
+    # plus handles that take their own path in the same pass: tensor-core modes and a
+    # spin-polarised cell
+    cases = [(n, L.LIBRPA_FP64) for n in NAMES] + [("cubic", L.LIBRPA_FP64_TC), ("mixed", L.LIBRPA_SPLIT),
+                                                    ("cubic_spin", L.LIBRPA_FP64)]
     inps = [(n, p, CONFIGS[n]()) for n, p in cases]
     hs = []
     b = None

@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 # (config, precision): FP64, the FP64-accurate tensor-core mode and the mixed mode side by side
 MIX = [("tiny", L.LIBRPA_FP64), ("cubic", L.LIBRPA_FP64), ("mixed", L.LIBRPA_SPLIT),
        ("cubic_3x1x2", L.LIBRPA_FP64_TC), ("one_atom_gamma", L.LIBRPA_FP64), ("cubic_3x3x1", L.LIBRPA_SPLIT),
-       ("cubic", L.LIBRPA_FP64_TC), ("mixed", L.LIBRPA_FP64)]
+       ("cubic", L.LIBRPA_FP64_TC), ("mixed", L.LIBRPA_FP64), ("cubic_spin", L.LIBRPA_FP64),
+       ("cubic_spin", L.LIBRPA_SPLIT)]
 
 
 def _grid(name, inp):
