@@ -282,16 +282,15 @@ int librpa_gpu_get_stats(librpa_gpu_t h, librpa_gpu_stats *s);
 /* ---------------------------------------------------------------- batched energies
  * Many independent structures in one pass (not in the paper, which computes one system
  * per call).  Every handle must be filled (set_* calls) before librpa_gpu_batch_run.
- * All handles run on the first handle's stream.  In the FP64 mode, the chi0 contraction
- * of all handles runs in rounds: round r takes the r-th batch of (R, tau) points of every
- * handle, and runs its GEMMs as single grouped launches over all those tiles, which have
- * uneven shapes.  The GEMM tile shape is picked by
- * timing the variants on the first run; from the second run on, that launch sequence is
- * replayed from a CUDA graph.  Handles in the tensor-core modes run their own chi0 path
- * in the same pass.  G, the transforms and
- * the ln det stage run per handle.  While a batch exists, run its handles only through
- * the batch.  After changing a handle's LRI blocks or structure, the next run re-plans
- * and captures again.  Destroy the batch before its handles. */
+ * The FP64-mode, single-channel handles run on the first such handle's stream, and their
+ * chi0 contraction runs in rounds: round r takes the r-th batch of (R, tau) points of every
+ * one of them, and runs its GEMMs as single grouped launches over all those tiles, which
+ * have uneven shapes.  The GEMM tile shape is picked by timing the variants on the first
+ * run; from the second run on, that launch sequence is replayed from a CUDA graph.  The
+ * other handles (tensor-core modes, nspins = 2) run their whole path at the same time on
+ * up to four library-owned streams (one host thread each).  While a batch exists, run its
+ * handles only through the batch.  After changing a handle's LRI blocks or structure, the
+ * next run re-plans and captures again.  Destroy the batch before its handles. */
 typedef struct librpa_gpu_batch *librpa_gpu_batch_t;
 
 typedef struct {
@@ -300,7 +299,8 @@ typedef struct {
   int var_nx, var_fin;     /* FP64 GEMM tile variants chosen: 0 = 64x64, 1 = 32x64, 2 = 64x32,
                               3 = 32x32, 4 = 128x64 (M x N); -1 = none */
   int failed_index;        /* handle of the last error (its last_error has the message), or -1 */
-  double ms_green, ms_chi0, ms_freq, ms_ec, ms_total;   /* device time of the last run */
+  double ms_green, ms_chi0, ms_freq, ms_ec;   /* device time of the merged handles' stages */
+  double ms_total;         /* wall time of the whole last run */
   long long launches;      /* kernel launches of the last run (graph nodes included) */
 } librpa_gpu_batch_stats;
 

@@ -1016,6 +1016,12 @@ bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
   for (size_t i = 0; i < nh && !fresh; ++i) fresh = m.gens[i] != hs[i]->plan.gen || m.hs[i] != hs[i];
   for (Handle *h : hs) h->cur_spin = 0;   // one channel (nspins = 1 handles only)
   if (fresh) {
+    if (!m.hs.empty() && m.hs[0] != hs[0]) {   // descriptor buffers belong to the old first handle
+      for (DevBuf &d : m.nx_args) m.hs[0]->release(d);
+      for (DevBuf &d : m.fin_args) m.hs[0]->release(d);
+      m.nx_args.clear();
+      m.fin_args.clear();
+    }
     m.reset();
     m.hs = hs;
     m.gens.clear();
