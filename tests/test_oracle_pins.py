@@ -376,3 +376,48 @@ def test_spin_two_level_closed_form(delta, c01, v):
     a = 1.0 * (2 * c01) ** 2 * v
     exact = 0.5 * (math.sqrt(delta ** 2 + 2 * a * delta) - delta - a)
     assert abs(out["ec"] - exact) < 1e-6 * abs(exact)
+
+
+# ---------------------------------------------------------------- P11: molecular limit
+
+
+def test_molecule_in_a_box_is_molecular_ri_rpa():
+    """P11: one k point and a molecule in a box large enough that no LRI block reaches a
+    periodic image is molecular RI-RPA.  Computed here in the MO basis with the exact frequency
+    kernel: rho^mu_ia = sum_jk Chat^mu_jk conj(c_ji) c_ka (Chat from Eq. LRI, both terms),
+    Pi(i w) = -2 sum_{i occ, a virt} rho_ia rho_ia^H 2D/(D^2 + w^2) V, and
+    E_c = (1/2 pi) sum_k W_k [ln det(1 - Pi) + Tr Pi]; the oracle's space-time E_c (G, Algorithm
+    1, cosine and Fourier transforms, LU) must agree within the grid's transform error."""
+    roh, ang = 1.81, math.radians(104.5)
+    o = np.array([20.0, 20.0, 20.0])
+    h1 = o + roh * np.array([math.sin(ang / 2), 0.0, -math.cos(ang / 2)])
+    h2 = o + roh * np.array([-math.sin(ang / 2), 0.0, -math.cos(ang / 2)])
+    st = syn.Structure(lat=np.eye(3) * 40.0, pos=np.array([o, h1, h2]), n_ao=np.array([5, 5, 5]),
+                       n_aux=np.array([30, 30, 30]), n_low=np.array([2, 1, 1]), kmesh=(1, 1, 1))
+    inp = syn.make_inputs(st, 17, vscale=2e-3)
+    g = ogrid.make_grid(16, *inp.delta_range)
+    ref = pipeline.rpa_energy(inp, g)["ec"]
+    # Eq. LRI pair coefficients of the molecule
+    ao = np.concatenate([[0], np.cumsum(st.n_ao)])
+    ax = np.concatenate([[0], np.cumsum(st.n_aux)])
+    chat = np.zeros((st.naux, st.nao, st.nao))
+    for I, K, R, C in inp.lri:
+        assert tuple(R) == (0, 0, 0)          # no periodic image within r_cut
+        mu, a, b = slice(ax[I], ax[I + 1]), slice(ao[I], ao[I + 1]), slice(ao[K], ao[K + 1])
+        chat[mu, a, b] += C                   # [mu in atom(i)] C[I,K]_{mu i k}
+        chat[mu, b, a] += C.transpose(0, 2, 1)  # [mu in atom(k)] C[K,I]_{mu k i}
+    eps, c, f = inp.eig[0], inp.wfc[0].T, inp.occ[0]   # c[:, n] = MO n in the NAO basis
+    occ, vir = np.where(f > 0.5)[0], np.where(f < 0.5)[0]
+    rho = np.einsum("mjk,ji,ka->mia", chat, c[:, occ].conj(), c[:, vir])
+    delta = eps[vir][None, :] - eps[occ][:, None]
+    v = inp.vq[0]
+    ec = 0.0
+    for w, wk in zip(g["omega"], g["w_omega"]):
+        ker = 2.0 * delta / (delta ** 2 + w ** 2)
+        chi = -2.0 * np.einsum("mia,ia,nia->mn", rho, ker, rho.conj())
+        pi = chi @ v
+        sign, logdet = np.linalg.slogdet(np.eye(st.naux) - pi)
+        assert sign.real > 0
+        ec += wk * (logdet + np.trace(pi).real) / (2.0 * math.pi)
+    assert ec < 0
+    assert abs(ec - ref) < 1e-6 * abs(ref), (ec, ref)
