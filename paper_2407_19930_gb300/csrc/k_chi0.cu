@@ -613,9 +613,14 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
   auto smem_for = [&](int nl) { return (size_t)(maxn * 2 * maxn + 2 * maxn * 64 + nl * maxn * 2 * maxn) * esz; };
   while (NL > 1 && smem_for(NL) > 200 * 1024) NL /= 2;
   const size_t osmem = smem_for(NL);
-  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
-  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
-  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem));
+  // the limit is the same fixed bound for every handle: handles on other host threads (batched
+  // and serving workers) set it concurrently, and a per-handle value could undercut a launch
+  // in flight on another thread
+  constexpr int kOasmSmemLimit = 200 * 1024;
+  if (osmem > (size_t)kOasmSmemLimit) throw Error{LIBRPA_E_ARG, "O assembly: atoms with too many NAOs"};
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOasmSmemLimit));
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOasmSmemLimit));
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOasmSmemLimit));
   OArgs oa;
   oa.G = g_spin(h);
   oa.g_gstride = (size_t)h.ntau * h.mesh.size() * h.nao * h.nao;

@@ -59,6 +59,16 @@ CONFIGS = {
         syn.cubic_two_atom(nao=5, naux=33, nlow=2, kmesh=(3, 1, 2)), 31, vscale=2e-3),
     # spin-polarised (nspins = 2): one more occupied band in the up channel
     "cubic_spin": lambda: syn.config_spin(),
+    # a water-shaped molecule in a 40 bohr box at one k point (no LRI block reaches an image)
+    "molecule": lambda: syn.make_inputs(
+        syn.Structure(lat=np.eye(3) * 40.0,
+                      pos=np.array([[20.0, 20.0, 20.0],
+                                    [20.0 + 1.81 * math.sin(math.radians(52.25)), 20.0,
+                                     20.0 - 1.81 * math.cos(math.radians(52.25))],
+                                    [20.0 - 1.81 * math.sin(math.radians(52.25)), 20.0,
+                                     20.0 - 1.81 * math.cos(math.radians(52.25))]]),
+                      n_ao=np.array([5, 5, 5]), n_aux=np.array([30, 30, 30]), n_low=np.array([2, 1, 1]),
+                      kmesh=(1, 1, 1)), 17, vscale=2e-3),
     # 9 cells of which 8 pair up as (R, -R): most chi0(R, tau) come from the pair symmetry
     "cubic_3x3x1": lambda: syn.make_inputs(
         syn.cubic_two_atom(nao=4, naux=16, nlow=2, kmesh=(3, 3, 1)), 41, vscale=2e-3),
