@@ -14,7 +14,9 @@ the paper's equations (arXiv:2407.19930, Sec. 2):
   transform (Sec. 2, "RPA correlation energy");
 * ``energy``     -- Tr[ln(1 - Pi) + Pi] through an LU factorisation of
   1 - chi0 V (the paper's route) and the E_c quadrature;
-* ``grid``       -- minimax tau / omega grids and the cosine-transform weights.
+* ``grid``       -- minimax tau / omega grids and the cosine-transform weights;
+* ``screen``     -- Green's-function block screening (Sec. 5's threshold; the
+  block rule is a reading, stated in the module).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import or run anything in this package.  The GPU library

@@ -4,13 +4,15 @@ Test infrastructure only (see the package docstring).
 
 G (Eq. green_mat) -> chi0(R, tau) (Algorithm 1, or the plain definition)
 -> chi0(R, i omega) (cosine transform) -> chi0(q, i omega) (Fourier
-transform) -> E_c (ln det by LU, quadrature over omega, mean over q).
+transform) -> E_c (ln det by LU, quadrature over omega, mean over q).  With a screening
+threshold the Green's functions pass through ``screen.screen_blocks`` first
+(Sec. 5, Green's-function screening).
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import energy, freq, green
+from . import energy, freq, green, screen as _screen
 from .chi0_alg1 import chi0_alg1
 from .chi0_definition import chi0_definition
 
@@ -25,10 +27,15 @@ def spin_factor(nspins: int) -> float:
     raise ValueError("nspins must be 1 or 2")
 
 
-def greens(inp, grid):
-    """[(G^occ, G^vir)] per spin channel."""
+def greens(inp, grid, screen=0.0):
+    """[(G^occ, G^vir)] per spin channel; blocks below the threshold ``screen`` dropped
+    when it is > 0."""
     st = inp.st
-    return [green.green(st.kmesh, inp.kfrac, e, o, w, inp.efermi, grid["tau"]) for e, o, w in inp.channels()]
+    gs = [green.green(st.kmesh, inp.kfrac, e, o, w, inp.efermi, grid["tau"]) for e, o, w in inp.channels()]
+    if screen > 0:
+        gs = [(_screen.screen_blocks(go, st.n_ao, screen)[0], _screen.screen_blocks(gv, st.n_ao, screen)[0])
+              for go, gv in gs]
+    return gs
 
 
 def chi0_tau(inp, grid, route="alg1", go=None, gv=None):
@@ -63,11 +70,11 @@ def chi0_q_omega(inp, grid, chi_tau):
     return out
 
 
-def rpa_energy(inp, grid, route="alg1", vq=None):
-    """Dict with G ([nspins] leading axis when nspins = 2), chi0 in every representation and
-    E_c (Ha per cell)."""
+def rpa_energy(inp, grid, route="alg1", vq=None, screen=0.0):
+    """Dict with G ([nspins] leading axis when nspins = 2; screened when ``screen`` > 0),
+    chi0 in every representation and E_c (Ha per cell)."""
     st = inp.st
-    gs = greens(inp, grid)
+    gs = greens(inp, grid, screen)
     if st.nspins == 1:
         go, gv = gs[0]
     else:

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from paper_2407_19930_gb300 import synthetic as syn
-from oracle import energy, freq, green, grid as ogrid, pipeline
+from oracle import energy, freq, green, grid as ogrid, pipeline, screen
 from oracle.chi0_alg1 import chi0_alg1
 from oracle.chi0_definition import chi0_definition
 from oracle.chi0_sos import chi0_sos
@@ -421,3 +421,53 @@ def test_molecule_in_a_box_is_molecular_ri_rpa():
         ec += wk * (logdet + np.trace(pi).real) / (2.0 * math.pi)
     assert ec < 0
     assert abs(ec - ref) < 1e-6 * abs(ref), (ec, ref)
+
+
+# ---------------------------------------------------------------- P12: Green's-function screening
+
+
+def test_screen_hand_fixture():
+    """The block rule on a hand-made G (atoms of 1 and 2 NAOs, 2 tau, 2 R): a block whose
+    largest |element| equals theta is kept, one just below is dropped, an all-zero block stays
+    zero, small elements of a kept block are untouched, and the rule acts per (tau, R, I, J)."""
+    th = 1e-3
+    G = np.zeros((2, 2, 3, 3))
+    G[0, 0, 0, 0] = -0.5                              # (0,0) kept
+    G[0, 0, 0, 1:3] = [th, -0.25 * th]                # (0,1) max == theta: kept
+    G[0, 0, 1:3, 0] = [0.999 * th, -0.5 * th]         # (1,0) below: dropped
+    G[0, 1, 1:3, 1:3] = [[2e-7, -3.0], [1e-9, 0.0]]   # (1,1) kept, tiny entries included
+    G[0, 1, 0, 0] = 1e-4                              # (0,0) at R 1: dropped
+    G[1, 0, 0, 1:3] = [-2e-3, 5e-4]                   # (0,1) at tau 1: kept
+    G[1, 1, 1:3, 0] = [1e-3, 0.0]                     # (1,0) at tau 1, R 1: kept (== theta)
+    G[1, 1, 1:3, 1:3] = 9e-4                          # (1,1) at tau 1, R 1: dropped
+    want = G.copy()
+    want[0, 0, 1:3, 0] = 0.0
+    want[0, 1, 0, 0] = 0.0
+    want[1, 1, 1:3, 1:3] = 0.0
+    keep_want = np.zeros((2, 2, 2, 2), dtype=bool)
+    keep_want[0, 0, 0, 0] = keep_want[0, 0, 0, 1] = True
+    keep_want[0, 1, 1, 1] = True
+    keep_want[1, 0, 0, 1] = True
+    keep_want[1, 1, 1, 0] = True
+    out, keep = screen.screen_blocks(G, [1, 2], th)
+    assert np.array_equal(out, want)
+    assert np.array_equal(keep, keep_want)
+    out0, keep0 = screen.screen_blocks(G, [1, 2], 0.0)   # theta = 0 keeps everything
+    assert np.array_equal(out0, G) and keep0.all()
+
+
+def test_screen_limits_of_the_energy(cubic):
+    """theta above every block maximum drops all of G: chi0 = 0 and E_c = 0 exactly
+    (ln det 1 + Tr 0); theta at or below every block maximum keeps all of G and gives the
+    unscreened E_c bit for bit; theta in between keeps nested block sets."""
+    g = ogrid.make_grid(8, *cubic.delta_range)
+    go, gv = pipeline.greens(cubic, g)[0]
+    bm = np.concatenate([screen.block_max(go, cubic.st.n_ao).ravel(), screen.block_max(gv, cubic.st.n_ao).ravel()])
+    full = pipeline.rpa_energy(cubic, g)
+    none = pipeline.rpa_energy(cubic, g, screen=2.0 * bm.max())
+    assert np.all(none["chi_tau"] == 0.0) and none["ec"] == 0.0
+    same = pipeline.rpa_energy(cubic, g, screen=bm.min())
+    assert same["ec"] == full["ec"]
+    k1 = screen.screen_blocks(go, cubic.st.n_ao, 1e-3)[1]
+    k2 = screen.screen_blocks(go, cubic.st.n_ao, 1e-2)[1]
+    assert np.all(k1 | ~k2) and k1.sum() > k2.sum()   # kept(1e-2) is a strict subset of kept(1e-3)
