@@ -387,14 +387,20 @@ def tc_roofline(s, peaks, src):
 
 
 def time_mode(L, inp, stream, device, ntau, mode, ec_ref, torch):
-    """One warm-up and one timed step of `mode` on its own handle; E_c against the headline's."""
+    """One warm-up and one timed step of `mode` on its own handle; E_c against the headline's.
+    `mode` is a precision preset, optionally with a Green's-function screening threshold
+    ("fp64@1e-3": the paper's production setting; its E_c difference is then the screening's)."""
+    prec, _, thr = mode.partition("@")
+    theta = float(thr) if thr else 0.0
     o = L.librpa_gpu_default_opts()
     o.device = device
     o.n_tau = ntau
-    o.precision = PRECISIONS[mode][0]
+    o.precision = PRECISIONS[prec][0]
     h = L.librpa_gpu_create(o, torch_stream=stream, torch_alloc=True)
     try:
         L.set_inputs(h, inp)
+        if theta > 0:
+            L.librpa_gpu_set_screening(h, theta)
         L.librpa_gpu_chi0(h)
         L.librpa_gpu_ec(h)
         torch.cuda.synchronize()
@@ -411,11 +417,19 @@ def time_mode(L, inp, stream, device, ntau, mode, ec_ref, torch):
     ms = e0.elapsed_time(e1)
     dmev = abs(ec - ec_ref) * MEV_PER_HA / inp.st.natoms
     peaks, src = _peaks()
-    return {"dtype": PRECISIONS[mode][1], "ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT,
-            "chi0_tflops_fp64_equiv": s["flop_chi0"] / (s["ms_chi0"] * 1e-3) / 1e12,
-            "stage_ms": {"green": s["ms_green"], "chi0": s["ms_chi0"], "freq": s["ms_freq"], "ec": s["ms_ec"]},
-            "ec_ha": ec, "ec_diff_vs_fp64_mev_per_atom": dmev, "within_0.1_mev_per_atom": dmev <= 0.1,
-            "roofline": tc_roofline(s, peaks, src), "steps": 1, "warmup": 1}
+    out = {"dtype": PRECISIONS[prec][1], "ms_per_step": ms, "value": 1e3 / ms, "unit": UNIT,
+           "chi0_tflops_fp64_equiv": s["flop_chi0"] / (s["ms_chi0"] * 1e-3) / 1e12,
+           "stage_ms": {"green": s["ms_green"], "chi0": s["ms_chi0"], "freq": s["ms_freq"], "ec": s["ms_ec"]},
+           "ec_ha": ec, "ec_diff_vs_fp64_mev_per_atom": dmev, "within_0.1_mev_per_atom": dmev <= 0.1,
+           "steps": 1, "warmup": 1}
+    if prec != "fp64":
+        out["roofline"] = tc_roofline(s, peaks, src)
+    if theta > 0:
+        out["screening"] = {"threshold": theta, "points_contracted": s["n_points_chi0"],
+                            "points_skipped": s["n_points_skipped"],
+                            "g_blocks_kept_frac": s["n_blocks_kept"] / max(1, s["n_blocks_total"]),
+                            "chi0_flop_alg": s["flop_chi0"]}
+    return out
 
 
 def _serve_inputs(n):
@@ -629,8 +643,9 @@ def main():
                     help="requests of the serving sample added to the headline line (0: none)")
     ap.add_argument("--rate", type=float, default=20.0, help="request arrival rate (Poisson), per second")
     ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--modes", default="fp64_tc,split,tf32x3,tf32,bf16",
-                    help="other precision modes timed after the headline (1 GPU; '' for none)")
+    ap.add_argument("--modes", default="fp64_tc,split,tf32x3,tf32,bf16,fp64@1e-3,fp64_tc@1e-3",
+                    help="other precision modes timed after the headline, 'mode@theta' with G screening "
+                         "(1 GPU; '' for none)")
     args = ap.parse_args()
     args.kmesh = tuple(int(x) for x in args.kmesh.split(","))
     if args.impl == "reference":

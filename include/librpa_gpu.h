@@ -118,6 +118,10 @@ typedef struct {
                                  products, tile padding and all); 0 in the FP64 mode */
   double flop_exec_gemm_ec;   /* the same for the timed ln det GEMMs */
   size_t bytes_device_peak;   /* largest device footprint of the handle so far */
+  long long n_points_chi0;    /* (R, tau) points contracted, summed over spin channels */
+  long long n_points_skipped; /* points left out because screening made their chi0 exactly zero */
+  long long n_blocks_kept;    /* atom-pair blocks of G kept by screening (all of them when off) */
+  long long n_blocks_total;   /* atom-pair blocks of G: nspins * 2 * ntau * nR * natoms^2 */
 } librpa_gpu_stats;
 
 /* Fill *o with defaults: device 0, own stream, cudaMalloc, n_tau = 16, FP64,
@@ -180,6 +184,21 @@ int librpa_gpu_set_coulomb(librpa_gpu_t h, int iq, const double *V_re, const dou
  * Errors: E_STATE (no structure), E_ARG. */
 int librpa_gpu_set_grid(librpa_gpu_t h, int ntau, const double *tau, int nomega,
                         const double *omega, const double *w_omega, const double *gamma);
+
+/* Green's-function block screening (Sec. 5: production runs screen G with a threshold of
+ * 1e-3; Sec. 2: the decay of G limits the range of R).  The paper gives no formula; the rule
+ * here: each atom-pair NAO block G^occ_{IJ}(R, tau_j) and G^vir_{IJ}(R, tau_j) is set to zero
+ * when its largest |element| is below `threshold` (absolute, FP64 comparison on the device),
+ * and kept unchanged otherwise.  Algorithm 1 then runs on the screened G.  Every term of chi0
+ * is a product of a G^occ and a G^vir factor, so chi0(R, tau) is exactly zero at points where
+ * every block one of the two Green's functions contributes was dropped; those points are not
+ * contracted (stats.n_points_skipped), and N- or X-step operands without a kept block are not
+ * multiplied on the FP64 route.  The result is that of the full contraction on the screened
+ * G.  threshold = 0 (the default) turns screening off.  The setting belongs to the handle
+ * (set_structure keeps it) and takes effect at the next
+ * librpa_gpu_chi0; librpa_gpu_get_green then returns the screened G.
+ * Errors: E_ARG (h NULL, threshold negative or not finite). */
+int librpa_gpu_set_screening(librpa_gpu_t h, double threshold);
 
 /* Stateless grid construction (host; Sec. 2: non-uniform tau/omega grids and gamma
  * from an L2 minimisation).  For n points and transition energies in [dmin, dmax]:

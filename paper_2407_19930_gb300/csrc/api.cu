@@ -126,6 +126,8 @@ void free_device_state(Handle &h) {
   h.release(h.gemm_args);
   h.release(h.oz_args);
   h.release(h.work);
+  h.release(h.d_gmask);
+  h.release(h.d_screen_tab);
   for (DevBuf *b : h.plan.all()) h.release(*b);
   h.lri_dirty = true;
 }
@@ -167,6 +169,8 @@ size_t estimate_device_bytes(Handle &h) {
   b += chi0_device_bytes(h, P);
   b += std::max(green_work_bytes(h), std::max(freq_work_bytes(h), ec_work_bytes(h)));
   b += (size_t)64 << 20;                                          // descriptor and tile uploads
+  if (h.g_screen > 0)                                             // block mask, atom tables
+    b += ns * 2 * (size_t)h.ntau * nk * h.natoms * h.natoms + 8 * (size_t)h.natoms + 512;
   h.ntau = ntau_saved;
   return b;
 }
@@ -441,6 +445,16 @@ int librpa_gpu_set_grid(librpa_gpu_t h, int ntau, const double *tau, int nomega,
   });
 }
 
+int librpa_gpu_set_screening(librpa_gpu_t h, double threshold) {
+  return guarded(h, [&]() -> int {
+    if (!(threshold >= 0.0) || !std::isfinite(threshold))
+      return fail(h, LIBRPA_E_ARG, "set_screening: threshold must be finite and >= 0");
+    h->g_screen = threshold;
+    h->chi0_done = false;
+    return LIBRPA_OK;
+  });
+}
+
 int librpa_gpu_build_grid(int n, double dmin, double dmax, double *tau, double *omega, double *w_omega,
                           double *gamma) {
   try {
@@ -493,7 +507,7 @@ int librpa_gpu_chi0(librpa_gpu_t h, double *out_re, double *out_im) {
     h->stats.ms_freq = t;
     for (auto &e : ev) cudaEventDestroy(e);
     h->resolve_timers();
-    h->stats.flop_chi0 = h->plan.flop_per_point * h->ntau * (double)chi0_r_list(h->mesh).size() * h->nspins;
+    h->stats.flop_chi0 = h->flop_chi0_run;
     h->stats.launches = launch_counter() - l0;
     h->stats.bytes_device = h->bytes_held;
     h->stats.bytes_device_peak = h->bytes_peak;

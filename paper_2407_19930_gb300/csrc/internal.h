@@ -74,6 +74,7 @@ struct Chi0Plan {
   std::vector<long long> bg_off, ag_off, n_off, x_off, o_off;
   long long bg_sz = 0, ag_sz = 0, n_sz = 0, x_sz = 0, o_sz = 0;
   double flop_per_point = 0;  // algorithmic FP64 flops per (R, tau) point
+  double flop_nx_per_point = 0;  // the part of it in the N and X steps
   // device copies of the per-atom tables, point list, workspace and GEMM descriptors
   DevBuf t_n_ao, t_n_aux, t_ao_off, t_aux_off, t_m, t_lam_off, t_kap_off, t_bg_off, t_ag_off, t_n_off, t_x_off,
       t_o_off, t_pts, ws, gargs1, gargs2;
@@ -129,6 +130,12 @@ struct Handle {
   std::vector<char> have_q;
   int vq_sym = -1;   // V(-q) = conj V(q) for every q: -1 not checked yet, 0 no, 1 yes
 
+  // Green's-function block screening: threshold (0 = off), the kept-block mask of the current
+  // G [spin][g][tau][R][I][J] (host copy) and its device buffers
+  double g_screen = 0;
+  std::vector<unsigned char> gmask;
+  DevBuf d_gmask, d_screen_tab;
+
   // grid
   bool have_grid = false, grid_user = false;
   int ntau = 0;
@@ -147,6 +154,7 @@ struct Handle {
   DevBuf oz_args;     // descriptors of the tensor-core GEMM launches
   DevBuf work;        // per-call workspace
   double oz_exec_flops = 0;  // MMA flops issued by the last digit-plane GEMM launch
+  double flop_chi0_run = 0;  // algorithmic flops of the last contraction (screened work left out)
   bool chi0_done = false, lri_dirty = true;
   Chi0Plan plan;
 

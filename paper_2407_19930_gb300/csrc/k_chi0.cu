@@ -492,6 +492,7 @@ void chi0_shape(const Handle &h, Chi0Plan &P) {
     fl += 2.0 * 2.0 * rowsV * P.m[V] * P.m_all;    // N-step, both G
     fl += 2.0 * 2.0 * h.nao * P.m[V] * rowsV;      // X-step, both G
   }
+  P.flop_nx_per_point = fl;
   for (int U = 0; U < nat; ++U) {
     const double cols = (double)h.n_ao[U] * P.m[U];
     for (int V = 0; V < nat; ++V) fl += 2.0 * h.n_aux[V] * cols * 4.0 * h.n_ao[V];   // O assembly
@@ -709,6 +710,107 @@ std::vector<Point> make_points(Handle &h, const std::vector<int> &rl, long long 
   return pts;
 }
 
+// Point selection under Green's-function screening (Sec. 5), from the kept-block mask of the
+// screened G.  For the point (R_p, tau) and one Green's function g, the contraction reads:
+//   N-step of V:  blocks (L, K) at R1 - R_p - R2, for (L, R2) in N[V] and (K, R1) in the union list;
+//   X-step of V:  blocks (I, L) at R_p + R2, every atom I;
+//   O assembly:   blocks (U, V) at R_p, and (V, K) at R1 - R_p for (K, R1) in the union list.
+// Every term of chi0 pairs a G^occ factor with a G^vir factor (M = G^vir N[G^occ] and
+// G^occ N[G^vir], Z = X[G^vir] G^occ and X[G^occ] G^vir), so chi0(R_p, tau) is exactly zero when
+// one Green's function has no kept block among those it contributes there: such points are not
+// contracted.  An N- or X-step operand with no kept block is exactly zero.
+struct ScreenSel {
+  std::vector<Point> pts;                // points to contract, in (tau, R) order
+  std::vector<unsigned char> nzN, nzX;   // [point][g][V]: the operand holds a kept block
+  long long skipped = 0;
+};
+
+ScreenSel screen_select(const Handle &h, const std::vector<int> &rl) {
+  const Chi0Plan &P = h.plan;
+  const int nat = h.natoms, nR = h.mesh.size(), ntau = h.ntau, nr = (int)rl.size();
+  const bool on = h.g_screen > 0 && !h.gmask.empty();
+  ScreenSel sel;
+  auto point = [&](int it, int iR) {
+    Point pt;
+    pt.itau = it;
+    pt.iR = iR;
+    h.mesh.split(iR, pt.R[0], pt.R[1], pt.R[2]);
+    return pt;
+  };
+  if (!on) {
+    for (int it = 0; it < ntau; ++it)
+      for (int r = 0; r < nr; ++r) sel.pts.push_back(point(it, rl[r]));
+    sel.nzN.assign(sel.pts.size() * 2 * nat, 1);
+    sel.nzX.assign(sel.pts.size() * 2 * nat, 1);
+    return sel;
+  }
+  // per V: distinct (L, K, R1 - R2) of the N-step and distinct (L, R2) of the X-step
+  struct Key { int L, K, d[3]; };
+  std::vector<std::vector<Key>> dn(nat), dx(nat);
+  for (int V = 0; V < nat; ++V) {
+    std::set<std::tuple<int, int, int, int, int>> sn, sx;
+    for (const NbEntry &l : P.nb[V]) {
+      sx.insert(std::make_tuple(l.K, 0, l.R[0], l.R[1], l.R[2]));
+      for (const auto &u : P.uni)
+        sn.insert(std::make_tuple(l.K, std::get<0>(u), std::get<1>(u) - l.R[0], std::get<2>(u) - l.R[1],
+                                  std::get<3>(u) - l.R[2]));
+    }
+    for (auto &t : sn) dn[V].push_back(Key{std::get<0>(t), std::get<1>(t), {std::get<2>(t), std::get<3>(t), std::get<4>(t)}});
+    for (auto &t : sx) dx[V].push_back(Key{std::get<0>(t), 0, {std::get<2>(t), std::get<3>(t), std::get<4>(t)}});
+  }
+  const size_t nn = (size_t)nat * nat;
+  std::vector<unsigned char> col(nR * nat), any_r(nR);   // per (R, J): a kept block (*, J); per R: any
+  for (int it = 0; it < ntau; ++it) {
+    std::vector<unsigned char> nz(nr * 4 * nat, 0), anyg(nr * 2, 0);   // [r][N/X][g][V], [r][g]
+    for (int g = 0; g < 2; ++g) {
+      const unsigned char *M = h.gmask.data() + ((size_t)(h.cur_spin * 2 + g) * ntau + it) * nR * nn;
+      std::fill(col.begin(), col.end(), 0);
+      std::fill(any_r.begin(), any_r.end(), 0);
+      for (int iR = 0; iR < nR; ++iR)
+        for (int I = 0; I < nat; ++I)
+          for (int J = 0; J < nat; ++J)
+            if (M[(size_t)iR * nn + (size_t)I * nat + J]) col[iR * nat + J] = any_r[iR] = 1;
+      for (int r = 0; r < nr; ++r) {
+        int R[3];
+        h.mesh.split(rl[r], R[0], R[1], R[2]);
+        bool any = any_r[rl[r]];
+        for (const auto &u : P.uni)
+          if (!any && col[h.mesh.index(std::get<1>(u) - R[0], std::get<2>(u) - R[1], std::get<3>(u) - R[2]) * nat +
+                          std::get<0>(u)])
+            any = true;
+        for (int V = 0; V < nat; ++V) {
+          bool n_any = false, x_any = false;
+          for (const Key &k : dn[V])
+            if (M[(size_t)h.mesh.index(k.d[0] - R[0], k.d[1] - R[1], k.d[2] - R[2]) * nn + (size_t)k.L * nat + k.K]) {
+              n_any = true;
+              break;
+            }
+          for (const Key &k : dx[V])
+            if (col[h.mesh.index(R[0] + k.d[0], R[1] + k.d[1], R[2] + k.d[2]) * nat + k.L]) {
+              x_any = true;
+              break;
+            }
+          nz[((size_t)r * 2 + 0) * 2 * nat + g * nat + V] = n_any;
+          nz[((size_t)r * 2 + 1) * 2 * nat + g * nat + V] = x_any;
+          any = any || n_any || x_any;
+        }
+        anyg[r * 2 + g] = any;
+      }
+    }
+    for (int r = 0; r < nr; ++r) {
+      if (!(anyg[r * 2] && anyg[r * 2 + 1])) {
+        ++sel.skipped;
+        continue;
+      }
+      sel.pts.push_back(point(it, rl[r]));
+      const unsigned char *a = nz.data() + (size_t)r * 4 * nat;
+      sel.nzN.insert(sel.nzN.end(), a, a + 2 * nat);
+      sel.nzX.insert(sel.nzX.end(), a + 2 * nat, a + 4 * nat);
+    }
+  }
+  return sel;
+}
+
 void timed_grouped(Handle &h, const oz::Sliced &a, const oz::Sliced &b, const std::vector<oz::Entry> &es, int *err,
                    DevBuf &args) {
   double fl = 0;
@@ -760,22 +862,31 @@ void fp64_gather(Handle &h, const Point *dpts, int np, const Fp64Ws &w) {
   LR_CUDA(cudaGetLastError());
 }
 
-// N- and X-step descriptors of np points (appended to b)
-void fp64_nx(Handle &h, int np, const Fp64Ws &w, std::vector<DGemm> &b) {
+// N- and X-step descriptors of np points (appended to b).  nzN / nzX ([point][g][V], nullable):
+// an operand without a kept G block under screening is exactly zero, and its GEMM runs with
+// K = 0, which writes zeros.  Returns the algorithmic flops of the descriptors.
+double fp64_nx(Handle &h, int np, const Fp64Ws &w, std::vector<DGemm> &b, const unsigned char *nzN = nullptr,
+               const unsigned char *nzX = nullptr) {
   const Chi0Plan &P = h.plan;
   const double *Cp = (const double *)h.d_cpack.p;
+  const int nat = h.natoms;
+  double fl = 0;
   for (int q = 0; q < np; ++q)
     for (int g = 0; g < 2; ++g)
-      for (int V = 0; V < h.natoms; ++V) {
+      for (int V = 0; V < nat; ++V) {
         const int rowsV = h.n_aux[V] * h.n_ao[V], mV = P.m[V];
+        const size_t e = ((size_t)q * 2 + g) * nat + V;
+        const int kn = !nzN || nzN[e] ? mV : 0, kx = !nzX || nzX[e] ? mV : 0;
         DGemm dn{Cp + P.cp_off[V], w.Bg + (size_t)q * 2 * P.bg_sz + g * P.bg_sz + P.bg_off[V],
-                 w.Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V], rowsV, P.m_all, mV, mV, mV, P.m_all,
+                 w.Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V], rowsV, P.m_all, kn, mV, mV, P.m_all,
                  1.0, 0.0};
         b.push_back(dn);
         DGemm dx{w.Ag + (size_t)q * 2 * P.ag_sz + g * P.ag_sz + P.ag_off[V], Cp + P.cp_off[V],
-                 w.Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V], h.nao, rowsV, mV, mV, mV, rowsV, 1.0, 0.0};
+                 w.Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V], h.nao, rowsV, kx, mV, mV, rowsV, 1.0, 0.0};
         b.push_back(dx);
+        fl += 2.0 * rowsV * P.m_all * kn + 2.0 * h.nao * rowsV * kx;
       }
+  return fl;
 }
 
 // final contraction chi0(R, tau)[U rows] = -s Cpack_U O_U^T of the points (appended to b)
@@ -846,7 +957,6 @@ void chi0_run_tc(Handle &h) {
   h.ensure(h.d_chi_tau, (size_t)ntau * nR * naux * naux * sizeof(double));
   const int rows_bg = 2 * nat * P.m_all, rows_ag = 2 * nat * nao, rows_o = nat * naux;
   const std::vector<int> rl = chi0_r_list(h.mesh);
-  const long long total_pts = (long long)ntau * rl.size();
   const TcWs tw = tc_ws(h, P);
   const long long npb = tw.npb;
   const size_t b_n = tw.b_n, b_x = tw.b_x, b_o = tw.b_o, b_bg = tw.b_bg, b_ag = tw.b_ag, b_od = tw.b_od;
@@ -865,10 +975,18 @@ void chi0_run_tc(Handle &h) {
   oz::sliced_bind(cpf, P.cp_f.p, naux, P.max_nm, S);
   const double spin = spin_factor(h);
   const size_t g_gstride = (size_t)ntau * nR * nao * nao;
-  for (h.cur_spin = 0; h.cur_spin < h.nspins; ++h.cur_spin)
+  // under screening, points left out keep chi0 = 0 (the second spin channel accumulates)
+  if (h.g_screen > 0) LR_CUDA(cudaMemsetAsync(h.d_chi_tau.p, 0, (size_t)ntau * nR * naux * naux * sizeof(double), s));
+  h.flop_chi0_run = 0;
+  for (h.cur_spin = 0; h.cur_spin < h.nspins; ++h.cur_spin) {
+  const ScreenSel sel = screen_select(h, rl);
+  const long long total_pts = (long long)sel.pts.size();
+  h.stats.n_points_chi0 += total_pts;
+  h.stats.n_points_skipped += sel.skipped;
+  h.flop_chi0_run += total_pts * P.flop_per_point;
   for (long long p0 = 0; p0 < total_pts; p0 += npb) {
     const int np = (int)std::min(npb, total_pts - p0);
-    std::vector<Point> pts = make_points(h, rl, p0, np);
+    std::vector<Point> pts(sel.pts.begin() + p0, sel.pts.begin() + p0 + np);
     h.ensure(P.t_pts, np * sizeof(Point));
     LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
     // digit planes of the gathered Green's-function operands, straight from G
@@ -965,6 +1083,7 @@ void chi0_run_tc(Handle &h) {
     }
     timed_grouped(h, cpf, sod, ef, err, P.gargs3);
   }
+  }
   h.cur_spin = 0;
   fill_partners(h);
   int e_host = 0;
@@ -986,25 +1105,35 @@ void chi0_run(Handle &h, double *ms_gemm) {
   cudaStream_t s = h.stream;
   h.ensure(h.d_chi_tau, (size_t)ntau * nR * naux * naux * sizeof(double));
   const std::vector<int> rl = chi0_r_list(h.mesh);
-  const long long total_pts = (long long)ntau * rl.size();
   const DpWs dw = dp_ws(h, P);
   const long long npb = dw.npb;
   h.ensure(P.ws, dw.total);
   const Fp64Ws w = fp64_ws(h, npb);
-  for (h.cur_spin = 0; h.cur_spin < h.nspins; ++h.cur_spin)
-  for (long long p0 = 0; p0 < total_pts; p0 += npb) {
-    const int np = (int)std::min(npb, total_pts - p0);
-    std::vector<Point> pts = make_points(h, rl, p0, np);
-    h.ensure(P.t_pts, np * sizeof(Point));
-    LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
-    const Point *dpts = (const Point *)P.t_pts.p;
-    fp64_gather(h, dpts, np, w);
-    std::vector<DGemm> b1, b2;
-    fp64_nx(h, np, w, b1);
-    dgemm_batched(h, b1, s, P.gargs1, &P.var_nx);
-    run_oassemble(h, dpts, np, w.Nw, w.Xw, w.Ow);
-    fp64_final(h, pts, w, b2);
-    dgemm_batched(h, b2, s, P.gargs2, &P.var_fin);
+  const bool scr = h.g_screen > 0;
+  // under screening, points left out keep chi0 = 0 (the second spin channel accumulates)
+  if (scr) LR_CUDA(cudaMemsetAsync(h.d_chi_tau.p, 0, (size_t)ntau * nR * naux * naux * sizeof(double), s));
+  h.flop_chi0_run = 0;
+  for (h.cur_spin = 0; h.cur_spin < h.nspins; ++h.cur_spin) {
+    const ScreenSel sel = screen_select(h, rl);
+    const long long total_pts = (long long)sel.pts.size();
+    h.stats.n_points_chi0 += total_pts;
+    h.stats.n_points_skipped += sel.skipped;
+    for (long long p0 = 0; p0 < total_pts; p0 += npb) {
+      const int np = (int)std::min(npb, total_pts - p0);
+      std::vector<Point> pts(sel.pts.begin() + p0, sel.pts.begin() + p0 + np);
+      h.ensure(P.t_pts, np * sizeof(Point));
+      LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
+      const Point *dpts = (const Point *)P.t_pts.p;
+      fp64_gather(h, dpts, np, w);
+      std::vector<DGemm> b1, b2;
+      const size_t z = (size_t)p0 * 2 * h.natoms;
+      h.flop_chi0_run += fp64_nx(h, np, w, b1, scr ? sel.nzN.data() + z : nullptr, scr ? sel.nzX.data() + z : nullptr);
+      h.flop_chi0_run += np * (P.flop_per_point - P.flop_nx_per_point);
+      dgemm_batched(h, b1, s, P.gargs1, &P.var_nx);
+      run_oassemble(h, dpts, np, w.Nw, w.Xw, w.Ow);
+      fp64_final(h, pts, w, b2);
+      dgemm_batched(h, b2, s, P.gargs2, &P.var_fin);
+    }
   }
   h.cur_spin = 0;
   fill_partners(h);
@@ -1049,6 +1178,8 @@ bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
     npb[i] = dw.npb;
     const std::vector<int> rl = chi0_r_list(h.mesh);
     pts[i] = make_points(h, rl, 0, (int)(h.ntau * rl.size()));
+    h.stats.n_points_chi0 = (long long)pts[i].size();
+    h.flop_chi0_run = pts[i].size() * P.flop_per_point;
     rounds = std::max(rounds, (int)((pts[i].size() + npb[i] - 1) / npb[i]));
     if (fresh) {
       h.ensure(P.t_pts, pts[i].size() * sizeof(Point));
@@ -1136,7 +1267,7 @@ bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
   return false;
 }
 
-bool chi0_fits_one_batch(const Handle &h) { return h.chi0_S < 0 && h.nspins == 1; }
+bool chi0_fits_one_batch(const Handle &h) { return h.chi0_S < 0 && h.nspins == 1 && !(h.g_screen > 0); }
 
 void MergedChi0::reset() {
   if (exec) cudaGraphExecDestroy(exec);

@@ -62,6 +62,63 @@ __global__ void k_phase_sum(const double2 *P, const double2 *twiddle, int nk, in
   atomicMax(&maxabs[1], __double_as_longlong(mim));
 }
 
+// Green's-function block screening (Sec. 5): the atom-pair block G^g_{IJ}(R, tau) is zeroed when
+// its largest |element| is below theta, and kept[b] = 1 for the blocks that stay.  One warp per
+// block; blocks flat over [spin][g][tau][R][I][J], the order of G's slabs and of the mask.
+__global__ void k_screen(double *G, const int *tab, int natoms, int nao, long long nblocks, double theta,
+                         unsigned char *kept) {
+  const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= nblocks) return;   // the same for every lane of the warp
+  const int J = (int)(b % natoms), I = (int)((b / natoms) % natoms);
+  const long long slab = b / ((long long)natoms * natoms);
+  const int *n_ao = tab, *ao_off = tab + natoms;
+  double *blk = G + (size_t)slab * nao * nao + (size_t)ao_off[I] * nao + ao_off[J];
+  const int nj = n_ao[J], n = n_ao[I] * nj;
+  double mx = 0.0;
+  for (int e = lane; e < n; e += 32) mx = fmax(mx, fabs(blk[(size_t)(e / nj) * nao + e % nj]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const bool keep = mx >= theta;
+  if (lane == 0) kept[b] = keep ? 1 : 0;
+  if (!keep)
+    for (int e = lane; e < n; e += 32) blk[(size_t)(e / nj) * nao + e % nj] = 0.0;
+}
+
+// Screens every spin channel's G in place (h.g_screen > 0) and keeps the block mask on the host
+// for the point selection of the contraction.
+void green_screen(Handle &h) {
+  const int nat = h.natoms, nR = h.mesh.size();
+  const long long nblocks = (long long)h.nspins * 2 * h.ntau * nR * nat * nat;
+  h.stats.n_blocks_total = nblocks;
+  if (!(h.g_screen > 0)) {
+    h.gmask.clear();
+    h.stats.n_blocks_kept = nblocks;
+    return;
+  }
+  cudaStream_t s = h.stream;
+  std::vector<int> tab(2 * nat);
+  for (int a = 0; a < nat; ++a) {
+    tab[a] = h.n_ao[a];
+    tab[nat + a] = h.ao_off[a];
+  }
+  h.ensure(h.d_screen_tab, tab.size() * sizeof(int));
+  h.ensure(h.d_gmask, (size_t)nblocks);
+  LR_CUDA(cudaMemcpyAsync(h.d_screen_tab.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  const long long threads = nblocks * 32;
+  k_screen<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>((double *)h.d_g.p, (const int *)h.d_screen_tab.p, nat,
+                                                             h.nao, nblocks, h.g_screen,
+                                                             (unsigned char *)h.d_gmask.p);
+  ++launch_counter();
+  LR_CUDA(cudaGetLastError());
+  h.gmask.resize((size_t)nblocks);
+  LR_CUDA(cudaMemcpyAsync(h.gmask.data(), h.d_gmask.p, (size_t)nblocks, cudaMemcpyDeviceToHost, s));
+  LR_CUDA(cudaStreamSynchronize(s));   // tab is a host temporary; the mask is read on the host next
+  long long kept = 0;
+  for (unsigned char c : h.gmask) kept += c;
+  h.stats.n_blocks_kept = kept;
+}
+
 }  // namespace
 
 size_t green_work_bytes(const Handle &h) {
@@ -160,6 +217,7 @@ double green_build(Handle &h) {
   unsigned long long mx[2];
   LR_CUDA(cudaMemcpyAsync(mx, d_max, 16, cudaMemcpyDeviceToHost, s));
   LR_CUDA(cudaStreamSynchronize(s));
+  green_screen(h);   // after the imaginary-part check's maxima: they describe the unscreened G
   double mre, mim;
   std::memcpy(&mre, &mx[0], 8);
   std::memcpy(&mim, &mx[1], 8);

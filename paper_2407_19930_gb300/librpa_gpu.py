@@ -56,7 +56,9 @@ class librpa_gpu_stats(ctypes.Structure):
                 ("flop_gemm_ec", ctypes.c_double), ("n_gemm_ec", ctypes.c_longlong),
                 ("launches", ctypes.c_longlong),
                 ("bytes_device", ctypes.c_size_t), ("flop_exec_gemm_chi0", ctypes.c_double),
-                ("flop_exec_gemm_ec", ctypes.c_double), ("bytes_device_peak", ctypes.c_size_t)]
+                ("flop_exec_gemm_ec", ctypes.c_double), ("bytes_device_peak", ctypes.c_size_t),
+                ("n_points_chi0", ctypes.c_longlong), ("n_points_skipped", ctypes.c_longlong),
+                ("n_blocks_kept", ctypes.c_longlong), ("n_blocks_total", ctypes.c_longlong)]
 
 
 class librpa_gpu_server_opts(ctypes.Structure):
@@ -104,6 +106,7 @@ _SIGS = {
                                             ctypes.c_double]),
     "librpa_gpu_set_coulomb": (ctypes.c_int, [_H, ctypes.c_int, _D, _D]),
     "librpa_gpu_set_grid": (ctypes.c_int, [_H, ctypes.c_int, _D, ctypes.c_int, _D, _D, _D]),
+    "librpa_gpu_set_screening": (ctypes.c_int, [_H, ctypes.c_double]),
     "librpa_gpu_build_grid": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D]),
     "librpa_gpu_get_grid": (ctypes.c_int, [_H, _I, _D, _D, _D, _D]),
     "librpa_gpu_chi0": (ctypes.c_int, [_H, _D, _D]),
@@ -263,6 +266,10 @@ def librpa_gpu_set_grid(h, tau, omega, w_omega, gamma):
     tau, omega, w_omega, gamma = _f64(tau), _f64(omega), _f64(w_omega), _f64(gamma)
     _check(h, load().librpa_gpu_set_grid(h, len(tau), _dp(tau), len(omega), _dp(omega), _dp(w_omega),
                                          _dp(gamma)))
+
+
+def librpa_gpu_set_screening(h, threshold):
+    _check(h, load().librpa_gpu_set_screening(h, float(threshold)))
 
 
 def librpa_gpu_build_grid(n, dmin, dmax):

@@ -23,10 +23,12 @@ TOL_CHI = 1e-10
 TOL_EC = 1e-8
 
 
-def _run(inp, grid, opts=None, **kw):
+def _run(inp, grid, opts=None, screening=0.0, **kw):
     h = L.librpa_gpu_create(opts, **kw)
     try:
         L.set_inputs(h, inp, grid)
+        if screening > 0:
+            L.librpa_gpu_set_screening(h, screening)
         st = inp.st
         chi = L.librpa_gpu_chi0(h, out=(st.nk, len(grid["omega"]), st.naux))
         ec, ecq, ecw = L.librpa_gpu_ec(h, st.nk, len(grid["omega"]))
