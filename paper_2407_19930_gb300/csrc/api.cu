@@ -123,6 +123,7 @@ void free_device_state(Handle &h) {
   h.release(h.d_eig);
   h.release(h.d_occ);
   h.release(h.zgemm_args);
+  h.release(h.rgemm_args);
   h.release(h.gemm_args);
   h.release(h.oz_args);
   h.release(h.work);
@@ -409,7 +410,7 @@ int librpa_gpu_set_coulomb(librpa_gpu_t h, int iq, const double *V_re, const dou
         v[2 * x + 1] = V_im[x];
       }
       h->have_q[iq] = 1;
-      h->vq_sym = -1;
+      h->vq_sym = h->vq_real = -1;
       return LIBRPA_OK;
     }
     cudaSetDevice(h->opts.device);
@@ -423,7 +424,7 @@ int librpa_gpu_set_coulomb(librpa_gpu_t h, int iq, const double *V_re, const dou
                             h->stream));
     LR_CUDA(cudaStreamSynchronize(h->stream));
     h->have_q[iq] = 1;
-    h->vq_sym = -1;
+    h->vq_sym = h->vq_real = -1;
     return LIBRPA_OK;
   });
 }
@@ -649,7 +650,7 @@ int librpa_gpu_set_coulomb_dev(librpa_gpu_t h, int iq, const double *V) {
     h->ensure(h->d_vq, n2 * 16 * h->mesh.size());
     LR_CUDA(cudaMemcpyAsync((char *)h->d_vq.p + n2 * 16 * iq, V, n2 * 16, cudaMemcpyDeviceToDevice, h->stream));
     h->have_q[iq] = 1;
-    h->vq_sym = -1;
+    h->vq_sym = h->vq_real = -1;
     return LIBRPA_OK;
   });
 }

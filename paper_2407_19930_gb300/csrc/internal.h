@@ -129,6 +129,7 @@ struct Handle {
   std::vector<double> efermi_k;
   std::vector<char> have_q;
   int vq_sym = -1;   // V(-q) = conj V(q) for every q: -1 not checked yet, 0 no, 1 yes
+  int vq_real = -1;  // V(q) real at every q = -q (same check): -1 not checked yet, 0 no, 1 yes
 
   // Green's-function block screening: threshold (0 = off), the kept-block mask of the current
   // G [spin][g][tau][R][I][J] (host copy) and its device buffers
@@ -150,6 +151,7 @@ struct Handle {
   DevBuf d_chi_qw;    // [nq][nomega][naux][naux] complex interleaved
   DevBuf d_cpack;     // packed LRI coefficients
   DevBuf zgemm_args;  // descriptors and tile lists of batched GEMM launches
+  DevBuf rgemm_args;  // the same for the real GEMMs of the ln det stage
   DevBuf gemm_args;
   DevBuf oz_args;     // descriptors of the tensor-core GEMM launches
   DevBuf work;        // per-call workspace

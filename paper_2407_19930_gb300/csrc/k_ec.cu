@@ -17,7 +17,11 @@
 //     2 x 2 real blocks [[Re, -Im], [Im, Re]], W produced transposed so that the second GEMM reads
 //     it row by row.
 // The diagonal blocks, the panel solves, the logarithms and the energy sum are FP64 in both.
+// On the FP64 route the q with q = -q (chi0 and, when checked, V real there) run every step in
+// real arithmetic (A = I - L^T chi0 L, real GEMMs and a real Cholesky): a quarter of the flops.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -137,19 +141,21 @@ __global__ void k_zero_upper(double2 *const *mats, int n, int ld) {
   if (j > i) M[(size_t)i * ld + j] = make_double2(0.0, 0.0);
 }
 
-// Largest |V(-q) - conj V(q)| over the pairs q < -q (res[0]) and largest |V(q)| (res[1]), as the
-// bit patterns of non-negative doubles (ordered like the values) for atomicMax.
+// Largest |V(-q) - conj V(q)| over the pairs q < -q (res[0]), largest |V(q)| (res[1]) and largest
+// |Im V(q)| over the q = -q (res[2]), as the bit patterns of non-negative doubles (ordered like the
+// values) for atomicMax.
 __global__ void k_conj_check(const double2 *V, int n, int n1, int n2, int n3, unsigned long long *res) {
   const int q = blockIdx.y;
   const int a = q / (n2 * n3), b = (q / n3) % n2, c = q % n3;
   const int p = (((n1 - a) % n1) * n2 + (n2 - b) % n2) * n3 + (n3 - c) % n3;
-  if (p <= q) return;
+  if (p < q) return;
+  const bool self = p == q;
   const size_t nn = (size_t)n * n;
   const double2 *Vq = V + nn * q, *Vp = V + nn * p;
   double d = 0.0, m = 0.0;
   for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < nn; x += (size_t)gridDim.x * blockDim.x) {
     const double2 u = Vq[x], v = Vp[x];
-    d = fmax(d, fmax(fabs(v.x - u.x), fabs(v.y + u.y)));
+    d = self ? fmax(d, fabs(u.y)) : fmax(d, fmax(fabs(v.x - u.x), fabs(v.y + u.y)));
     m = fmax(m, fmax(fabs(u.x), fabs(u.y)));
     if (isnan(u.x + u.y + v.x + v.y)) d = INFINITY;
   }
@@ -158,9 +164,210 @@ __global__ void k_conj_check(const double2 *V, int n, int n1, int n2, int n3, un
     m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicMax(res, (unsigned long long)__double_as_longlong(d));
+    atomicMax(res + (self ? 2 : 0), (unsigned long long)__double_as_longlong(d));
     atomicMax(res + 1, (unsigned long long)__double_as_longlong(m));
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// Real route for the q with q = -q (time-reversal-invariant q: q.R is a multiple of pi for every
+// lattice vector, so chi0(q, i omega) = sum_R (+-1) chi0(R, i omega) is real symmetric, and V(q)
+// is real when V(-q) = conj V(q)).  There A = I - L^T chi0 L is real and every product runs in
+// real arithmetic: a quarter of the complex flops.
+
+// Lt = (Re L)^T, n x n, through 32 x 32 shared-memory tiles
+__global__ void k_real_transpose(const double2 *L, int n, double *Lt) {
+  __shared__ double t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int gr = r0 + r, gc = c0 + threadIdx.x;
+    if (gr < n && gc < n) t[r][threadIdx.x] = L[(size_t)gr * n + gc].x;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int gr = c0 + r, gc = r0 + threadIdx.x;   // Lt[gr][gc] = L[gc][gr]
+    if (gr < n && gc < n) Lt[(size_t)gr * n + gc] = t[threadIdx.x][r];
+  }
+}
+
+__global__ void k_real_part(const double2 *src, size_t count, double *dst) {
+  const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < count) dst[x] = src[x].x;
+}
+
+struct RGemm {
+  const double *A, *B;   // A [M][K] (lda), B [N][K] (ldb), row-major
+  double *C;             // C [M][N] (ldc)
+  int M, N, K, lda, ldb, ldc;
+  double alpha, beta;
+};
+struct RTile {
+  int e, m0, n0, k0;     // descriptor, output tile origin, first k (rows of A zero before it)
+};
+
+// C = alpha A B^T + beta C on the FP64 tensor cores (mma.sync m8n8k4 f64): one 64 x 64 tile per
+// CTA, four warps with 32 x 32 warp tiles, K staged 16 at a time through shared memory from the
+// tile's k0 (A is upper triangular in the ln det products, zero left of the tile's first row).
+__global__ void __launch_bounds__(128) k_dgemm_tri(const RGemm *__restrict__ gs, const RTile *__restrict__ tiles) {
+  constexpr int BM = 64, BN = 64, KS = 16, NT = 128;
+  const RTile t = tiles[blockIdx.x];
+  const RGemm g = gs[t.e];
+  __shared__ double As[BM][KS + 1];
+  __shared__ double Bs[BN][KS + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1, gid = lane >> 2, tig = lane & 3;
+  double acc[4][4][2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c][0] = acc[r][c][1] = 0.0;
+  for (int k0 = t.k0; k0 < g.K; k0 += KS) {
+    for (int e = tid; e < BM * KS; e += NT) {
+      const int row = e / KS, k = e % KS, gm = t.m0 + row, gk = k0 + k;
+      As[row][k] = (gm < g.M && gk < g.K) ? g.A[(size_t)gm * g.lda + gk] : 0.0;
+    }
+    for (int e = tid; e < BN * KS; e += NT) {
+      const int row = e / KS, k = e % KS, gn = t.n0 + row, gk = k0 + k;
+      Bs[row][k] = (gn < g.N && gk < g.K) ? g.B[(size_t)gn * g.ldb + gk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KS; kk += 4) {
+      double a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[wm * 32 + r * 8 + gid][kk + tig];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[wn * 32 + c * 8 + gid][kk + tig];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                       : "+d"(acc[r][c][0]), "+d"(acc[r][c][1])
+                       : "d"(a[r]), "d"(b[c]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int gm = t.m0 + wm * 32 + r * 8 + gid;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int gn = t.n0 + wn * 32 + c * 8 + tig * 2 + hh;
+        if (gn >= g.N) continue;
+        double *p = g.C + (size_t)gm * g.ldc + gn;
+        const double v = g.alpha * acc[r][c][hh];
+        *p = g.beta == 0.0 ? v : v + g.beta * *p;
+      }
+  }
+}
+
+// Real diagonal-block Cholesky (as k_potrf_diag, real arithmetic).
+__global__ void __launch_bounds__(256) k_potrf_diag_r(double *const *mats, int n, int ld, int p0, double *lndet,
+                                                      int *info) {
+  extern __shared__ double ar[];   // [NB][NB + 1]
+  const int b = blockIdx.x;
+  double *M = mats[b];
+  const int nb = min(NB, n - p0);
+  const int lda = NB + 1;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    ar[i * lda + j] = j <= i ? M[(size_t)(p0 + i) * ld + p0 + j] : 0.0;
+  }
+  __syncthreads();
+  __shared__ double dsh;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  double lsum = 0.0;
+  for (int j = 0; j < nb; ++j) {
+    if (threadIdx.x == 0) {
+      double d = ar[j * lda + j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        d = 1.0;
+      }
+      d = sqrt(d);
+      ar[j * lda + j] = d;
+      lsum += 2.0 * log(d);
+      dsh = d;
+    }
+    __syncthreads();
+    const double inv = 1.0 / dsh;
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) ar[i * lda + j] *= inv;
+    __syncthreads();
+    const int m = nb - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k > i) continue;
+      ar[i * lda + k] -= ar[i * lda + j] * ar[k * lda + j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e % nb;
+    if (j <= i) M[(size_t)(p0 + i) * ld + p0 + j] = ar[i * lda + j];
+  }
+  if (threadIdx.x == 0) {
+    lndet[b] += lsum;
+    if (bad) info[b] = 1;
+  }
+}
+
+// Real panel solve X L_pp^T = B (as k_trsm_panel, real arithmetic).
+__global__ void __launch_bounds__(64) k_trsm_panel_r(double *const *mats, int n, int ld, int p0) {
+  extern __shared__ double tr[];
+  double(*L)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(tr);
+  double(*X)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(tr + NB * (NB + 1));
+  const int b = blockIdx.y;
+  double *M = mats[b];
+  const int nb = min(NB, n - p0);
+  const int r0 = p0 + nb + blockIdx.x * 64;
+  if (r0 >= n) return;
+  for (int e = threadIdx.x; e < nb * nb; e += 64) {
+    const int i = e / nb, j = e % nb;
+    L[i][j] = M[(size_t)(p0 + i) * ld + p0 + j];
+  }
+  const int rows = min(64, n - r0);
+  for (int e = threadIdx.x; e < rows * nb; e += 64) {
+    const int i = e / nb, j = e % nb;
+    X[i][j] = M[(size_t)(r0 + i) * ld + p0 + j];
+  }
+  __syncthreads();
+  const int i = threadIdx.x;
+  if (i < rows) {
+    for (int j = 0; j < nb; ++j) {
+      double sv = X[i][j];
+      for (int k = 0; k < j; ++k) sv -= X[i][k] * L[j][k];
+      X[i][j] = sv / L[j][j];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * nb; e += 64) {
+    const int r = e / nb, j = e % nb;
+    M[(size_t)(r0 + r) * ld + p0 + j] = X[r][j];
+  }
+}
+
+// A = -L^T chi0 L on entry: trace[b] = -sum A_ii, then A_ii += 1 (real route).
+__global__ void k_diag_shift_r(double *const *mats, int n, int ld, double *trace) {
+  double *M = mats[blockIdx.x];
+  double sv = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double *p = M + (size_t)i * ld + i;
+    sv -= *p;
+    *p += 1.0;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = sv;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) trace[blockIdx.x] = red[0];
 }
 
 // A = -L^H chi0 L on entry (lower triangle).  trace[b] = Re Tr(L^H chi0 L) = -sum Re A_ii;
@@ -278,6 +485,72 @@ void potrf_batched(Handle &h, double2 *const *d_mats, const std::vector<double2 
   LR_CUDA(cudaGetLastError());
 }
 
+// Batched real GEMMs (k_dgemm_tri) of one launch.  shape: 0 = every output tile, 1 = tiles on or
+// above the diagonal (n0 >= m0), 2 = on or below (n0 <= m0); kfrom_row: K starts at the tile's
+// first row (A zero left of its diagonal).  flops: algorithmic count for the stats.
+void rgemm_batched(Handle &h, const std::vector<RGemm> &gs, int shape, bool kfrom_row, double flops) {
+  constexpr int T = 64;
+  std::vector<RTile> tiles;
+  for (int e = 0; e < (int)gs.size(); ++e)
+    for (int m0 = 0; m0 < gs[e].M; m0 += T)
+      for (int n0 = 0; n0 < gs[e].N; n0 += T) {
+        if ((shape == 1 && n0 < m0) || (shape == 2 && n0 > m0)) continue;
+        tiles.push_back({e, m0, n0, kfrom_row ? m0 : 0});
+      }
+  if (tiles.empty()) return;
+  const size_t b1 = gs.size() * sizeof(RGemm), b2 = tiles.size() * sizeof(RTile);
+  const size_t off2 = (b1 + 255) / 256 * 256;
+  static thread_local std::vector<char> host;
+  host.resize(off2 + b2);
+  std::memcpy(host.data(), gs.data(), b1);
+  std::memcpy(host.data() + off2, tiles.data(), b2);
+  h.ensure(h.rgemm_args, off2 + b2);
+  cudaStream_t s = h.stream;
+  LR_CUDA(cudaMemcpyAsync(h.rgemm_args.p, host.data(), off2 + b2, cudaMemcpyHostToDevice, s));
+  const RGemm *dg = reinterpret_cast<const RGemm *>(h.rgemm_args.p);
+  const RTile *dt = reinterpret_cast<const RTile *>((const char *)h.rgemm_args.p + off2);
+  Handle::Timed tm{nullptr, nullptr, flops, 1};
+  LR_CUDA(cudaEventCreate(&tm.a));
+  LR_CUDA(cudaEventCreate(&tm.b));
+  LR_CUDA(cudaEventRecord(tm.a, s));
+  for (size_t t0 = 0; t0 < tiles.size(); t0 += 1u << 30) {
+    const unsigned nb = (unsigned)std::min<size_t>(tiles.size() - t0, 1u << 30);
+    k_dgemm_tri<<<nb, 128, 0, s>>>(dg, dt + t0);
+    ++launch_counter();
+  }
+  LR_CUDA(cudaEventRecord(tm.b, s));
+  h.timed.push_back(tm);
+  LR_CUDA(cudaGetLastError());
+}
+
+// Blocked real Cholesky of `mats` (n x n, lower, in place), in step (as potrf_batched).
+void potrf_batched_r(Handle &h, double *const *d_mats, const std::vector<double *> &mats, int n, int ld,
+                     double *lndet, int *info) {
+  cudaStream_t s = h.stream;
+  const int B = (int)mats.size();
+  const size_t smem = (size_t)NB * (NB + 1) * sizeof(double);
+  LR_CUDA(cudaFuncSetAttribute(k_potrf_diag_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LR_CUDA(cudaFuncSetAttribute(k_trsm_panel_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smem)));
+  for (int p0 = 0; p0 < n; p0 += NB) {
+    k_potrf_diag_r<<<B, 256, smem, s>>>(d_mats, n, ld, p0, lndet, info);
+    ++launch_counter();
+    const int nb = std::min(NB, n - p0), rest = n - p0 - nb;
+    if (rest <= 0) break;
+    dim3 g((unsigned)((rest + 63) / 64), (unsigned)B);
+    k_trsm_panel_r<<<g, 64, 2 * smem, s>>>(d_mats, n, ld, p0);
+    ++launch_counter();
+    // A22 -= P P^T on the lower tiles, P = A[p0+nb.., p0..p0+nb)
+    std::vector<RGemm> batch;
+    for (int b = 0; b < B; ++b) {
+      double *M = mats[b];
+      const double *P = M + (size_t)(p0 + nb) * ld + p0;
+      batch.push_back(RGemm{P, P, M + (size_t)(p0 + nb) * ld + p0 + nb, rest, rest, nb, ld, ld, ld, -1.0, 1.0});
+    }
+    rgemm_batched(h, batch, 2, false, 2.0 * B * (0.5 * rest * (rest + 1.0)) * nb);
+  }
+  LR_CUDA(cudaGetLastError());
+}
+
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Workspace of the ln det stage: L[nq], W[nw], A[nw] (complex n x n), pointer tables,
@@ -371,23 +644,35 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   // q <-> -q: chi0(R) is real, so chi0(-q) = conj chi0(q); when also V(-q) = conj V(q) (to 1e-12
   // of max |V|), the integrand of -q equals that of q (ln det and trace of complex-conjugate
   // matrices), and only q <= -q is computed.  The check runs once per set of V(q).
-  if (h.vq_sym < 0) {
-    unsigned long long *res = (unsigned long long *)(w + o_ld);   // lndet is cleared again below
-    LR_CUDA(cudaMemsetAsync(res, 0, 16, s));
+  // The same check gives the real route (section above) its condition: V(q) real at q = -q.
+  if (h.vq_sym < 0 || h.vq_real < 0) {
+    // 24 bytes at lndet (its region is at least 256 bytes long; it is cleared again below)
+    unsigned long long *res = (unsigned long long *)(w + o_ld);
+    LR_CUDA(cudaMemsetAsync(res, 0, 24, s));
     k_conj_check<<<dim3(64, (unsigned)nq), 256, 0, s>>>((const double2 *)h.d_vq.p, n, h.mesh.n1, h.mesh.n2,
                                                         h.mesh.n3, res);
     ++launch_counter();
     LR_CUDA(cudaGetLastError());
-    double dm[2] = {0, 0};
-    LR_CUDA(cudaMemcpyAsync(dm, res, 16, cudaMemcpyDeviceToHost, s));
+    double dm[3] = {0, 0, 0};
+    LR_CUDA(cudaMemcpyAsync(dm, res, 24, cudaMemcpyDeviceToHost, s));
     LR_CUDA(cudaStreamSynchronize(s));
     h.vq_sym = dm[0] <= 1e-12 * dm[1] ? 1 : 0;
-    LR_CUDA(cudaMemsetAsync(lndet, 0, 16, s));
+    h.vq_real = dm[2] <= 1e-12 * dm[1] ? 1 : 0;
+    LR_CUDA(cudaMemsetAsync(lndet, 0, 24, s));
   }
   std::vector<int> qlist;
   for (int q = 0; q < nq; ++q)
     if (h.vq_sym != 1 || q <= h.mesh.neg(q)) qlist.push_back(q);
   const int nql = (int)qlist.size();
+  // positions in qlist, the complex ones first, then those of the real route (FP64 route only):
+  // the per-(q, omega) ln det and trace are kept in this order until the end
+  std::vector<int> order;
+  auto real_q = [&](int q) { return S < 0 && h.vq_real == 1 && q == h.mesh.neg(q); };
+  for (int qi = 0; qi < nql; ++qi)
+    if (!real_q(qlist[qi])) order.push_back(qi);
+  const int nx = (int)order.size();
+  for (int qi = 0; qi < nql; ++qi)
+    if (real_q(qlist[qi])) order.push_back(qi);
   // Cholesky of every V(q) computed, packed in qlist order (the batched factorisation needs a
   // uniform stride)
   std::vector<double2 *> lp(nql);
@@ -403,7 +688,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     ++launch_counter();
   }
   const double2 *chi = (const double2 *)h.d_chi_qw.p;
-  // A(q, omega) of the q of a chunk, packed: A[(qi - c0) * nw + k]; each chunk is factorised in
+  // A(q, omega) of the q of a chunk, packed: A[(pos - c0) * nw + k]; each chunk is factorised in
   // one lockstep batch
   double2 **aptr = ptrs + nq;
   double *lndet_c = (double *)(w + lay.o_ldc), *trace_c = (double *)(w + lay.o_trc);
@@ -415,14 +700,14 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   const double fl_w = 8.0 * nw * dn * (dn * (dn + 1) / 2), fl_a = 8.0 * nw * (dn * (dn + 1) * (dn + 2) / 6);
   // FP64 route: A needs W only on and below its diagonal tiles (j >= k), sum_k (n - k)^2 MACs
   const double fl_w_lower = 8.0 * nw * (dn * (dn + 1) * (2 * dn + 1) / 6);
-  for (int c0 = 0; c0 < nql; c0 += nc) {
-    const int c1 = std::min(nql, c0 + nc);
+  for (int c0 = 0; c0 < nx; c0 += nc) {
+    const int c1 = std::min(nx, c0 + nc);
     std::vector<double2 *> ap((size_t)(c1 - c0) * nw);
     for (size_t b = 0; b < ap.size(); ++b) ap[b] = Am + b * n2;
     LR_CUDA(cudaMemcpyAsync(aptr, ap.data(), ap.size() * 8, cudaMemcpyHostToDevice, s));
-    for (int qi = c0; qi < c1; ++qi) {
-      const int q = qlist[qi];
-      double2 *Aq = Am + (size_t)(qi - c0) * nw * n2;
+    for (int pos = c0; pos < c1; ++pos) {
+      const int qi = order[pos], q = qlist[qi];
+      double2 *Aq = Am + (size_t)(pos - c0) * nw * n2;
       if (S >= 0) {
         const double2 *L = Lq + (size_t)qi * n2;
         oz::split_complex(L, n, oz::OP_N, false, n, n, 1, 0, sl, s);     // B'^T of W = chi0 L
@@ -496,10 +781,43 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     ++launch_counter();
     potrf_batched(h, aptr, ap, n, n, lndet_c + (size_t)c0 * nw, info + nq + (size_t)c0 * nw, tc);
   }
-  for (int qi = 0; qi < nql; ++qi) {   // to the flat (q, omega) order
-    const int q = qlist[qi];
-    LR_CUDA(cudaMemcpyAsync(lndet + (size_t)q * nw, lndet_c + (size_t)qi * nw, nw * 8, cudaMemcpyDeviceToDevice, s));
-    LR_CUDA(cudaMemcpyAsync(trace + (size_t)q * nw, trace_c + (size_t)qi * nw, nw * 8, cudaMemcpyDeviceToDevice, s));
+  if (nql > nx) {
+    // real route, all its (q, omega) in one lockstep batch, in the A region (real matrices take
+    // half the room of complex ones): Ar[B] then Lt; W's region holds Re chi0 and W^T of one q
+    const int nr = nql - nx;
+    const size_t B = (size_t)nr * nw;
+    double *Ar = (double *)Am, *Lt = Ar + B * n2;
+    double *Xr = (double *)Wm, *WT = Xr + (size_t)nw * n2;
+    std::vector<double *> ar(B);
+    for (size_t b = 0; b < B; ++b) ar[b] = Ar + b * n2;
+    double **rptr = reinterpret_cast<double **>(aptr);
+    LR_CUDA(cudaMemcpyAsync(rptr, ar.data(), B * 8, cudaMemcpyHostToDevice, s));
+    const unsigned nt = (unsigned)((n + 31) / 32);
+    for (int r = 0; r < nr; ++r) {
+      const int qi = order[nx + r], q = qlist[qi];
+      k_real_transpose<<<dim3(nt, nt), dim3(32, 8), 0, s>>>(Lq + (size_t)qi * n2, n, Lt);
+      const size_t cnt = (size_t)nw * n2;
+      k_real_part<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(chi + (size_t)q * nw * n2, cnt, Xr);
+      launch_counter() += 2;
+      LR_CUDA(cudaGetLastError());
+      // W^T = Lt Xr^T (= (chi0 L)^T) on and above the diagonal tiles; A = -Lt (W^T)^T = -L^T W on
+      // and below them; Lt is upper triangular, so K starts at the tile's first row
+      std::vector<RGemm> g1, g2;
+      for (int k = 0; k < nw; ++k) {
+        g1.push_back(RGemm{Lt, Xr + (size_t)k * n2, WT + (size_t)k * n2, n, n, n, n, n, n, 1.0, 0.0});
+        g2.push_back(RGemm{Lt, WT + (size_t)k * n2, Ar + ((size_t)r * nw + k) * n2, n, n, n, n, n, n, -1.0, 0.0});
+      }
+      rgemm_batched(h, g1, 1, true, fl_w_lower / 4);
+      rgemm_batched(h, g2, 2, true, fl_a / 4);
+    }
+    k_diag_shift_r<<<(unsigned)B, 256, 0, s>>>(rptr, n, n, trace_c + (size_t)nx * nw);
+    ++launch_counter();
+    potrf_batched_r(h, rptr, ar, n, n, lndet_c + (size_t)nx * nw, info + nq + (size_t)nx * nw);
+  }
+  for (int pos = 0; pos < nql; ++pos) {   // to the flat (q, omega) order
+    const int q = qlist[order[pos]];
+    LR_CUDA(cudaMemcpyAsync(lndet + (size_t)q * nw, lndet_c + (size_t)pos * nw, nw * 8, cudaMemcpyDeviceToDevice, s));
+    LR_CUDA(cudaMemcpyAsync(trace + (size_t)q * nw, trace_c + (size_t)pos * nw, nw * 8, cudaMemcpyDeviceToDevice, s));
   }
   for (int q : qlist) {   // the integrands of -q
     const int p = h.mesh.neg(q);
@@ -525,10 +843,12 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     for (int q = 0; q < nq; ++q) ec_q[q] = res[1 + q];
   if (ec_w)
     for (int k = 0; k < nw; ++k) ec_w[k] = res[1 + nq + k];
-  // flop count of this stage (complex MAC = 8 real flops): per q (4/3 n^3 real for the Cholesky of
-  // V), per (q, omega): W = chi0 L (n^3/2 MAC), L^H W lower (n^3/6 MAC), Cholesky (n^3/6 MAC)
+  // flop count of this stage (complex MAC = 8 real flops, real MAC = 2): per q (4/3 n^3 real for
+  // the Cholesky of V), per (q, omega): W = chi0 L (n^3/2 MAC; n^3/3 on the tiles the FP64 route
+  // needs), L^H W lower (n^3/6 MAC), Cholesky (n^3/6 MAC)
   const double n3 = (double)n * n * n;
-  h.stats.flop_ec = nql * (8.0 * n3 / 6.0) + (double)nql * nw * 8.0 * ((S >= 0 ? n3 / 2 : n3 / 3) + n3 / 6 + n3 / 6);
+  const double macs = (S >= 0 ? n3 / 2 : n3 / 3) + n3 / 6 + n3 / 6;
+  h.stats.flop_ec = nql * (8.0 * n3 / 6.0) + (double)nx * nw * 8.0 * macs + (double)(nql - nx) * nw * 2.0 * macs;
   return LIBRPA_OK;
 }
 
