@@ -57,7 +57,7 @@ TRAFFIC = {
     "k_zgemm": {"bytes_per_launch": 1.6075e9, "src_sha": "02ef5086221f2c12"},
     # 330 launches of one FP64 step (N/X-step and final-contraction groups, 160 batches each, plus
     # the tile tuner's first pass): 229.7 GB read + 84.8 GB written (profiles/k_dgemm_nt_dram_graphene_fp64.md)
-    "k_dgemm_nt": {"bytes_per_launch": 0.953e9, "src_sha": "b00f0c05ede94537"},
+    "k_dgemm_nt": {"bytes_per_launch": 0.953e9, "src_sha": "613c2603be84cf54"},
 }
 
 

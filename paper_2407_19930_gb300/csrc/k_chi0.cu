@@ -979,110 +979,110 @@ void chi0_run_tc(Handle &h) {
   if (h.g_screen > 0) LR_CUDA(cudaMemsetAsync(h.d_chi_tau.p, 0, (size_t)ntau * nR * naux * naux * sizeof(double), s));
   h.flop_chi0_run = 0;
   for (h.cur_spin = 0; h.cur_spin < h.nspins; ++h.cur_spin) {
-  const ScreenSel sel = screen_select(h, rl);
-  const long long total_pts = (long long)sel.pts.size();
-  h.stats.n_points_chi0 += total_pts;
-  h.stats.n_points_skipped += sel.skipped;
-  h.flop_chi0_run += total_pts * P.flop_per_point;
-  for (long long p0 = 0; p0 < total_pts; p0 += npb) {
-    const int np = (int)std::min(npb, total_pts - p0);
-    std::vector<Point> pts(sel.pts.begin() + p0, sel.pts.begin() + p0 + np);
-    h.ensure(P.t_pts, np * sizeof(Point));
-    LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
-    // digit planes of the gathered Green's-function operands, straight from G
-    oz::GatherSrc gs;
-    gs.kind = 0;
-    gs.G = g_spin(h);
-    gs.g_gstride = (long long)g_gstride;
-    gs.nR = nR;
-    gs.nao = nao;
-    gs.n1 = h.mesh.n1;
-    gs.n2 = h.mesh.n2;
-    gs.n3 = h.mesh.n3;
-    gs.natoms = nat;
-    gs.rows_per_entry = P.m_all;
-    gs.pts = (const int *)P.t_pts.p;
-    gs.uni = (const int *)P.d_uni.p;
-    gs.lam = (const int *)P.d_lam.p;
-    gs.lam_off = (const long long *)P.t_lam_off.p;
-    gs.m = (const int *)P.t_m.p;
-    oz::Sliced sbg, sag, sod;
-    oz::sliced_bind(sbg, wbg, np * rows_bg, P.max_m, S);
-    oz::sliced_bind(sag, wag, np * rows_ag, P.max_m, S);
-    oz::sliced_bind(sod, wod, np * rows_o, P.max_nm, S);
-    oz::split_gather(gs, np * rows_bg, P.max_m, sbg, s);
-    gs.kind = 1;
-    gs.rows_per_entry = nao;
-    oz::split_gather(gs, np * rows_ag, P.max_m, sag, s);
-    // N-step: N_V = Cpack_V Bg_V^T;  X-step: X_V = Ag_V Cpack_V^T (as FP32 pairs when the O
-    // assembly runs in FP32 pairs)
-    const bool pairs = S >= 4 && S <= oz::SMAX;
-    std::vector<oz::Entry> en, ex;
-    for (int q = 0; q < np; ++q)
-      for (int g = 0; g < 2; ++g)
-        for (int V = 0; V < nat; ++V) {
-          const int rowsV = h.n_aux[V] * h.n_ao[V], e = (q * 2 + g) * nat + V;
-          oz::Entry a{};
-          a.a_row0 = P.cpnx_off[V];
-          a.b_row0 = e * P.m_all;
-          a.M = rowsV;
-          a.N = P.m_all;
-          a.K = P.m[V];
-          a.C = Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V];
-          a.ldc = P.m_all;
-          a.alpha = 1.0;
-          a.mode = pairs ? 3 : 0;
-          en.push_back(a);
-          oz::Entry b{};
-          b.a_row0 = e * nao;
-          b.b_row0 = P.cpnx_off[V];
-          b.M = nao;
-          b.N = rowsV;
-          b.K = P.m[V];
-          b.C = Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V];
-          b.mode = pairs ? 3 : 0;
-          b.ldc = rowsV;
-          b.alpha = 1.0;
-          ex.push_back(b);
-        }
-    timed_grouped(h, cpnx, sbg, en, err, P.gargs1);
-    timed_grouped(h, sag, cpnx, ex, err, P.gargs2);
-    run_oassemble(h, (const Point *)P.t_pts.p, np, Nw, Xw, Ow);
-    // digit planes of O (rows nu per (point, U), K = n_U m_U), then the final contraction
-    {
-      std::vector<long long> off(np * nat);
-      std::vector<int> ke(np * nat);
+    const ScreenSel sel = screen_select(h, rl);
+    const long long total_pts = (long long)sel.pts.size();
+    h.stats.n_points_chi0 += total_pts;
+    h.stats.n_points_skipped += sel.skipped;
+    h.flop_chi0_run += total_pts * P.flop_per_point;
+    for (long long p0 = 0; p0 < total_pts; p0 += npb) {
+      const int np = (int)std::min(npb, total_pts - p0);
+      std::vector<Point> pts(sel.pts.begin() + p0, sel.pts.begin() + p0 + np);
+      h.ensure(P.t_pts, np * sizeof(Point));
+      LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
+      // digit planes of the gathered Green's-function operands, straight from G
+      oz::GatherSrc gs;
+      gs.kind = 0;
+      gs.G = g_spin(h);
+      gs.g_gstride = (long long)g_gstride;
+      gs.nR = nR;
+      gs.nao = nao;
+      gs.n1 = h.mesh.n1;
+      gs.n2 = h.mesh.n2;
+      gs.n3 = h.mesh.n3;
+      gs.natoms = nat;
+      gs.rows_per_entry = P.m_all;
+      gs.pts = (const int *)P.t_pts.p;
+      gs.uni = (const int *)P.d_uni.p;
+      gs.lam = (const int *)P.d_lam.p;
+      gs.lam_off = (const long long *)P.t_lam_off.p;
+      gs.m = (const int *)P.t_m.p;
+      oz::Sliced sbg, sag, sod;
+      oz::sliced_bind(sbg, wbg, np * rows_bg, P.max_m, S);
+      oz::sliced_bind(sag, wag, np * rows_ag, P.max_m, S);
+      oz::sliced_bind(sod, wod, np * rows_o, P.max_nm, S);
+      oz::split_gather(gs, np * rows_bg, P.max_m, sbg, s);
+      gs.kind = 1;
+      gs.rows_per_entry = nao;
+      oz::split_gather(gs, np * rows_ag, P.max_m, sag, s);
+      // N-step: N_V = Cpack_V Bg_V^T;  X-step: X_V = Ag_V Cpack_V^T (as FP32 pairs when the O
+      // assembly runs in FP32 pairs)
+      const bool pairs = S >= 4 && S <= oz::SMAX;
+      std::vector<oz::Entry> en, ex;
       for (int q = 0; q < np; ++q)
-        for (int U = 0; U < nat; ++U) {
-          off[q * nat + U] = (long long)q * P.o_sz + P.o_off[U];
-          ke[q * nat + U] = h.n_ao[U] * P.m[U];
-        }
-      h.ensure(P.t_oe_off, off.size() * 8);
-      h.ensure(P.t_oe_k, ke.size() * 4);
-      LR_CUDA(cudaMemcpyAsync(P.t_oe_off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s));
-      LR_CUDA(cudaMemcpyAsync(P.t_oe_k.p, ke.data(), ke.size() * 4, cudaMemcpyHostToDevice, s));
-      oz::split_ragged(Ow, (const long long *)P.t_oe_off.p, (const int *)P.t_oe_k.p, naux, np * nat, P.max_nm, sod, s);
-      LR_CUDA(cudaStreamSynchronize(s));   // the host tables above are temporaries
-    }
-    std::vector<oz::Entry> ef;
-    for (int q = 0; q < np; ++q) {
-      double *chi = (double *)h.d_chi_tau.p + ((size_t)pts[q].itau * nR + pts[q].iR) * naux * naux;
-      for (int U = 0; U < nat; ++U) {
-        oz::Entry f{};
-        f.a_row0 = h.aux_off[U];
-        f.b_row0 = (q * nat + U) * naux;
-        f.M = h.n_aux[U];
-        f.N = naux;
-        f.K = h.n_ao[U] * P.m[U];
-        f.C = chi + (size_t)h.aux_off[U] * naux;
-        f.ldc = naux;
-        f.alpha = -spin;
-        f.beta = h.cur_spin > 0 ? 1.0 : 0.0;
-        ef.push_back(f);
+        for (int g = 0; g < 2; ++g)
+          for (int V = 0; V < nat; ++V) {
+            const int rowsV = h.n_aux[V] * h.n_ao[V], e = (q * 2 + g) * nat + V;
+            oz::Entry a{};
+            a.a_row0 = P.cpnx_off[V];
+            a.b_row0 = e * P.m_all;
+            a.M = rowsV;
+            a.N = P.m_all;
+            a.K = P.m[V];
+            a.C = Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V];
+            a.ldc = P.m_all;
+            a.alpha = 1.0;
+            a.mode = pairs ? 3 : 0;
+            en.push_back(a);
+            oz::Entry b{};
+            b.a_row0 = e * nao;
+            b.b_row0 = P.cpnx_off[V];
+            b.M = nao;
+            b.N = rowsV;
+            b.K = P.m[V];
+            b.C = Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V];
+            b.mode = pairs ? 3 : 0;
+            b.ldc = rowsV;
+            b.alpha = 1.0;
+            ex.push_back(b);
+          }
+      timed_grouped(h, cpnx, sbg, en, err, P.gargs1);
+      timed_grouped(h, sag, cpnx, ex, err, P.gargs2);
+      run_oassemble(h, (const Point *)P.t_pts.p, np, Nw, Xw, Ow);
+      // digit planes of O (rows nu per (point, U), K = n_U m_U), then the final contraction
+      {
+        std::vector<long long> off(np * nat);
+        std::vector<int> ke(np * nat);
+        for (int q = 0; q < np; ++q)
+          for (int U = 0; U < nat; ++U) {
+            off[q * nat + U] = (long long)q * P.o_sz + P.o_off[U];
+            ke[q * nat + U] = h.n_ao[U] * P.m[U];
+          }
+        h.ensure(P.t_oe_off, off.size() * 8);
+        h.ensure(P.t_oe_k, ke.size() * 4);
+        LR_CUDA(cudaMemcpyAsync(P.t_oe_off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s));
+        LR_CUDA(cudaMemcpyAsync(P.t_oe_k.p, ke.data(), ke.size() * 4, cudaMemcpyHostToDevice, s));
+        oz::split_ragged(Ow, (const long long *)P.t_oe_off.p, (const int *)P.t_oe_k.p, naux, np * nat, P.max_nm, sod, s);
+        LR_CUDA(cudaStreamSynchronize(s));   // the host tables above are temporaries
       }
+      std::vector<oz::Entry> ef;
+      for (int q = 0; q < np; ++q) {
+        double *chi = (double *)h.d_chi_tau.p + ((size_t)pts[q].itau * nR + pts[q].iR) * naux * naux;
+        for (int U = 0; U < nat; ++U) {
+          oz::Entry f{};
+          f.a_row0 = h.aux_off[U];
+          f.b_row0 = (q * nat + U) * naux;
+          f.M = h.n_aux[U];
+          f.N = naux;
+          f.K = h.n_ao[U] * P.m[U];
+          f.C = chi + (size_t)h.aux_off[U] * naux;
+          f.ldc = naux;
+          f.alpha = -spin;
+          f.beta = h.cur_spin > 0 ? 1.0 : 0.0;
+          ef.push_back(f);
+        }
+      }
+      timed_grouped(h, cpf, sod, ef, err, P.gargs3);
     }
-    timed_grouped(h, cpf, sod, ef, err, P.gargs3);
-  }
   }
   h.cur_spin = 0;
   fill_partners(h);
