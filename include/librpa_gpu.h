@@ -185,6 +185,17 @@ int librpa_gpu_set_coulomb(librpa_gpu_t h, int iq, const double *V_re, const dou
 int librpa_gpu_set_grid(librpa_gpu_t h, int ntau, const double *tau, int nomega,
                         const double *omega, const double *w_omega, const double *gamma);
 
+/* Weights w_q of the q sum of E_c (Sec. 2, E_c equation, whose 1/N_q is the uniform case;
+ * Appendix B passes irreducible k points with weights, set_ibz2bz_index_and_weight).
+ *   w [nq], one weight per q of the full Gamma-centred mesh (flat order), finite and >= 0,
+ *   at least one > 0; w = NULL restores 1/N_q.  The caller maps its irreducible set onto the
+ *   mesh: a representative carries its star's weight, the other members 0.  librpa_gpu_ec then
+ *   returns E_c = (1/2 pi) sum_q w_q sum_k W_k [...] and ec_q[q] = w_q's term; q of zero weight
+ *   are not computed (when V(-q) = conj V(q), a q and -q share one computation).  The weights
+ *   are not normalised.  set_structure resets them.
+ * Errors: E_STATE (no structure), E_ARG. */
+int librpa_gpu_set_q_weights(librpa_gpu_t h, const double *w);
+
 /* Green's-function block screening (Sec. 5: production runs screen G with a threshold of
  * 1e-3; Sec. 2: the decay of G limits the range of R).  The paper gives no formula; the rule
  * here: each atom-pair NAO block G^occ_{IJ}(R, tau_j) and G^vir_{IJ}(R, tau_j) is set to zero
@@ -231,7 +242,7 @@ int librpa_gpu_chi0(librpa_gpu_t h, double *out_re, double *out_im);
 
 /* RPA correlation energy (Sec. 2, Eq. for E_c with Pi = chi0 V and Tr ln = ln det):
  *   E_c = (1/2 pi) sum_q w_q sum_k W_k [ln det(1 - Pi(q, i omega_k)) + Tr Pi(q, i omega_k)]
- * with w_q = 1/N_q.  ln det(1 - chi0 V) is computed as ln det(I - L^H chi0 L) with the
+ * with w_q = 1/N_q (or librpa_gpu_set_q_weights).  ln det(1 - chi0 V) is computed as ln det(I - L^H chi0 L) with the
  * Cholesky factor V = L L^H and a blocked Cholesky of I - L^H chi0 L (FP64).
  *   ec    -> E_c in Ha per cell;
  *   ec_q  -> [nq] per-q contributions (nullable);  ec_w -> [nomega] per-frequency (nullable).

@@ -310,6 +310,7 @@ int librpa_gpu_set_structure(librpa_gpu_t h, int natoms, const double lat[9], co
     h->r_cut = r_cut;
     const int nk = h->mesh.size();
     h->lri.clear();
+    h->wq.clear();
     h->stage_wfc.clear();
     h->stage_vq.clear();
     h->eig.assign((size_t)nspins * nk * h->nao, 0.0);
@@ -442,6 +443,26 @@ int librpa_gpu_set_grid(librpa_gpu_t h, int ntau, const double *tau, int nomega,
     h->gamma.assign(gamma, gamma + (size_t)nomega * ntau);
     h->have_grid = h->grid_user = true;
     h->chi0_done = false;
+    return LIBRPA_OK;
+  });
+}
+
+int librpa_gpu_set_q_weights(librpa_gpu_t h, const double *w) {
+  return guarded(h, [&]() -> int {
+    if (!h->have_structure) return fail(h, LIBRPA_E_STATE, "set_q_weights before set_structure");
+    if (!w) {
+      h->wq.clear();
+      return LIBRPA_OK;
+    }
+    const int nq = h->mesh.size();
+    bool any = false;
+    for (int q = 0; q < nq; ++q) {
+      if (!(w[q] >= 0.0) || !std::isfinite(w[q]))
+        return fail(h, LIBRPA_E_ARG, "set_q_weights: weights must be finite and >= 0");
+      any = any || w[q] > 0.0;
+    }
+    if (!any) return fail(h, LIBRPA_E_ARG, "set_q_weights: at least one weight must be > 0");
+    h->wq.assign(w, w + nq);
     return LIBRPA_OK;
   });
 }

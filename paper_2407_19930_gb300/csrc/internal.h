@@ -130,6 +130,7 @@ struct Handle {
   std::vector<char> have_q;
   int vq_sym = -1;   // V(-q) = conj V(q) for every q: -1 not checked yet, 0 no, 1 yes
   int vq_real = -1;  // V(q) real at every q = -q (same check): -1 not checked yet, 0 no, 1 yes
+  std::vector<double> wq;   // per-q weights of the E_c sum (set_q_weights); empty = 1 / N_q
 
   // Green's-function block screening: threshold (0 = off), the kept-block mask of the current
   // G [spin][g][tau][R][I][J] (host copy) and its device buffers

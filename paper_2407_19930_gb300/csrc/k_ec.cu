@@ -390,14 +390,16 @@ __global__ void k_diag_shift(double2 *const *mats, int n, int ld, double *trace)
   if (threadIdx.x == 0) trace[blockIdx.x] = red[0];
 }
 
-// K6: E_c, per-q and per-omega parts from the per-(q, omega) ln det and trace.
-__global__ void k_energy(const double *lndet, const double *trace, const double *w_omega, int nq, int nw,
-                         double *out /* [1 + nq + nw] */) {
+// K6: E_c, per-q and per-omega parts from the per-(q, omega) ln det and trace.  w_q: per-q weights
+// of the q sum, or nullptr for 1 / N_q.
+__global__ void k_energy(const double *lndet, const double *trace, const double *w_omega, const double *w_q, int nq,
+                         int nw, double *out /* [1 + nq + nw] */) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double pref = 1.0 / (2.0 * M_PI * nq);
+  const double uniform = 1.0 / (2.0 * M_PI * nq);
   double tot = 0.0;
   for (int k = 0; k < nw; ++k) out[1 + nq + k] = 0.0;
   for (int q = 0; q < nq; ++q) {
+    const double pref = w_q ? w_q[q] / (2.0 * M_PI) : uniform;
     double sq = 0.0;
     for (int k = 0; k < nw; ++k) {
       const double f = pref * w_omega[k] * (lndet[q * nw + k] + trace[q * nw + k]);
@@ -556,7 +558,7 @@ size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 // Workspace of the ln det stage: L[nq], W[nw], A[nw] (complex n x n), pointer tables,
 // lndet/trace/info, output, and for the tensor-core route the digit planes.
 struct EcLayout {
-  size_t o_L, o_W, o_A, o_ptr, o_ld, o_tr, o_ldc, o_trc, o_inf, o_out, o_wo, o_err;
+  size_t o_L, o_W, o_A, o_ptr, o_ld, o_tr, o_ldc, o_trc, o_inf, o_out, o_wo, o_wq, o_err;
   size_t o_sx = 0, o_sw = 0, o_sl = 0, o_slh = 0, o_pa = 0, o_pb = 0;
   size_t total = 0;
 };
@@ -587,6 +589,7 @@ EcLayout ec_layout(const Handle &h) {
   l.o_inf = take((size_t)(nq + nq * nw) * 4);
   l.o_out = take((size_t)(1 + nq + nw) * 8);
   l.o_wo = take((size_t)nw * 8);
+  l.o_wq = take((size_t)nq * 8);
   l.o_err = take(4);
   if (S >= 0) {
     l.o_sx = take(oz::sliced_bytes(nw * 2 * n, 2 * n, S));
@@ -627,6 +630,11 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   LR_CUDA(cudaMemsetAsync(info, 0, (size_t)(nq + nq * nw) * 4, s));
   LR_CUDA(cudaMemsetAsync(err, 0, 4, s));
   LR_CUDA(cudaMemcpyAsync(wo, h.w_omega.data(), (size_t)nw * 8, cudaMemcpyHostToDevice, s));
+  // per-q weights of the q sum (set_q_weights), else 1 / N_q; q of zero weight are not computed
+  const bool weighted = !h.wq.empty();
+  double *wqd = weighted ? (double *)(w + lay.o_wq) : nullptr;
+  if (weighted) LR_CUDA(cudaMemcpyAsync(wqd, h.wq.data(), (size_t)nq * 8, cudaMemcpyHostToDevice, s));
+  auto weight = [&](int q) { return weighted ? h.wq[q] : 1.0; };
   TcScratch tcs;
   TcScratch *tc = nullptr;
   oz::Sliced sx, sw, sl, slh;
@@ -661,8 +669,10 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     LR_CUDA(cudaMemsetAsync(lndet, 0, 24, s));
   }
   std::vector<int> qlist;
-  for (int q = 0; q < nq; ++q)
-    if (h.vq_sym != 1 || q <= h.mesh.neg(q)) qlist.push_back(q);
+  for (int q = 0; q < nq; ++q) {
+    const int p = h.mesh.neg(q);
+    if (h.vq_sym == 1 ? q <= p && (weight(q) > 0 || weight(p) > 0) : weight(q) > 0) qlist.push_back(q);
+  }
   const int nql = (int)qlist.size();
   // positions in qlist, the complex ones first, then those of the real route (FP64 route only):
   // the per-(q, omega) ln det and trace are kept in this order until the end
@@ -825,7 +835,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     LR_CUDA(cudaMemcpyAsync(lndet + (size_t)p * nw, lndet + (size_t)q * nw, nw * 8, cudaMemcpyDeviceToDevice, s));
     LR_CUDA(cudaMemcpyAsync(trace + (size_t)p * nw, trace + (size_t)q * nw, nw * 8, cudaMemcpyDeviceToDevice, s));
   }
-  k_energy<<<1, 1, 0, s>>>(lndet, trace, wo, nq, nw, out);
+  k_energy<<<1, 1, 0, s>>>(lndet, trace, wo, wqd, nq, nw, out);
   ++launch_counter();
   LR_CUDA(cudaGetLastError());
   std::vector<double> res(1 + nq + nw);

@@ -107,6 +107,7 @@ _SIGS = {
     "librpa_gpu_set_coulomb": (ctypes.c_int, [_H, ctypes.c_int, _D, _D]),
     "librpa_gpu_set_grid": (ctypes.c_int, [_H, ctypes.c_int, _D, ctypes.c_int, _D, _D, _D]),
     "librpa_gpu_set_screening": (ctypes.c_int, [_H, ctypes.c_double]),
+    "librpa_gpu_set_q_weights": (ctypes.c_int, [_H, _D]),
     "librpa_gpu_build_grid": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D]),
     "librpa_gpu_get_grid": (ctypes.c_int, [_H, _I, _D, _D, _D, _D]),
     "librpa_gpu_chi0": (ctypes.c_int, [_H, _D, _D]),
@@ -266,6 +267,14 @@ def librpa_gpu_set_grid(h, tau, omega, w_omega, gamma):
     tau, omega, w_omega, gamma = _f64(tau), _f64(omega), _f64(w_omega), _f64(gamma)
     _check(h, load().librpa_gpu_set_grid(h, len(tau), _dp(tau), len(omega), _dp(omega), _dp(w_omega),
                                          _dp(gamma)))
+
+
+def librpa_gpu_set_q_weights(h, w=None):
+    if w is None:
+        _check(h, load().librpa_gpu_set_q_weights(h, None))
+        return
+    w = _f64(w)
+    _check(h, load().librpa_gpu_set_q_weights(h, _dp(w)))
 
 
 def librpa_gpu_set_screening(h, threshold):

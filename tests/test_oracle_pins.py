@@ -471,3 +471,20 @@ def test_screen_limits_of_the_energy(cubic):
     k1 = screen.screen_blocks(go, cubic.st.n_ao, 1e-3)[1]
     k2 = screen.screen_blocks(go, cubic.st.n_ao, 1e-2)[1]
     assert np.all(k1 | ~k2) and k1.sum() > k2.sum()   # kept(1e-2) is a strict subset of kept(1e-3)
+
+
+def test_weights_folded_onto_q_leq_minus_q():
+    """The integrand of -q equals that of q (chi0(-q) = conj chi0(q) from real chi0(R), and
+    V(-q) = conj V(q)): E_c with each pair's weight moved onto q <= -q equals the 1/N_q sum, and
+    an irreducible set's weights (star weights on representatives, 0 elsewhere) reproduce it."""
+    inp = syn.make_inputs(syn.cubic_two_atom(nao=4, naux=16, nlow=2, kmesh=(3, 3, 1)), 41, vscale=2e-3)
+    st = inp.st
+    g = ogrid.make_grid(8, *inp.delta_range)
+    out = pipeline.rpa_energy(inp, g)
+    mi = syn.minus_index(st.kmesh)
+    w = np.zeros(st.nk)
+    for q in range(st.nk):
+        w[min(q, mi[q])] += 1.0 / st.nk
+    assert np.count_nonzero(w) < st.nk
+    ec_w = energy.correlation_energy(out["chi_qw"], inp.vq, g["w_omega"], wq=w)[0]
+    assert abs(ec_w - out["ec"]) < 1e-13 * abs(out["ec"])
