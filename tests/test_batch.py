@@ -1,4 +1,4 @@
-"""Batched energies (the batched row of the survey's next items): several structures with
+"""Batched energies: several structures with
 uneven block shapes in one pass, the FP64 chi0 GEMMs of all of them as single grouped
 launches, replayed from a CUDA graph on the second run.  Every energy must equal the same
 handle run alone, and match the oracle."""

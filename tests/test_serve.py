@@ -1,5 +1,5 @@
-"""Serving loop: continuous batching of RPA energy requests (the serving row of the survey's
-next items).  Each result in a mixed, overlapping batch must equal the same request run alone,
+"""Serving loop: continuous batching of RPA energy requests on one GPU, admitted by an HBM
+budget.  Each result in a mixed, overlapping batch must equal the same request run alone,
 and the device-memory estimate used for admission must bound the memory actually held."""
 import time
 
