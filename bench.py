@@ -37,8 +37,8 @@ UNIT = "energies/s"
 WORKLOAD = ("graphene 4x4 supercell + H2O-shaped molecule: 35 atoms, n_ao 431, N_aux 2010, "
             "4x4x1 k-mesh, 16 tau/omega points")
 
-# FP64 tensor-core peak: measured BF16 dense peak x the nominal FP64/BF16 ratio of GB300
-# (1.25 TFLOP/s / 2250 TFLOP/s); no FP64 figure is in the measured-peaks file.
+# nominal FP64/BF16 ratio of GB300 (1.25 TFLOP/s / 2250 TFLOP/s): the FP64 peak derived from the
+# measured BF16 peak, reported next to the FP64 peaks this benchmark measures itself
 NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
 
 # precision presets of the library (include/librpa_gpu.h): name -> (LIBRPA_* value, dtype label)
@@ -123,7 +123,81 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ------------------------------------------------------------------ peaks measured in the run
+
+
+def measure_fp64_peaks(device):
+    """FP64 and TF32 peaks of this GPU, measured now: the DFMA pipe and the FP64 tensor path
+    (mma.sync m8n8k4, the instruction of the FP64 chi0 GEMM) by the register-only probes of
+    probe/peaks.cu, a cuBLAS DGEMM and a cuBLAS TF32 GEMM (8192^3, torch.matmul), each timed with
+    CUDA events after a warm-up, with the SM clock sampled meanwhile."""
+    import ctypes
+    import torch
+    from paper_2407_19930_gb300 import build as lbuild
+    lib = ctypes.CDLL(lbuild.PROBE_LIB)
+    lib.librpa_probe_fp64.restype = ctypes.c_int
+    out = {}
+    clocks = ClockSampler()
+    clocks.start()
+    for name, kind, iters in (("dfma", 0, 200000), ("dmma_m8n8k4", 1, 100000)):
+        tf, ms = ctypes.c_double(), ctypes.c_double()
+        rc = lib.librpa_probe_fp64(kind, iters, 8, ctypes.byref(tf), ctypes.byref(ms))
+        out[name] = {"tflops": tf.value, "ms": ms.value} if rc == 0 else {"error": rc}
+    n = 8192
+
+    def gemm(dtype, tf32):
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        try:
+            a = torch.randn(n, n, dtype=dtype, device=device)
+            b = torch.randn(n, n, dtype=dtype, device=device)
+            c = a @ b
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            reps = 3 if dtype == torch.float64 else 20
+            e0.record()
+            for _ in range(reps):
+                c = a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            del a, b, c
+            return {"tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12, "ms": ms}
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+
+    out["cublas_dgemm"] = gemm(torch.float64, False)
+    out["cublas_tf32"] = gemm(torch.float32, True)
+    out["clocks"] = clocks.stop()
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ CPU oracle sample
+
+
+def cpu_model():
+    """nproc and the CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    name = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().startswith("Model name:"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        name = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "model": name}
+
 
 
 def cpu_sample(inp, grid, budget_s=25.0):
@@ -159,8 +233,18 @@ def cpu_sample(inp, grid, budget_s=25.0):
     t_energy = npts * tp + st.nk * ntau * t_lu + t_green
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"t_energy_s": t_energy, "t_point_s": tp, "t_lu_s": t_lu, "t_green_s": t_green, "cores": cores,
+            "t_sample_s": sum(t_pt) + t_lu + t_green / ntau,
             "sample": "chi0(R,tau) by Algorithm 1 on %d of %d (R,tau) points, ln det by LU on 1 of %d (q,omega), "
                       "G on 1 of %d tau; extrapolated to one energy" % (len(pts), npts, st.nk * ntau, ntau)}
+
+
+def oracle_full_energy(inp, grid):
+    """Seconds of one whole RPA energy by the oracle (G, Algorithm 1 at every (R, tau) point, the
+    transforms, LU of every (q, omega)); returns (seconds, E_c)."""
+    from oracle import pipeline
+    t0 = time.perf_counter()
+    out = pipeline.rpa_energy(inp, grid)
+    return time.perf_counter() - t0, out["ec"]
 
 
 # ------------------------------------------------------------------ arms
@@ -189,28 +273,86 @@ def dist_init():
 
 
 def run_reference(args):
+    """The oracle as the reference arm.  Each step is a bounded sample of one energy of the
+    workload (Algorithm 1 at one (R, tau) point, one LU of a (q, omega) matrix, G at one tau);
+    ms_per_step is the measured wall time of that sample, and value is one energy's time
+    extrapolated from the sample (stated in the "extrapolated" key).  With --full NAME the whole
+    energy of a workload runs instead, median of --steps runs plus one single-thread run."""
     ws, rank, local = dist_init()
     if rank != 0:
         return 0
     from paper_2407_19930_gb300 import synthetic as syn
     from oracle import build as obuild, grid as ogrid
     obuild.build()
+    if args.full:
+        return run_reference_full(args)
     inp = syn.config_graphene()
     grid = ogrid.make_grid(16, *inp.delta_range)
     per = []
     for i in range(args.warmup + args.steps):
-        s = cpu_sample(inp, grid, budget_s=max(5.0, 60.0 / max(1, args.warmup + args.steps)))
+        t0 = time.perf_counter()
+        s = cpu_sample(inp, grid, budget_s=0.0)
+        s["wall_s"] = time.perf_counter() - t0
         if i >= args.warmup:
             per.append(s)
     t = statistics.median([s["t_energy_s"] for s in per])
     v = 1.0 / t
+    ms_step = statistics.median([s["wall_s"] for s in per]) * 1e3
+    cpu = cpu_model()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD},
+            "extrapolated": {"value_from": "per-step sample times scaled to one energy: %d (R,tau) points x "
+                                          "median point time + %d LUs x LU time + G" % (16 * 16, 16 * 16),
+                             "s_per_energy": t, "ms_per_step_is": "measured wall time of one sample step",
+                             "t_point_s": statistics.median([s["t_point_s"] for s in per]),
+                             "t_lu_s": statistics.median([s["t_lu_s"] for s in per])},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": per[0]["cores"], "kind": "oracle",
-                             "sample": per[0]["sample"]},
+                             "sample": per[0]["sample"], "nproc": cpu["nproc"], "cpu_model": cpu["model"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_full(args):
+    """Whole energies by the oracle on the host cores: median of --steps runs with every core,
+    and one run with a single OpenMP thread (a child process, the thread count being fixed when
+    the OpenMP runtime starts)."""
+    from paper_2407_19930_gb300 import synthetic as syn
+    from oracle import grid as ogrid
+    if args.full == "cubic":
+        inp, ntau, name = syn.config_cubic(), 8, ("cubic cell: 2 atoms, 8 NAO / 24 ABF each, 2x2x2 k-mesh, "
+                                                  "8 tau/omega points")
+    else:
+        inp, ntau, name = syn.config_graphene(), 16, WORKLOAD
+    grid = ogrid.make_grid(ntau, *inp.delta_range)
+    if args.single_thread_child:
+        t, ec = oracle_full_energy(inp, grid)
+        print(json.dumps({"t": t, "ec": ec}), flush=True)
+        return 0
+    times, ecs = [], []
+    for _ in range(args.steps):
+        t, ec = oracle_full_energy(inp, grid)
+        times.append(t)
+        ecs.append(ec)
+    single = None
+    if args.single_thread:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--full", args.full,
+                            "--single-thread-child"], capture_output=True, text=True, env=env)
+        if r.returncode == 0:
+            single = json.loads(r.stdout.strip().splitlines()[-1])
+    t = statistics.median(times)
+    cpu = cpu_model()
+    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "none",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": name},
+            "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "whole energies, median of %d runs" % len(times),
+                             "nproc": cpu["nproc"], "cpu_model": cpu["model"], "runs_s": times,
+                             "single_thread_s": single["t"] if single else None},
+            "ec_ha": ecs[0]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -248,6 +390,9 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    peaks_run = None
+    if not args.no_peaks:
+        peaks_run = measure_fp64_peaks(torch.device("cuda", local))
     try:
         L.set_inputs(h, inp)
         for _ in range(args.warmup):
@@ -260,8 +405,6 @@ def run_gpu(args):
         except Exception:
             pass
         clocks = ClockSampler(uuid)
-        launches = 0
-        stats = []
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         barrier()
@@ -269,14 +412,13 @@ def run_gpu(args):
         ev0.record(stream)
         for _ in range(args.steps):
             L.librpa_gpu_chi0(h)
-            s1 = L.librpa_gpu_get_stats(h)
             ec, _, _ = L.librpa_gpu_ec(h)
-            s2 = L.librpa_gpu_get_stats(h)
-            launches += s2["launches"]
-            stats.append(s2)
         ev1.record(stream)
         barrier()
         clk = clocks.stop()
+        # counters of the last step (every step launches the same kernels), read after the timed region
+        stats = [L.librpa_gpu_get_stats(h)]
+        launches = stats[-1]["launches"] * args.steps
         t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, "cuda")
         value = job_value(args.steps, ws, t)
         # ---------------- end to end through host buffers
@@ -310,8 +452,14 @@ def run_gpu(args):
         return 0
     s = stats[-1]
     peaks, src = _peaks()
-    fp64_peak = peaks["bf16_tflops"] * NOMINAL_FP64_OVER_BF16 if src == "measured" else 1.9e3 * NOMINAL_FP64_OVER_BF16
-    fp64_peak_sus = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * NOMINAL_FP64_OVER_BF16
+    fp64_derived = peaks["bf16_tflops"] * NOMINAL_FP64_OVER_BF16
+    # the FP64 kernels' roofline: the FP64 tensor-path peak measured in this run (the same
+    # mma.sync m8n8k4 instruction as k_dgemm_nt; the derived value when the probes were skipped)
+    dmma = (peaks_run or {}).get("dmma_m8n8k4", {}).get("tflops")
+    fp64_peak = dmma if dmma else fp64_derived
+    fp64_src = ("measured in this run: DMMA m8n8k4 register probe (probe/peaks.cu), SM clock median %s MHz"
+                % ((peaks_run.get("clocks") or {}).get("sm_mhz") if peaks_run else None)) if dmma else \
+        "derived: %s BF16 dense burst x nominal FP64/BF16 (1.25/2250)" % src
     # dominant kernel by device time within the step
     kern = {"k_dgemm_nt": (s["ms_gemm_chi0"], s["flop_gemm_chi0"], s["n_gemm_chi0"], "paper_2407_19930_gb300/csrc/k_chi0.cu"),
             "k_zgemm": (s["ms_gemm_ec"], s["flop_gemm_ec"], s["n_gemm_ec"], "paper_2407_19930_gb300/csrc/k_zgemm.cu")}
@@ -341,11 +489,12 @@ def run_gpu(args):
         "ec_ha": ec,
         "roofline": {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp64_peak if achieved else None, "traffic": traffic,
-                     "peak_note": "FP64 MMA: %s BF16 dense burst peak x nominal FP64/BF16 (1.25/2250); "
-                                  "sustained-based peak %.3f" % (src, fp64_peak_sus),
+                     "peak_note": "FP64 tensor path, %s; derived from the BF16 peak: %.3f" % (fp64_src, fp64_derived),
                      "launches": nl, "flop": fl},
         "clocks": clk,
     }
+    if peaks_run:
+        line["peaks_measured"] = peaks_run
     if args.precision != "fp64":
         line["roofline"] = tc_roofline(s, peaks, src)
     if modes:
@@ -359,8 +508,10 @@ def run_gpu(args):
         from oracle import build as obuild, grid as ogrid
         obuild.build()
         cb = cpu_sample(inp, ogrid.make_grid(args.ntau, *inp.delta_range))
+        cpu = cpu_model()
         line["cpu_baseline"] = {"value": 1.0 / cb["t_energy_s"], "unit": UNIT, "cores": cb["cores"],
-                                "kind": "oracle", "sample": cb["sample"],
+                                "kind": "oracle", "sample": cb["sample"], "sample_s": cb["t_sample_s"],
+                                "nproc": cpu["nproc"], "cpu_model": cpu["model"],
                                 "chi0_tflops": s["flop_chi0"] / (args.ntau * st.nk) / cb["t_point_s"] / 1e12}
     print(json.dumps(line), flush=True)
     if dist:
@@ -630,6 +781,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--full", choices=["cubic", "graphene"], default=None,
+                    help="reference arm: whole oracle energies of this workload instead of the sample")
+    ap.add_argument("--single-thread", action="store_true", help="with --full: also one single-thread run")
+    ap.add_argument("--single-thread-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FP64/TF32 peak probes")
     # smaller variants of the same workload, for profiler captures only (not bench lines)
     ap.add_argument("--kmesh", default="4,4,1", help="k-mesh of the graphene slab (profiling variants)")
     ap.add_argument("--ntau", type=int, default=16)

@@ -95,6 +95,11 @@ typedef struct {
   int check_level;               /* 0 = none; 1 = check G is real and the pivots finite */
   int chi0_slices;               /* 0 = from precision; 1..5 = digit planes of the chi0 GEMMs */
   int ec_slices;                 /* 0 = from precision; 1..5 = digit planes of the ln det GEMMs */
+  int test_stall_gemms;          /* testing only (0 = off): the handle's first test_stall_gemms
+                                    tensor-core GEMM launches have every tile's MMA issuer wait
+                                    (100 us) on a barrier that nothing arrives at, so the bounded-wait
+                                    failure path runs: the call returns LIBRPA_E_TIMEOUT, later
+                                    calls of the handle run normally */
 } librpa_gpu_opts;
 
 /* Per-stage device times (ms, CUDA events on the handle's stream) and work counts of
@@ -125,13 +130,13 @@ typedef struct {
 } librpa_gpu_stats;
 
 /* Fill *o with defaults: device 0, own stream, cudaMalloc, n_tau = 16, FP64,
- * no budget, check_level 1. */
+ * no budget, check_level 1, no test stalls. */
 void librpa_gpu_default_opts(librpa_gpu_opts *o);
 
 /* Environment setup (paper: initialize_librpa_environment).  Creates a handle
  * bound to o->device.  *h is set to NULL on failure.
- * Errors: E_ARG (h or o NULL, bad device or n_tau < 1 or > 64, unknown precision),
- *         E_CUDA. */
+ * Errors: E_ARG (h or o NULL, bad device or n_tau < 1 or > 64, unknown precision,
+ *         test_stall_gemms < 0), E_CUDA. */
 int librpa_gpu_create(librpa_gpu_t *h, const librpa_gpu_opts *o);
 
 /* Structure and k-mesh (paper: set_dimension, set_latvec_and_G, set_kgrids_kvec_tot).
@@ -266,16 +271,21 @@ int librpa_gpu_ec(librpa_gpu_t h, double *ec, double *ec_q, double *ec_w);
  *   stream  cudaStream_t (NULL: the legacy default stream) of the current device, which
  *           must hold V, chi and out;
  *   msg     optional buffer of msg_len bytes for a one-line error description.
- * The caller owns every buffer; nothing is allocated, the library calls no cudaMalloc,
- * cudaFree or allocating routine.  The work is enqueued on `stream` and the call returns
- * without waiting: out is valid once the stream is synchronised.  Scratch is one static
- * device array of LIBRPA_NOALLOC_SCRATCH_BYTES, held on every GPU that loads the library
- * until the process exits, shared by all calls and keeping the last call's contents
- * (each call writes every scratch value before reading it): calls that overlap on the
- * GPU race, so order them on one stream or with events.  The first call made with a
- * given device current looks up the array's device address (set-up, once per device);
- * make that first call before any stream capture.
- * Errors: E_ARG (sizes, NULL or misaligned pointers; nomega = 0 is a no-op), E_CUDA. */
+ * The caller owns every buffer; the library calls no cudaMalloc, cudaFree or allocating
+ * routine.  The work is enqueued on `stream` and the call returns without waiting: out is
+ * valid once the stream is synchronised.  Scratch is one static device array of
+ * LIBRPA_NOALLOC_SCRATCH_BYTES, shared by all calls and keeping the last call's contents
+ * (each call writes every scratch value before reading it): calls that overlap on the GPU
+ * race, so order them on one stream or with events.
+ * Set-up: the first call made with a given device current looks up the array's device
+ * address, once per device.  With lazy module loading (the CUDA default) the device also
+ * creates the array at that moment, taking its 16 MiB of device memory, which it holds until
+ * the process exits (with CUDA_MODULE_LOADING=EAGER every GPU that loads the library holds it
+ * from the start).  So make the first call at start-up, before the caller's own memory pool
+ * claims the device and before any stream capture: a call with nomega = 0 does only this
+ * set-up (V, chi and out are then not used and may be NULL).
+ * Errors: E_ARG (sizes, NULL or misaligned pointers), E_NOMEM (the device had no memory left
+ * to create the array at set-up), E_CUDA. */
 #define LIBRPA_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 #define LIBRPA_NOALLOC_MAX_NAUX 591
 int librpa_gpu_ec_noalloc(int naux, int nomega, const double *V, const double *chi, double *out,

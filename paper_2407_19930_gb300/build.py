@@ -33,11 +33,12 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(SRC, "*.h")) + glob.glob(os.path.join(INC, "*.h"))
+    return (_sources() + glob.glob(os.path.join(SRC, "*.h")) + glob.glob(os.path.join(INC, "*.h")) +
+            [os.path.join(HERE, "probe", "peaks.cu")])
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(os.path.join(BUILD, "libpeaks.so")):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
@@ -73,7 +74,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    _build_probe(nvcc)
     return LIB
+
+
+PROBE_SRC = os.path.join(HERE, "probe", "peaks.cu")
+PROBE_LIB = os.path.join(BUILD, "libpeaks.so")
+
+
+def _build_probe(nvcc: str) -> str:
+    """The FP64 peak probes the benchmark measures its roofline against (a library of its own,
+    outside the C ABI)."""
+    cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PROBE_SRC, "-o", PROBE_LIB]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("compile failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

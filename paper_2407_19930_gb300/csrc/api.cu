@@ -245,7 +245,7 @@ int librpa_gpu_create(librpa_gpu_t *hp, const librpa_gpu_opts *o) {
   if (!hp || !o) return LIBRPA_E_ARG;
   *hp = nullptr;
   if (o->n_tau < 1 || o->n_tau > 64 || o->precision < LIBRPA_FP64 || o->precision > LIBRPA_TF32X3 ||
-      o->chi0_slices < 0 || o->chi0_slices > 5 || o->ec_slices < 0 || o->ec_slices > 5)
+      o->chi0_slices < 0 || o->chi0_slices > 5 || o->ec_slices < 0 || o->ec_slices > 5 || o->test_stall_gemms < 0)
     return LIBRPA_E_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -256,6 +256,7 @@ int librpa_gpu_create(librpa_gpu_t *hp, const librpa_gpu_opts *o) {
   librpa_gpu *h = new (std::nothrow) librpa_gpu();
   if (!h) return LIBRPA_E_NOMEM;
   h->opts = *o;
+  h->stalls_left = o->test_stall_gemms;
   {
     // arithmetic per stage (-1 = FP64 pipes, 0 = plain BF16, 1..5 = digit planes, 6 = plain
     // TF32, 7 = 3xTF32): presets, then explicit overrides
@@ -580,6 +581,7 @@ int librpa_gpu_ec(librpa_gpu_t h, double *ec, double *ec_q, double *ec_w) {
     h->stats.bytes_device_peak = h->bytes_peak;
     if (rc == LIBRPA_E_NOT_PD)
       return fail(h, rc, "ec: a Cholesky pivot was <= 0 (V(q) or 1 - V^1/2 chi0 V^1/2 not positive definite)");
+    if (rc == LIBRPA_E_TIMEOUT) return fail(h, rc, "ec: a bounded wait in the tensor-core GEMM ran out");
     return rc;
   });
 }

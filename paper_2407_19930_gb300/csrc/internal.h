@@ -157,6 +157,7 @@ struct Handle {
   DevBuf oz_args;     // descriptors of the tensor-core GEMM launches
   DevBuf work;        // per-call workspace
   double oz_exec_flops = 0;  // MMA flops issued by the last digit-plane GEMM launch
+  int stalls_left = 0;       // testing only: tensor-core GEMM launches still to take the failure path
   double flop_chi0_run = 0;  // algorithmic flops of the last contraction (screened work left out)
   bool chi0_done = false, lri_dirty = true;
   Chi0Plan plan;

@@ -15,7 +15,9 @@
 // Scratch: a file-scope __device__ array of LIBRPA_NOALLOC_SCRATCH_BYTES, split into slots of
 // 3 naux^2 complex values (L, T = chi L, A) per CTA.  Every value a CTA reads from its slot is
 // written earlier in the same call, so nothing needs clearing; the array keeps the last call's
-// contents.  All calls share it: calls that overlap on the GPU race.
+// contents.  All calls share it: calls that overlap on the GPU race.  The device creates the
+// array when it loads this file's module: with lazy module loading (the CUDA default) that is
+// the first call made with the device current, which therefore takes 16 MiB of device memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -72,12 +74,13 @@ __device__ double cta_cholesky(double2 *M, int n, double2 *col, double *s_piv) {
     }
     if (tid == 0) lsum += log(r);
     __syncthreads();
-    const int m = n - j - 1;
-    for (int e = tid; e < m * m; e += kThreads) {
-      const int ii = j + 1 + e / m, kk = j + 1 + e % m;
-      if (kk <= ii) {
+    // trailing update of the lower triangle only: one warp per row, lanes along the row
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int ii = j + 1 + warp; ii < n; ii += kThreads / 32) {
+      const double2 ci = col[ii];
+      for (int kk = j + 1 + lane; kk <= ii; kk += 32) {
         double2 &x = M[(size_t)ii * n + kk];
-        const double2 p = cmul_conj_b(col[ii], col[kk]);
+        const double2 p = cmul_conj_b(ci, col[kk]);
         x = make_double2(x.x - p.x, x.y - p.y);
       }
     }
@@ -211,8 +214,8 @@ extern "C" int librpa_gpu_ec_noalloc(int naux, int nomega, const double *V, cons
     return fail(msg, msg_len, LIBRPA_E_ARG, buf);
   }
   if (nomega < 0) return fail(msg, msg_len, LIBRPA_E_ARG, "librpa_gpu_ec_noalloc: nomega < 0");
-  if (nomega == 0) return LIBRPA_OK;
-  if (!V || !chi || !out) return fail(msg, msg_len, LIBRPA_E_ARG, "librpa_gpu_ec_noalloc: NULL V, chi or out");
+  if (nomega > 0 && (!V || !chi || !out))
+    return fail(msg, msg_len, LIBRPA_E_ARG, "librpa_gpu_ec_noalloc: NULL V, chi or out");
   if (((uintptr_t)V | (uintptr_t)chi) % 16 || (uintptr_t)out % 8)
     return fail(msg, msg_len, LIBRPA_E_ARG,
                 "librpa_gpu_ec_noalloc: V and chi must be 16-byte aligned, out 8-byte aligned");
@@ -222,17 +225,29 @@ extern "C" int librpa_gpu_ec_noalloc(int naux, int nomega, const double *V, cons
   if (dev < 0 || dev >= kMaxDevices) return fail(msg, msg_len, LIBRPA_E_ARG, "librpa_gpu_ec_noalloc: device index >= 64");
   void *base = nullptr;
   {
-    // set-up, once per device, on the first call made with that device current
+    // set-up, once per device, on the first call made with that device current.  Under lazy
+    // module loading (the CUDA default) this is also when the device creates the static array:
+    // its memory is taken here, so this lookup can fail for lack of device memory.
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch[dev]) {
       e = cudaGetSymbolAddress(&g_scratch[dev], noalloc_scratch);
       if (e != cudaSuccess) {
         g_scratch[dev] = nullptr;
+        if (e == cudaErrorMemoryAllocation) {
+          cudaGetLastError();
+          std::snprintf(buf, sizeof buf,
+                        "librpa_gpu_ec_noalloc: out of device memory while the device created the %d MiB "
+                        "static scratch array (first call on device %d); make the first call, e.g. with "
+                        "nomega = 0, before other code claims the device's memory",
+                        (int)(LIBRPA_NOALLOC_SCRATCH_BYTES >> 20), dev);
+          return fail(msg, msg_len, LIBRPA_E_NOMEM, buf);
+        }
         return fail_cuda(msg, msg_len, "cudaGetSymbolAddress(noalloc_scratch)", e);
       }
     }
     base = g_scratch[dev];
   }
+  if (nomega == 0) return LIBRPA_OK;   // set-up only
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return fail_cuda(msg, msg_len, "cudaDeviceGetAttribute", e);

@@ -251,12 +251,15 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// bounded wait: false after ~limit_ns
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+// bounded wait: false after ~limit_ns, or as soon as *abort is set (abort may be NULL: the
+// waits that drain a CTA's own copies and MMAs before it exits never give up early)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                          const volatile int *abort = nullptr) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (abort && *abort) return false;
     if (global_ns() - t0 > limit_ns) return false;
   }
 }
@@ -353,11 +356,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// stall_ns > 0 (testing only): the MMA issuer first waits that long on an mbarrier nothing
+// arrives at, so the tile takes the bounded-wait failure path.  On any failure the CTA sets
+// *err, stops issuing, waits (with the full limit) for the TMA copies and MMAs it has already
+// issued, frees its TMEM and returns.
 template <int S>
 __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
     k_ozgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              const Entry *__restrict__ entries, const Tile *__restrict__ tiles, const int *__restrict__ expoA,
-             const int *__restrict__ expoB, int *err) {
+             const int *__restrict__ expoB, int *err, uint64_t stall_ns) {
   constexpr bool TF = S == S_TF32 || S == S_TF32X3;   // kind::tf32
   constexpr bool PLAIN = S == 0 || TF;                 // one FP32 accumulator over all K
   constexpr int NP = S == S_TF32X3 ? 2 : PLAIN ? 1 : S;   // planes per operand
@@ -370,7 +377,7 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
   constexpr int EPI_WARPS = epi_warps(S), HALF = BN * 4 / EPI_WARPS;   // HALF: columns per epilogue warp
   constexpr uint32_t TMEM_COLS = tmem_cols<PLAIN ? 1 : NP>();
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t full[NST], empty[NST], tfull, tempty;
+  __shared__ uint64_t full[NST], empty[NST], tfull, tempty, mdone, never;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -386,6 +393,8 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
     }
     mbar_init(&tfull, 1);
     mbar_init(&tempty, EPI_WARPS);
+    mbar_init(&mdone, 1);
+    mbar_init(&never, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -406,9 +415,10 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
   const int quad = warp & 3, half = warp >> 2;   // epilogue: TMEM lane quadrant, column half
   if (warp == EPI_WARPS) {
     if (lane == 0) {
+      int issued = 0;
       for (int i = 0; i < nsteps; ++i) {
         const int st = i % NST;
-        if (abort_flag || !mbar_wait(&empty[st], ((i / NST) & 1) ^ 1, WAIT_NS)) {
+        if (abort_flag || !mbar_wait(&empty[st], ((i / NST) & 1) ^ 1, WAIT_NS, &abort_flag)) {
           abort_flag = 1;
           break;
         }
@@ -419,17 +429,26 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
         for (int p = 0; p < NP; ++p) tma_load_3d(sa + p * A_BYTES, &tmA, &full[st], k0, arow, p);
 #pragma unroll
         for (int p = 0; p < NP; ++p) tma_load_3d(sb + p * B_BYTES, &tmB, &full[st], k0, brow, p);
+        issued = i + 1;
       }
+      // after a failure: the copies of the last NST issued stages may still be in flight
+      // (earlier ones were consumed); wait for each to land before the CTA exits
+      if (abort_flag)
+        for (int i = issued > NST ? issued - NST : 0; i < issued; ++i) mbar_wait(&full[i % NST], (i / NST) & 1, WAIT_NS);
     }
   } else if (warp == EPI_WARPS + 1) {
     if (lane == 0) {
+      if (stall_ns) {   // testing only: a barrier nothing arrives at
+        mbar_wait(&never, 0, stall_ns, &abort_flag);
+        abort_flag = 1;
+      }
       for (int i = 0; i < nsteps; ++i) {
         const int st = i % NST, gi = i / G, c = i % G;
-        if (c == 0 && gi > 0 && (abort_flag || !mbar_wait(&tempty, (gi - 1) & 1, WAIT_NS))) {
+        if (c == 0 && gi > 0 && (abort_flag || !mbar_wait(&tempty, (gi - 1) & 1, WAIT_NS, &abort_flag))) {
           abort_flag = 1;
           break;
         }
-        if (abort_flag || !mbar_wait(&full[st], (i / NST) & 1, WAIT_NS)) {
+        if (abort_flag || !mbar_wait(&full[st], (i / NST) & 1, WAIT_NS, &abort_flag)) {
           abort_flag = 1;
           break;
         }
@@ -454,10 +473,16 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
         umma_commit(&empty[st]);
         if (c == G - 1 || i == nsteps - 1) umma_commit(&tfull);
       }
+      // after a failure: wait until every MMA this thread issued has completed (they read the
+      // shared-memory stages and write TMEM)
+      if (abort_flag) {
+        umma_commit(&mdone);
+        mbar_wait(&mdone, 0, WAIT_NS);
+      }
     }
   } else {
     for (int gi = 0; gi < ngroups; ++gi) {
-      bool ok = !abort_flag && mbar_wait(&tfull, gi & 1, WAIT_NS);
+      bool ok = !abort_flag && mbar_wait(&tfull, gi & 1, WAIT_NS, &abort_flag);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
         abort_flag = 1;
@@ -518,13 +543,7 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
     }
   }
   __syncthreads();
-  if (abort_flag) {
-    if (tid == 0) atomicExch(err, 1);
-    // let copies and MMAs already issued land before the CTA gives up its memory
-    if (tid == 0) {
-      for (int s = 0; s < NST; ++s) mbar_wait(&empty[s], 0, WAIT_NS / 8);
-    }
-  }
+  if (abort_flag && tid == 0) atomicExch(err, 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
@@ -550,10 +569,10 @@ CUtensorMap make_map(const Sliced &o, int box_rows) {
 
 template <int S>
 void launch(const CUtensorMap &ma, const CUtensorMap &mb, const Entry *e, const Tile *t, unsigned ntiles,
-            const int *ea, const int *eb, int *err, cudaStream_t s) {
+            const int *ea, const int *eb, int *err, uint64_t stall_ns, cudaStream_t s) {
   const int smem = NST * planes(S) * (BM + BN) * 64 + 1024;
   LR_CUDA(cudaFuncSetAttribute(k_ozgemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k_ozgemm<S><<<ntiles, 32 * (epi_warps(S) + 2), smem, s>>>(ma, mb, e, t, ea, eb, err);
+  k_ozgemm<S><<<ntiles, 32 * (epi_warps(S) + 2), smem, s>>>(ma, mb, e, t, ea, eb, err, stall_ns);
 }
 
 }  // namespace
@@ -645,15 +664,21 @@ long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry
   const Tile *dt = (const Tile *)((const char *)args.p + off2);
   const CUtensorMap ma = make_map(a, BM), mb = make_map(b, BN);
   const unsigned nt = (unsigned)tiles.size();
+  // testing only: the handle's first opts.test_stall_gemms launches take the failure path
+  uint64_t stall = 0;
+  if (h.stalls_left > 0) {
+    --h.stalls_left;
+    stall = 100000;   // 100 us per tile
+  }
   switch (a.S) {
-    case 0: launch<0>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
-    case 1: launch<1>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
-    case 2: launch<2>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
-    case 3: launch<3>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
-    case 4: launch<4>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
-    case S_TF32: launch<S_TF32>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
-    case S_TF32X3: launch<S_TF32X3>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
-    default: launch<5>(ma, mb, de, dt, nt, a.expo, b.expo, err, s); break;
+    case 0: launch<0>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
+    case 1: launch<1>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
+    case 2: launch<2>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
+    case 3: launch<3>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
+    case 4: launch<4>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
+    case S_TF32: launch<S_TF32>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
+    case S_TF32X3: launch<S_TF32X3>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
+    default: launch<5>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
   }
   ++launch_counter();
   LR_CUDA(cudaGetLastError());

@@ -45,7 +45,7 @@ class librpa_gpu_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("n_tau", ctypes.c_int),
                 ("precision", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("check_level", ctypes.c_int),
-                ("chi0_slices", ctypes.c_int), ("ec_slices", ctypes.c_int)]
+                ("chi0_slices", ctypes.c_int), ("ec_slices", ctypes.c_int), ("test_stall_gemms", ctypes.c_int)]
 
 
 class librpa_gpu_stats(ctypes.Structure):
