@@ -15,7 +15,7 @@ through the C ABI and E_c read back inside the timed region.
 Under torchrun (N > 1) every rank computes its own energy (independent
 requests, no collective on the data path): weak scaling, value = all ranks'
 energies / the slowest rank's time.  ``--impl reference`` times the CPU oracle
-(the paper's Algorithm 1 in plain C, OpenMP) on a bounded sample of the same
+(chi0 from the matrix form of Sec. 2 in plain C, OpenMP) on a bounded sample of the same
 workload.
 """
 import argparse
@@ -201,11 +201,11 @@ def cpu_model():
 
 
 def cpu_sample(inp, grid, budget_s=25.0):
-    """Time the oracle (Algorithm 1 in plain C with OpenMP, numpy LU) on a bounded
+    """Time the oracle (chi0 by the matrix form in plain C with OpenMP, numpy LU) on a bounded
     sample of the workload and extrapolate to one RPA energy."""
     import numpy as np
     from oracle import energy, green
-    from oracle.chi0_alg1 import chi0_alg1
+    from oracle.chi0_matrix import chi0_matrix_form
     st = inp.st
     ntau = len(grid["tau"])
     t0 = time.perf_counter()
@@ -216,7 +216,7 @@ def cpu_sample(inp, grid, budget_s=25.0):
     deadline = time.perf_counter() + budget_s
     for p in [(0, 0), (5, 0), (10, 0)]:
         t0 = time.perf_counter()
-        chi0_alg1(st, inp.lri, go, gv, [p])
+        chi0_matrix_form(st, inp.lri, go, gv, [p])
         t_pt.append(time.perf_counter() - t0)
         pts.append(p)
         if time.perf_counter() > deadline:
@@ -234,12 +234,12 @@ def cpu_sample(inp, grid, budget_s=25.0):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"t_energy_s": t_energy, "t_point_s": tp, "t_lu_s": t_lu, "t_green_s": t_green, "cores": cores,
             "t_sample_s": sum(t_pt) + t_lu + t_green / ntau,
-            "sample": "chi0(R,tau) by Algorithm 1 on %d of %d (R,tau) points, ln det by LU on 1 of %d (q,omega), "
+            "sample": "chi0(R,tau) by the oracle's matrix form on %d of %d (R,tau) points, ln det by LU on 1 of %d (q,omega), "
                       "G on 1 of %d tau; extrapolated to one energy" % (len(pts), npts, st.nk * ntau, ntau)}
 
 
 def oracle_full_energy(inp, grid):
-    """Seconds of one whole RPA energy by the oracle (G, Algorithm 1 at every (R, tau) point, the
+    """Seconds of one whole RPA energy by the oracle (G, chi0 at every (R, tau) point, the
     transforms, LU of every (q, omega)); returns (seconds, E_c)."""
     from oracle import pipeline
     t0 = time.perf_counter()
@@ -274,7 +274,7 @@ def dist_init():
 
 def run_reference(args):
     """The oracle as the reference arm.  Each step is a bounded sample of one energy of the
-    workload (Algorithm 1 at one (R, tau) point, one LU of a (q, omega) matrix, G at one tau);
+    workload (chi0 at one (R, tau) point, one LU of a (q, omega) matrix, G at one tau);
     ms_per_step is the measured wall time of that sample, and value is one energy's time
     extrapolated from the sample (stated in the "extrapolated" key).  With --full NAME the whole
     energy of a workload runs instead, median of --steps runs plus one single-thread run."""

@@ -6,8 +6,9 @@ the paper's equations (arXiv:2407.19930, Sec. 2):
 * ``green``      -- Eq. green_mat: G^occ / G^vir (R, tau) from KS eigen-data;
 * ``chi0_definition`` -- Eqs. LRI + chi0_NAOs + chi0_ABFs written out with
   dense neighbourhood matrices (the plain definition of chi0_{mu nu}(R, tau));
-* ``chi0_alg1``  -- Algorithm 1 loop by loop (X, N, M, Z, O, chi += C O),
-  plain C with OpenMP over (R, tau); also the timed CPU baseline;
+* ``chi0_matrix`` -- the four-term matrix form of chi0_{mu nu}(R, tau) of Sec. 2
+  (the equation combining Eqs. chi0_NAOs, chi0_ABFs and LRI), term by term in
+  plain C with OpenMP over (point, atom pair); also the timed CPU baseline;
 * ``chi0_sos``   -- an independent sum-over-states form in k space, used to
   pin the two routes above (exact in tau; Lorentzian in i omega);
 * ``freq``       -- the tau -> i omega cosine transform and R -> q Fourier

@@ -1,4 +1,4 @@
-"""Build the oracle's C part (Algorithm 1 loops) into oracle/_build/.
+"""Build the oracle's C part (chi0 from the matrix form of Sec. 2) into oracle/_build/.
 
 Test infrastructure only.  Plain gcc, OpenMP, no GPU code.
 """
@@ -9,11 +9,11 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(BUILD, "liboracle_alg1.so")
+LIB = os.path.join(BUILD, "liboracle_chi0.so")
 
 
 def build(force: bool = False) -> str:
-    src = os.path.join(HERE, "alg1.c")
+    src = os.path.join(HERE, "chi0_matrix.c")
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(src):
         return LIB
     os.makedirs(BUILD, exist_ok=True)

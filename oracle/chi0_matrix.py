@@ -1,4 +1,5 @@
-"""Oracle: Python entry to the plain-C Algorithm 1 (``alg1.c``).
+"""Oracle: Python entry to the plain-C evaluation of chi0(R, tau) from the four-term matrix form of
+Sec. 2 (``chi0_matrix.c``).
 
 Test infrastructure only (see the package docstring).
 """
@@ -17,7 +18,7 @@ def _load():
     global _lib
     if _lib is None:
         _lib = ctypes.CDLL(_build.build())
-        _lib.oracle_chi0_alg1.restype = ctypes.c_int
+        _lib.oracle_chi0_matrix.restype = ctypes.c_int
     return _lib
 
 
@@ -36,7 +37,7 @@ def pack_lri(lri):
     return blk_I, blk_K, blk_R, blk_off, C
 
 
-def chi0_alg1(st, lri, go, gv, points, pairs=None, spin=2.0, out=None):
+def chi0_matrix_form(st, lri, go, gv, points, pairs=None, spin=2.0, out=None):
     """chi0(R, tau) [len(points)][N_aux][N_aux] for (iR, itau) points.
 
     ``pairs``: optional list of (U, V) atom pairs; only those blocks are
@@ -60,7 +61,7 @@ def chi0_alg1(st, lri, go, gv, points, pairs=None, spin=2.0, out=None):
     else:
         pr = np.ascontiguousarray(np.array(pairs, dtype=np.int32).reshape(-1))
         npairs = len(pr) // 2
-    rc = lib.oracle_chi0_alg1(
+    rc = lib.oracle_chi0_matrix(
         ctypes.c_int(st.natoms), _ptr(n_ao, ctypes.c_int), _ptr(n_aux, ctypes.c_int),
         _ptr(kmesh, ctypes.c_int), ctypes.c_int(len(lri)), _ptr(blk_I, ctypes.c_int),
         _ptr(blk_K, ctypes.c_int), _ptr(blk_R, ctypes.c_int), _ptr(blk_off, ctypes.c_long),
@@ -69,5 +70,5 @@ def chi0_alg1(st, lri, go, gv, points, pairs=None, spin=2.0, out=None):
         _ptr(pts, ctypes.c_int), ctypes.c_int(npairs), _ptr(pr, ctypes.c_int),
         _ptr(out, ctypes.c_double))
     if rc != 0:
-        raise RuntimeError("oracle_chi0_alg1 failed: %d" % rc)
+        raise RuntimeError("oracle_chi0_matrix failed: %d" % rc)
     return out

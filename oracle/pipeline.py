@@ -2,7 +2,7 @@
 
 Test infrastructure only (see the package docstring).
 
-G (Eq. green_mat) -> chi0(R, tau) (Algorithm 1, or the plain definition)
+G (Eq. green_mat) -> chi0(R, tau) (the four-term matrix form, or the plain definition)
 -> chi0(R, i omega) (cosine transform) -> chi0(q, i omega) (Fourier
 transform) -> E_c (ln det by LU, quadrature over omega, mean over q).  With a screening
 threshold the Green's functions pass through ``screen.screen_blocks`` first
@@ -13,7 +13,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import energy, freq, green, screen as _screen
-from .chi0_alg1 import chi0_alg1
+from .chi0_matrix import chi0_matrix_form
 from .chi0_definition import chi0_definition
 
 
@@ -38,7 +38,7 @@ def greens(inp, grid, screen=0.0):
     return gs
 
 
-def chi0_tau(inp, grid, route="alg1", go=None, gv=None):
+def chi0_tau(inp, grid, route="matrix", go=None, gv=None):
     """chi0(R, tau) as [ntau][nR][N][N]: the contraction of each spin channel with its own
     Green's functions, summed.  go / gv: one channel's arrays, or [nspins] of them."""
     st = inp.st
@@ -51,8 +51,8 @@ def chi0_tau(inp, grid, route="alg1", go=None, gv=None):
     s = spin_factor(st.nspins)
     c = 0.0
     for g_o, g_v in gs:
-        if route == "alg1":
-            c = c + chi0_alg1(st, inp.lri, g_o, g_v, pts, spin=s)
+        if route == "matrix":
+            c = c + chi0_matrix_form(st, inp.lri, g_o, g_v, pts, spin=s)
         elif route == "definition":
             c = c + chi0_definition(st, inp.lri, g_o, g_v, pts, spin=s)
         else:
@@ -70,7 +70,7 @@ def chi0_q_omega(inp, grid, chi_tau):
     return out
 
 
-def rpa_energy(inp, grid, route="alg1", vq=None, screen=0.0):
+def rpa_energy(inp, grid, route="matrix", vq=None, screen=0.0):
     """Dict with G ([nspins] leading axis when nspins = 2; screened when ``screen`` > 0),
     chi0 in every representation and E_c (Ha per cell)."""
     st = inp.st

@@ -9,7 +9,7 @@ block G^occ_{IJ}(R, tau) is dropped (replaced by zeros) when the largest
 absolute value of its elements is below the threshold theta, and kept
 unchanged otherwise; G^vir is screened the same way on its own blocks.  The
 threshold is absolute (G is dimensionless).  theta = 0 keeps every block.
-Algorithm 1 then runs on the screened Green's functions unchanged: a term whose
+chi0 then runs on the screened Green's functions unchanged: a term whose
 G block was dropped contributes nothing, so the cost follows the number of
 kept blocks, and lattice vectors R whose G blocks are all dropped drop out of
 chi0 altogether (the R range limited by the decay of G).

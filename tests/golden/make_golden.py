@@ -1,5 +1,5 @@
 """Writes ``oracle_energies.json``: E_c (Ha per cell) with its per-q and per-omega parts, computed
-by the CPU oracle alone (``oracle.pipeline.rpa_energy``, Algorithm 1 route) on seeded synthetic
+by the CPU oracle alone (``oracle.pipeline.rpa_energy``, matrix-form route of chi0) on seeded synthetic
 requests, without and with Green's-function screening.  Run from the repository root:
 
     python tests/golden/make_golden.py

@@ -1,8 +1,8 @@
 """The benchmark's workload shape at its full auxiliary size, end to end against the oracle.
 
 The graphene slab (35 atoms: 32 C + a water-shaped molecule; n_ao 431, N_aux 2010) with the
-k-mesh cut to 1x1x1 and 2x2x1 and 8 tau/omega points, so that the oracle (Algorithm 1 in plain
-C, LU of 1 - chi0 V) finishes in about a minute.  Every chi0(q, i omega) element, E_c and its
+k-mesh cut to 1x1x1 and 2x2x1 and 8 tau/omega points, so that the oracle (the matrix form of chi0 in
+plain C, LU of 1 - chi0 V) finishes in about a minute.  Every chi0(q, i omega) element, E_c and its
 per-q and per-omega parts are compared: the N_aux = 2010 matrices run the ln det stage's 32-panel
 tile loops, its workspace chunking and the chi0 contraction's full atom-pair tables, which the
 small parity cases do not reach.

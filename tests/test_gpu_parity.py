@@ -14,7 +14,7 @@ from paper_2407_19930_gb300 import librpa_gpu as L
 from paper_2407_19930_gb300 import synthetic as syn
 from oracle import grid as ogrid, pipeline
 from oracle import green as ogreen
-from oracle.chi0_alg1 import chi0_alg1
+from oracle.chi0_matrix import chi0_matrix_form
 
 pytestmark = pytest.mark.gpu
 
@@ -400,7 +400,7 @@ def test_hbm_budget():
 def test_graphene_full_size_sampled():
     """The 35-atom graphene + water slab (N_aux = 2010, 4x4x1 k, 16 tau points) in the
     configuration the benchmark times: sampled chi0(R, tau) blocks against the oracle's
-    Algorithm 1, and properties that hold at any size for the rest."""
+    the oracle's matrix form of chi0, and properties that hold at any size for the rest."""
     inp = syn.config_graphene()
     st = inp.st
     grid = ogrid.make_grid(16, *inp.delta_range)
@@ -418,7 +418,7 @@ def test_graphene_full_size_sampled():
     finally:
         L.librpa_gpu_destroy(h)
     go, gv = ogreen.green(st.kmesh, inp.kfrac, inp.eig, inp.occ, inp.wfc, inp.efermi, grid["tau"])
-    ref = chi0_alg1(st, inp.lri, go, gv, samples, pairs=pairs)
+    ref = chi0_matrix_form(st, inp.lri, go, gv, samples, pairs=pairs)
     ao = np.concatenate([[0], np.cumsum(st.n_aux)])
     for p, (iR, it) in enumerate(samples):
         scale = np.abs(chis[(iR, it)]).max()

@@ -13,7 +13,7 @@ import pytest
 
 from paper_2407_19930_gb300 import synthetic as syn
 from oracle import energy, freq, green, grid as ogrid, pipeline, screen
-from oracle.chi0_alg1 import chi0_alg1
+from oracle.chi0_matrix import chi0_matrix_form
 from oracle.chi0_definition import chi0_definition
 from oracle.chi0_sos import chi0_sos
 
@@ -86,14 +86,14 @@ def test_green_matches_bvk_supercell(cubic):
 
 @pytest.mark.parametrize("name", ["tiny", "cubic"])
 def test_three_routes_agree_in_tau(name, request):
-    """Algorithm 1 == plain definition (R space) and == sum over states (q space),
+    """Four-term matrix form == plain definition (R space) and == sum over states (q space),
     an algebraic identity with no grid error."""
     inp = request.getfixturevalue(name)
     st = inp.st
     tau = np.array([0.25, 1.3])
     go, gv = _green(inp, tau)
     pts = [(iR, it) for it in range(len(tau)) for iR in range(st.nk)]
-    ca = chi0_alg1(st, inp.lri, go, gv, pts)
+    ca = chi0_matrix_form(st, inp.lri, go, gv, pts)
     cd = chi0_definition(st, inp.lri, go, gv, pts)
     scale = np.abs(ca).max()
     assert scale > 1.0
@@ -338,7 +338,7 @@ def test_spin_identical_channels_equal_unpolarised():
 
 
 def test_spin_routes_agree_in_tau():
-    """Polarised channels (one more occupied band spin up): Algorithm 1 on each channel's Green's
+    """Polarised channels (one more occupied band spin up): the matrix form on each channel's Green's
     functions, summed with s = 1, equals the sum over states of both channels in q space."""
     inp = syn.config_spin()
     st = inp.st

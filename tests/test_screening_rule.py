@@ -4,7 +4,7 @@ The library leaves out the (R, tau) points where one of G^occ, G^vir has no kept
 the blocks the contraction reads there (N-step: (L, K) at R1 - R - R2 for (L, R2) in N[V] and
 (K, R1) in the union of the neighbour lists; X-step: (I, L) at R + R2; O assembly: (U, V) at R
 and (V, K) at R1 - R), because every term of chi0 pairs a G^occ with a G^vir factor.  Here the
-same rule, restated in Python, must only leave out points where the oracle's Algorithm 1 on the
+same rule, restated in Python, must only leave out points where the oracle's chi0 (matrix form) on the
 screened G gives exactly zero, and must leave some out.  With the on-site block C[V, V, 0] in
 N[V] the O-assembly sets are inside the X- and N-step sets; the rule keeps them for neighbour
 lists without it.  Dropping the X- or the N-step set from the rule fails the single-block test.
@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import grid as ogrid, pipeline, screen
-from oracle.chi0_alg1 import chi0_alg1
+from oracle.chi0_matrix import chi0_matrix_form
 from paper_2407_19930_gb300 import synthetic as syn
 
 
@@ -57,7 +57,7 @@ def test_left_out_points_have_zero_chi0(name, theta):
     cells = [(a, b, c) for a in range(n1) for b in range(n2) for c in range(n3)]
     ntau = len(grid["tau"])
     pts = [(iR, it) for it in range(ntau) for iR in range(st.nk)]
-    chi = chi0_alg1(st, inp.lri, go, gv, pts).reshape(ntau, st.nk, st.naux, st.naux)
+    chi = chi0_matrix_form(st, inp.lri, go, gv, pts).reshape(ntau, st.nk, st.naux, st.naux)
     left_out = 0
     for it in range(ntau):
         for iR, R in enumerate(cells):
@@ -71,7 +71,7 @@ def test_left_out_points_have_zero_chi0(name, theta):
 @pytest.mark.parametrize("g_single", ["occ", "vir"])
 def test_every_block_that_reaches_chi0_is_read(g_single):
     """Completeness of the rule, one block at a time: with a single atom-pair block of one Green's
-    function kept (the other Green's function whole), every point where Algorithm 1 gives a
+    function kept (the other Green's function whole), every point where the oracle's chi0 gives a
     non-zero chi0 must be one the rule keeps.  Run over every block of a 2-atom cell on a 9x1x1
     mesh, long enough that the N-step blocks (near -R) and the X-step blocks (near +R) are the
     only route for some block and point."""
@@ -99,7 +99,7 @@ def test_every_block_that_reaches_chi0_is_read(g_single):
                 mask = np.zeros((st.nk, st.natoms, st.natoms), dtype=bool)
                 mask[iRb, I, J] = True
                 g_o, g_v = (single, gv) if g_single == "occ" else (go, single)
-                chi = chi0_alg1(st, inp.lri, g_o, g_v, pts).reshape(st.nk, st.naux, st.naux)
+                chi = chi0_matrix_form(st, inp.lri, g_o, g_v, pts).reshape(st.nk, st.naux, st.naux)
                 for iR, R in enumerate(cells):
                     if np.any(chi[iR] != 0.0):
                         reached += 1
