@@ -49,15 +49,13 @@ PRECISIONS = {"fp64": (0, "f64"), "fp64_tc": (1, "f64-accurate: bf16 digit plane
               "tf32x3": (5, "mixed: chi0 GEMMs as 3xtf32 split products (fp32 accumulation), ln det on 5 digit planes")}
 MEV_PER_HA = 27211.386245988
 
-# DRAM traffic per launch of the dominant kernels from one ncu capture (see profiles/),
-# valid only while the kernel source is unchanged (sha256 of the file at capture time).
+# DRAM traffic per launch of the dominant kernels from one ncu capture (see profiles/), valid only
+# while the kernel's source text is unchanged (sha256 of the text between the markers at capture time).
 TRAFFIC = {
-    # 98 launches of one FP64 step of the graphene workload (16 G-build GEMMs, the ln det GEMMs and
-    # Cholesky trailing updates): 92.5 GB read + 65.0 GB written (profiles/k_zgemm_dram_graphene_fp64.md)
-    "k_zgemm": {"bytes_per_launch": 1.6075e9, "src_sha": "02ef5086221f2c12"},
-    # 330 launches of one FP64 step (N/X-step and final-contraction groups, 160 batches each, plus
-    # the tile tuner's first pass): 229.7 GB read + 84.8 GB written (profiles/k_dgemm_nt_dram_graphene_fp64.md)
-    "k_dgemm_nt": {"bytes_per_launch": 0.953e9, "src_sha": "613c2603be84cf54"},
+    # Gamma case of the graphene slab, one (R, tau) point per launch as at 4x4x1: N/X group 0.681 GB,
+    # final contraction 1.225 GB, averaged (profiles/k_dgemm_nt_dram_graphene_gamma.md)
+    "k_dgemm_nt": {"bytes_per_launch": 0.953e9, "src": "paper_2407_19930_gb300/csrc/k_chi0.cu",
+                   "begin": "template <int WM, int WN>", "end": "// tile variants {WM, WN}", "src_sha": "d413a0b3da389a16"},
 }
 
 
@@ -70,9 +68,14 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def _src_sha(path):
+def _src_sha(path, begin=None, end=None):
+    """sha256 (16 hex digits) of a source file, or of its text from `begin` up to `end`."""
     with open(os.path.join(ROOT, path), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+        b = f.read()
+    if begin:
+        i = b.index(begin.encode())
+        b = b[i:b.index(end.encode(), i)]
+    return hashlib.sha256(b).hexdigest()[:16]
 
 
 class ClockSampler:
@@ -467,7 +470,7 @@ def run_gpu(args):
     ms, fl, nl, srcf = kern[name]
     achieved = fl / (ms * 1e-3) / 1e12 if ms > 0 else None
     tr = TRAFFIC.get(name)
-    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _src_sha(srcf) else None
+    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _src_sha(tr["src"], tr["begin"], tr["end"]) else None
     step_ms = t / args.steps * 1e3 * ws / ws
     chi0_tflops = s["flop_chi0"] / (s["ms_chi0"] * 1e-3) / 1e12
     line = {
@@ -501,9 +504,19 @@ def run_gpu(args):
         line["modes"] = modes
     if ws == 1 and args.serve_sample > 0:
         torch.cuda.empty_cache()   # the headline's blocks cached by torch go back to the device
-        m = serve_measure(L, _serve_inputs(args.serve_sample), args.rate, args.slots, args.ntau, local)
-        line["serving"] = {k: m[k] for k in ("value", "unit", "workload", "slots", "latency_ms", "completed",
-                                             "failed", "errors", "peak_running")}
+        reqs = _serve_inputs(args.serve_sample)
+        sweep = []
+        for rate in [float(x) for x in args.serve_rates.split(",") if x]:
+            m = serve_measure(L, reqs, rate, args.slots, args.ntau, local)
+            sweep.append({"rate_req_per_s": rate, "value": m["value"], "unit": UNIT, "latency_ms": m["latency_ms"],
+                          "completed": m["completed"], "failed": m["failed"], "peak_running": m["peak_running"],
+                          "seconds": m["seconds"], "errors": m["errors"]})
+        sizes = [inp.st.natoms for inp in reqs]
+        line["serving"] = {"workload": "%d requests per arrival rate, Poisson arrivals, random cells of %d-%d atoms "
+                                       "(5/9/13 NAO, 20/40/60 ABF), k-mesh 1x1x1..3x3x1, %d tau; precision per "
+                                       "request alternating fp64_tc / split"
+                                       % (len(reqs), min(sizes), max(sizes), args.ntau),
+                           "slots": args.slots, "sweep": sweep}
     if ws == 1 and not args.no_cpu:
         from oracle import build as obuild, grid as ogrid
         obuild.build()
@@ -795,8 +808,10 @@ def main():
     ap.add_argument("--batch", action="store_true", help="batched workload instead of the headline")
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=16)
-    ap.add_argument("--serve-sample", type=int, default=8,
-                    help="requests of the serving sample added to the headline line (0: none)")
+    ap.add_argument("--serve-sample", type=int, default=12,
+                    help="requests per arrival rate of the serving sweep added to the headline line (0: none)")
+    ap.add_argument("--serve-rates", default="5,20,50,200",
+                    help="arrival rates (req/s) of the serving sweep in the headline line")
     ap.add_argument("--rate", type=float, default=20.0, help="request arrival rate (Poisson), per second")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--modes", default="fp64_tc,split,tf32x3,tf32,bf16,fp64@1e-3,fp64_tc@1e-3",

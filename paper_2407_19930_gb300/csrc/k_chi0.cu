@@ -32,6 +32,28 @@
 namespace librpa {
 namespace {
 
+// a 2^sh as FP64, rounded to nearest even, by integer instructions (zero and results outside the
+// normal range through FP64)
+__device__ __forceinline__ double librpa_i64_to_f64(long long a, int sh) {
+  if (a == 0) return 0.0;
+  const unsigned long long neg = a < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  const int lz = __clzll((long long)m);
+  m <<= lz;
+  unsigned long long mant = m >> 11;
+  const unsigned rem = (unsigned)(m & 0x7FFull);
+  int e = 1086 - lz + sh;
+  if (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++e;
+    }
+  }
+  if (e <= 0 || e >= 2047) return ldexp((double)a, sh);
+  return __longlong_as_double((long long)(neg | ((unsigned long long)e << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
 // ---------------------------------------------------------------------------------------
 // batched FP64 "NT" GEMM on the tensor cores: C[m][n] = alpha sum_k A[m][k] B[n][k] + beta C
 struct DGemm {
@@ -237,7 +259,24 @@ struct ArDF {
     const float h = __double2float_rn(v);
     return make_float2(h, __double2float_rn(v - (double)h));
   }
-  __device__ static double to(T v) { return (double)v.x + (double)v.y; }
+  // x + y in FP64 by integer instructions (the FP64 pipe of GB300 runs at ~1/64 of the FP32 rate):
+  // both significands on the larger exponent's scale in an int64 (the smaller one truncated when it
+  // lies more than 38 binades lower: a relative error below 2^-61), then one rounding to FP64
+  __device__ static double to(T v) {
+    const unsigned bx = __float_as_uint(v.x), by = __float_as_uint(v.y);
+    const int ex = (int)((bx >> 23) & 0xFF), ey = (int)((by >> 23) & 0xFF);
+    if (ex == 0 || ey == 0 || ex == 255 || ey == 255) return (double)v.x + (double)v.y;   // zero, subnormal, inf
+    long long mx = (long long)((bx & 0x7FFFFFu) | 0x800000u), my = (long long)((by & 0x7FFFFFu) | 0x800000u);
+    if (bx >> 31) mx = -mx;
+    if (by >> 31) my = -my;
+    long long a, b;   // a: the operand with the larger exponent
+    int ea, d;
+    if (ex >= ey) { a = mx; b = my; ea = ex; d = ex - ey; } else { a = my; b = mx; ea = ey; d = ey - ex; }
+    const int up = d < 38 ? d : 38;   // a << up keeps 24 + 38 < 63 bits
+    const long long sum = (a << up) + (d - up < 63 ? (b >> (d - up)) : (b < 0 ? -1 : 0));
+    // value = sum 2^(ea - 127 - 23 - up)
+    return librpa_i64_to_f64(sum, ea - 150 - up);
+  }
   __device__ static T zero() { return make_float2(0.f, 0.f); }
   // N and X arrive from their GEMMs already as (hi, lo) pairs in 8-byte slots
   __device__ static T load(const double *p) { return *reinterpret_cast<const float2 *>(p); }

@@ -11,6 +11,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -320,6 +322,92 @@ struct Tile {
   int e, m0, n0;
 };
 
+// ------------------------------------------------------------------ epilogue conversions
+// The FP64 pipe of GB300 runs at about 1/64 of its FP32 rate, so the epilogue builds its FP64 (and
+// FP32-pair) outputs from the exact int64 digit sums with integer instructions: normalise by the
+// leading-one position, round to nearest even, and put the scale 2^sh into the exponent field.
+// Results outside the normal range take the FP64 route (rare).
+
+// a 2^sh as FP64, rounded to nearest even
+__device__ __forceinline__ double i64_to_f64(long long a, int sh) {
+  if (a == 0) return 0.0;
+  const unsigned long long neg = a < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  const int lz = __clzll((long long)m);
+  m <<= lz;                                    // leading one at bit 63
+  unsigned long long mant = m >> 11;           // 53 significant bits
+  const unsigned rem = (unsigned)(m & 0x7FFull);
+  int e = 1086 - lz + sh;                      // biased exponent: 1023 + (63 - lz) + sh
+  if (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++e;
+    }
+  }
+  if (e <= 0 || e >= 2047) return ldexp((double)a, sh);
+  return __longlong_as_double((long long)(neg | ((unsigned long long)e << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// u 2^sh as FP32 (u < 2^63), rounded to nearest even; *ok = false outside the normal range
+__device__ __forceinline__ float u64_to_f32(unsigned long long u, int sh, bool *ok) {
+  if (u == 0) return 0.f;
+  const int lz = __clzll((long long)u);
+  u <<= lz;
+  unsigned mant = (unsigned)(u >> 40);         // 24 significant bits
+  const unsigned long long rem = u & 0xFFFFFFFFFFull;
+  int e = 190 - lz + sh;                       // biased exponent: 127 + (63 - lz) + sh
+  if (rem > 0x8000000000ull || (rem == 0x8000000000ull && (mant & 1u))) {
+    ++mant;
+    if (mant >> 24) {
+      mant >>= 1;
+      ++e;
+    }
+  }
+  if (e <= 0 || e >= 255) {
+    *ok = false;
+    return 0.f;
+  }
+  return __uint_as_float(((unsigned)e << 23) | (mant & 0x7FFFFFu));
+}
+
+// a 2^sh as an unevaluated pair of FP32 numbers (hi, lo): hi = the value rounded to 24 bits, lo =
+// the remainder rounded to 24 bits (about 48 significant bits)
+__device__ __forceinline__ float2 i64_to_f32x2(long long a, int sh) {
+  if (a == 0) return make_float2(0.f, 0.f);
+  const bool neg = a < 0;
+  unsigned long long m = neg ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  const int lz = __clzll((long long)m);
+  m <<= lz;                                    // leading one at bit 63; value = m 2^(sh - lz)
+  unsigned long long hm = m >> 40;
+  long long r = (long long)(m & 0xFFFFFFFFFFull);
+  if (r > 0x8000000000ll || (r == 0x8000000000ll && (hm & 1ull))) {
+    ++hm;
+    r -= 0x10000000000ll;                      // the remainder of the rounded-up hi is negative
+  }
+  bool ok = true;
+  float hi = u64_to_f32(hm, sh - lz + 40, &ok);   // hm <= 2^24: exact
+  float lo = u64_to_f32((unsigned long long)(r < 0 ? -r : r), sh - lz, &ok);
+  if (!ok) {   // outside the FP32 normal range: through FP64
+    const double v = ldexp((double)a, sh);
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+  }
+  if (r < 0) lo = -lo;
+  return neg ? make_float2(-hi, -lo) : make_float2(hi, lo);
+}
+
+// f 2^sh as FP64 (exact), integer instructions; zero, subnormal and non-finite f through FP64
+__device__ __forceinline__ double f32_to_f64(float f, int sh) {
+  const unsigned b = __float_as_uint(f);
+  const int e = (int)((b >> 23) & 0xFF);
+  if (e == 0 || e == 255) return ldexp((double)f, sh);
+  const int ed = e - 127 + 1023 + sh;
+  if (ed <= 0 || ed >= 2047) return ldexp((double)f, sh);
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | ((unsigned long long)ed << 52) |
+                                          ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
 template <int S>
 __host__ __device__ constexpr uint32_t tmem_cols() {
   return S * BN <= 64 ? 64 : S * BN <= 128 ? 128 : S * BN <= 256 ? 256 : 512;
@@ -508,36 +596,84 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
       }
     }
     if (!failed) {
-      const int row = m0 + 32 * quad + lane;
-      const int ea = (!PLAIN && row < en.M) ? expoA[en.a_row0 + row] : 0;
+      // Values are formed with thread = tile row (the TMEM lane layout).  Row-major outputs
+      // (modes 0, 1, 3) go through a per-warp staging area in shared memory (the pipeline's stages,
+      // idle once the last MMA completed) and are written with lane = column, so that each warp
+      // store covers consecutive addresses; the transposed complex output (mode 2) is already
+      // consecutive along rows and is stored directly.
+      const int rl = 32 * quad + lane, row = m0 + rl;
+      const bool row_ok = row < en.M;
+      const int ea = (!PLAIN && row_ok) ? expoA[en.a_row0 + row] : 0;
+      const int cbase = n0 + half * HALF;
+      const bool pow2 = en.alpha_shift != kNoShift;   // alpha = +-2^alpha_shift: folded into the exponent
+      const int ash = pow2 ? en.alpha_shift : 0;
+      const bool aneg = pow2 && en.alpha < 0.0;
+      const bool staged = en.mode != 2;
+      constexpr int PITCH = HALF + 1;
+      double *stg = reinterpret_cast<double *>(smem) + (size_t)warp * 32 * PITCH;
 #pragma unroll
       for (int cb = 0; cb < HALF / 16; ++cb) {
         uint32_t r[16];
         if constexpr (PLAIN) tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + half * HALF + cb * 16, r);
-        if (row >= en.M) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int col = n0 + half * HALF + cb * 16 + j;
-          if (col >= en.N) break;
-          double v;
-          if constexpr (PLAIN)
-            v = nsteps > 0 ? en.alpha * (double)__uint_as_float(r[j]) : 0.0;
-          else
-            v = en.alpha * ldexp((double)acc[cb * 16 + j], ea + expoB[en.b_row0 + col] - 14 - 8 * (S - 1));
-          double *p;
-          if (en.mode == 3) {   // real, as an unevaluated pair of FP32 numbers (hi, lo)
-            const float hi = __double2float_rn(v);
-            reinterpret_cast<float2 *>(en.C)[(long long)row * en.ldc + col] =
-                make_float2(hi, __double2float_rn(v - (double)hi));
-            continue;
+          const int c = cb * 16 + j, col = cbase + c;
+          const bool ok = row_ok && col < en.N;
+          double v = 0.0;
+          float2 pr = make_float2(0.f, 0.f);
+          if (ok) {
+            if constexpr (PLAIN) {
+              if (nsteps > 0) v = f32_to_f64(__uint_as_float(r[j]), ash);
+              if (aneg) v = -v;
+              if (!pow2) v *= en.alpha;
+              if (en.mode == 3) {
+                pr.x = __double2float_rn(v);   // exact: a rounded FP32 sum times +-1
+                pr.y = 0.f;
+                if (!pow2) pr.y = __double2float_rn(v - (double)pr.x);
+              }
+            } else {
+              const int sh = ea + expoB[en.b_row0 + col] - 14 - 8 * (S - 1) + ash;
+              const long long a = aneg ? -acc[c] : acc[c];
+              if (en.mode == 3 && pow2) {
+                pr = i64_to_f32x2(a, sh);
+              } else {
+                v = i64_to_f64(a, sh);
+                if (!pow2) v *= en.alpha;
+                if (en.mode == 3) {
+                  pr.x = __double2float_rn(v);
+                  pr.y = __double2float_rn(v - (double)pr.x);
+                }
+              }
+            }
           }
-          if (en.mode == 0)
-            p = en.C + (long long)row * en.ldc + col;
-          else if (en.mode == 1)
-            p = en.C + 2 * ((long long)(row >> 1) * en.ldc + col) + (row & 1);
-          else
-            p = en.C + 2 * ((long long)col * en.ldc + (row >> 1)) + (row & 1);
-          *p = en.beta == 0.0 ? v : v + en.beta * *p;
+          if (en.mode == 3) v = __longlong_as_double((long long)(((unsigned long long)__float_as_uint(pr.y) << 32) |
+                                                                 __float_as_uint(pr.x)));
+          if (staged) {
+            stg[lane * PITCH + c] = v;
+          } else if (ok) {
+            double *p = en.C + 2 * ((long long)col * en.ldc + (row >> 1)) + (row & 1);
+            *p = en.beta == 0.0 ? v : v + en.beta * *p;
+          }
+        }
+      }
+      if (staged) {
+        __syncwarp();
+        for (int rr = 0; rr < 32; ++rr) {
+          const int grow = m0 + 32 * quad + rr;
+          if (grow >= en.M) break;
+#pragma unroll
+          for (int c0 = 0; c0 < HALF; c0 += 32) {
+            const int c = c0 + lane, col = cbase + c;
+            if (col >= en.N) continue;
+            const double v = stg[rr * PITCH + c];
+            if (en.mode == 3) {   // the 8 bytes already hold the pair (hi, lo)
+              reinterpret_cast<double *>(en.C)[(long long)grow * en.ldc + col] = v;
+              continue;
+            }
+            double *p = en.mode == 0 ? en.C + (long long)grow * en.ldc + col
+                                     : en.C + 2 * ((long long)(grow >> 1) * en.ldc + col) + (grow & 1);
+            *p = en.beta == 0.0 ? v : v + en.beta * *p;
+          }
         }
       }
     }
@@ -570,7 +706,11 @@ CUtensorMap make_map(const Sliced &o, int box_rows) {
 template <int S>
 void launch(const CUtensorMap &ma, const CUtensorMap &mb, const Entry *e, const Tile *t, unsigned ntiles,
             const int *ea, const int *eb, int *err, uint64_t stall_ns, cudaStream_t s) {
-  const int smem = NST * planes(S) * (BM + BN) * 64 + 1024;
+  // the pipeline's stages, large enough to hold the epilogue's staging area (32 rows x (HALF + 1)
+  // doubles per epilogue warp) once the mainloop is done
+  const int ring = NST * planes(S) * (BM + BN) * 64;
+  const int stage_out = epi_warps(S) * 32 * (BN * 4 / epi_warps(S) + 1) * 8;
+  const int smem = std::max(ring, stage_out) + 1024;
   LR_CUDA(cudaFuncSetAttribute(k_ozgemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   k_ozgemm<S><<<ntiles, 32 * (epi_warps(S) + 2), smem, s>>>(ma, mb, e, t, ea, eb, err, stall_ns);
 }
@@ -657,6 +797,14 @@ long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry
   const size_t b1 = entries.size() * sizeof(Entry), off2 = (b1 + 255) / 256 * 256, b2 = tiles.size() * sizeof(Tile);
   std::vector<char> host(off2 + b2);
   std::memcpy(host.data(), entries.data(), b1);
+  // alpha = +-2^k goes into the epilogue's exponent arithmetic (every GEMM of the path), other
+  // values are multiplied in FP64
+  for (size_t e = 0; e < entries.size(); ++e) {
+    Entry &en = reinterpret_cast<Entry *>(host.data())[e];
+    int ex = 0;
+    const double fr = std::frexp(std::fabs(en.alpha), &ex);
+    en.alpha_shift = (en.alpha != 0.0 && fr == 0.5) ? ex - 1 : kNoShift;
+  }
   std::memcpy(host.data() + off2, tiles.data(), b2);
   h.ensure(args, off2 + b2);
   LR_CUDA(cudaMemcpyAsync(args.p, host.data(), off2 + b2, cudaMemcpyHostToDevice, s));

@@ -91,6 +91,7 @@ struct Out {
 // One GEMM of a grouped launch: C = alpha A[a_row0 .. + M) B[b_row0 .. + N)^T + beta C over
 // K columns.  K range per output tile starts at (m0 * km + n0 * kn) rounded down to BK
 // (triangular operands); lower_div > 0 skips tiles with n0 > m0 / lower_div.
+constexpr int kNoShift = 1 << 30;
 struct Entry {
   int a_row0, b_row0, M, N, K;
   int km, kn, lower_div;
@@ -98,6 +99,7 @@ struct Entry {
   long long ldc;
   int mode;
   double alpha, beta;
+  int alpha_shift;   // set by gemm_grouped: k when alpha = +-2^k, else kNoShift
 };
 
 // Grouped launch over all tiles of all entries; operand digit planes of the A role in `a`, of

@@ -1,5 +1,6 @@
 """Serving loop: continuous batching of RPA energy requests on one GPU, admitted by an HBM
-budget.  Each result in a mixed, overlapping batch must equal the same request run alone,
+budget.  Each result in a mixed, overlapping batch must equal the same request run alone and the
+oracle's energy (FP64 and the FP64-accurate mode to 1e-8 Ha, the mixed mode within 0.1 meV/atom),
 and the device-memory estimate used for admission must bound the memory actually held."""
 import time
 
@@ -7,7 +8,8 @@ import numpy as np
 import pytest
 
 from paper_2407_19930_gb300 import librpa_gpu as L
-from oracle import grid as ogrid
+from paper_2407_19930_gb300 import synthetic as syn
+from oracle import grid as ogrid, pipeline
 
 from test_gpu_parity import CONFIGS, _opts
 
@@ -52,7 +54,12 @@ def test_estimate_bounds_the_device_footprint(alone):
         assert 0 < peak <= est, (name, prec, peak, est)
 
 
-def test_mix_equals_alone(alone):
+MEV = 27211.386245988
+
+
+@pytest.fixture(scope="module")
+def served(alone):
+    """The whole mix through one server, under a budget that makes some requests wait."""
     ests = sorted(a[5] for a in alone)
     budget = ests[-1] + ests[-2] + ests[-3]   # at most three of the largest at once: requests must wait
     s = L.librpa_gpu_server_create(slots=3, hbm_budget=budget)
@@ -70,6 +77,26 @@ def test_mix_equals_alone(alone):
         L.librpa_gpu_server_destroy(s)
         for r in reqs:
             L.librpa_gpu_destroy(r)
+    return res, st, budget
+
+
+def test_mix_matches_the_oracle(alone, served):
+    """Every served energy against the oracle's on the same input and grid."""
+    res, _, _ = served
+    refs = {}
+    for (name, prec, inp, grid, ec, est, peak), r in zip(alone, res):
+        if name not in refs:
+            refs[name] = pipeline.rpa_energy(inp, grid)["ec"]
+        ref = refs[name]
+        assert r is not None and r["status"] == L.LIBRPA_OK, (name, r)
+        if prec == L.LIBRPA_SPLIT:
+            assert abs(r["ec"] - ref) * MEV / inp.st.natoms < 0.1, (name, r["ec"], ref)
+        else:
+            assert abs(r["ec"] - ref) < 1e-8, (name, prec, r["ec"], ref)
+
+
+def test_mix_equals_alone(alone, served):
+    res, st, budget = served
     for (name, prec, inp, grid, ec, est, peak), r in zip(alone, res):
         assert r is not None and r["status"] == L.LIBRPA_OK, (name, r)
         assert abs(r["ec"] - ec) <= 1e-12 * abs(ec), (name, prec, r["ec"], ec)
@@ -115,3 +142,31 @@ def test_requests_arriving_while_others_run_are_admitted():
             L.librpa_gpu_destroy(r)
     assert all(r["status"] == L.LIBRPA_OK for r in res)
     assert res[0]["ec"] == res[2]["ec"] and res[1]["ec"] == res[3]["ec"]
+
+
+def test_random_cells_of_the_serving_stream_match_the_oracle():
+    """Requests drawn like the serving workload's (random cells of mixed species and k-meshes up to
+    3x3x1), kept small enough for the oracle: served concurrently, each against the oracle."""
+    inputs = [syn.config_request(i, natoms_range=(2, 6), seed_base=4040) for i in range(4)]
+    modes = [L.LIBRPA_FP64, L.LIBRPA_SPLIT, L.LIBRPA_FP64_TC, L.LIBRPA_FP64]
+    grids = [ogrid.make_grid(8, *inp.delta_range) for inp in inputs]
+    s = L.librpa_gpu_server_create(slots=4)
+    reqs, tickets = [], []
+    try:
+        for inp, grid, prec in zip(inputs, grids, modes):
+            r = L.librpa_gpu_server_request(s, _opts(prec))
+            reqs.append(r)
+            L.set_inputs(r, inp, grid)
+            tickets.append(L.librpa_gpu_server_submit(s, r))
+        res = [L.librpa_gpu_server_wait(s, t, 300.0) for t in tickets]
+    finally:
+        L.librpa_gpu_server_destroy(s)
+        for r in reqs:
+            L.librpa_gpu_destroy(r)
+    for inp, grid, prec, r in zip(inputs, grids, modes, res):
+        assert r["status"] == L.LIBRPA_OK
+        ref = pipeline.rpa_energy(inp, grid)["ec"]
+        if prec == L.LIBRPA_SPLIT:
+            assert abs(r["ec"] - ref) * MEV / inp.st.natoms < 0.1, (r["ec"], ref)
+        else:
+            assert abs(r["ec"] - ref) < 1e-8, (prec, r["ec"], ref)
