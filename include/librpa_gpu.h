@@ -95,8 +95,8 @@ typedef struct {
   int check_level;               /* 0 = none; 1 = check G is real and the pivots finite */
   int chi0_slices;               /* 0 = from precision; 1..5 = digit planes of the chi0 GEMMs */
   int ec_slices;                 /* 0 = from precision; 1..5 = digit planes of the ln det GEMMs */
-  int test_stall_gemms;          /* testing only (0 = off): the handle's first test_stall_gemms
-                                    tensor-core GEMM launches have every tile's MMA issuer wait
+  int test_stall_gemms;          /* testing only (0 = off): in the handle's first test_stall_gemms
+                                    tensor-core GEMM launches the MMA issuer of every CTA waits
                                     (100 us) on a barrier that nothing arrives at, so the bounded-wait
                                     failure path runs: the call returns LIBRPA_E_TIMEOUT, later
                                     calls of the handle run normally */

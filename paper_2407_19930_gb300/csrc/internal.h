@@ -75,6 +75,7 @@ struct Chi0Plan {
   long long bg_sz = 0, ag_sz = 0, n_sz = 0, x_sz = 0, o_sz = 0;
   double flop_per_point = 0;  // algorithmic FP64 flops per (R, tau) point
   double flop_nx_per_point = 0;  // the part of it in the N and X steps
+  double flop_fin_per_point = 0; // the part of it in the final contraction
   // device copies of the per-atom tables, point list, workspace and GEMM descriptors
   DevBuf t_n_ao, t_n_aux, t_ao_off, t_aux_off, t_m, t_lam_off, t_kap_off, t_bg_off, t_ag_off, t_n_off, t_x_off,
       t_o_off, t_pts, ws, gargs1, gargs2;
@@ -88,10 +89,11 @@ struct Chi0Plan {
   long long gen = 0;
   std::vector<int> cpnx_off;
   DevBuf cp_nx, cp_f, t_oe_off, t_oe_k, gargs3;
+  DevBuf t_ozero;   // screening: O-assembly blocks that are exactly zero, per point batch
   std::vector<DevBuf *> all() {
     return {&d_lam, &d_uni, &d_kap, &t_n_ao, &t_n_aux, &t_ao_off, &t_aux_off, &t_m, &t_lam_off, &t_kap_off,
             &t_bg_off, &t_ag_off, &t_n_off, &t_x_off, &t_o_off, &t_pts, &ws, &gargs1, &gargs2,
-            &cp_nx, &cp_f, &t_oe_off, &t_oe_k, &gargs3};
+            &cp_nx, &cp_f, &t_oe_off, &t_oe_k, &gargs3, &t_ozero};
   }
 };
 
@@ -157,6 +159,7 @@ struct Handle {
   DevBuf oz_args;     // descriptors of the tensor-core GEMM launches
   DevBuf work;        // per-call workspace
   double oz_exec_flops = 0;  // MMA flops issued by the last digit-plane GEMM launch
+  double oz_alg_flops = 0;   // algorithmic flops (2 M N K over the summed K) of that launch
   int stalls_left = 0;       // testing only: tensor-core GEMM launches still to take the failure path
   double flop_chi0_run = 0;  // algorithmic flops of the last contraction (screened work left out)
   bool chi0_done = false, lri_dirty = true;

@@ -23,6 +23,7 @@
 // dedicated kernel.  The GEMMs run on the FP64 tensor cores (mma.sync m8n8k4 .f64).
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <set>
 #include <vector>
 
@@ -32,28 +33,6 @@
 namespace librpa {
 namespace {
 
-// a 2^sh as FP64, rounded to nearest even, by integer instructions (zero and results outside the
-// normal range through FP64)
-__device__ __forceinline__ double librpa_i64_to_f64(long long a, int sh) {
-  if (a == 0) return 0.0;
-  const unsigned long long neg = a < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
-  const int lz = __clzll((long long)m);
-  m <<= lz;
-  unsigned long long mant = m >> 11;
-  const unsigned rem = (unsigned)(m & 0x7FFull);
-  int e = 1086 - lz + sh;
-  if (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) {
-    ++mant;
-    if (mant >> 53) {
-      mant >>= 1;
-      ++e;
-    }
-  }
-  if (e <= 0 || e >= 2047) return ldexp((double)a, sh);
-  return __longlong_as_double((long long)(neg | ((unsigned long long)e << 52) | (mant & 0xFFFFFFFFFFFFFull)));
-}
-
 // ---------------------------------------------------------------------------------------
 // batched FP64 "NT" GEMM on the tensor cores: C[m][n] = alpha sum_k A[m][k] B[n][k] + beta C
 struct DGemm {
@@ -62,8 +41,10 @@ struct DGemm {
   int M, N, K, lda, ldb, ldc;
   double alpha, beta;
 };
+// An output tile; c_n >= 0: only the K chunks (of GK) listed at chunks[c_off .. + c_n) are summed
+// (block-sparse operands under Green's-function screening: the others multiply exact zeros).
 struct DTile {
-  int e, m0, n0;
+  int e, m0, n0, c_off, c_n;
 };
 
 constexpr int GK = 16, GPAD = GK + 1;
@@ -79,7 +60,8 @@ __device__ __forceinline__ void dmma_m8n8k4(double &c0, double &c1, double a, do
 // (chunks of 16, m8n8k4 steps of 4), so the tile shape never changes the result.
 template <int WM, int WN>
 __global__ void __launch_bounds__(32 * WM * WN) k_dgemm_nt(const DGemm *__restrict__ gs,
-                                                           const DTile *__restrict__ tiles) {
+                                                           const DTile *__restrict__ tiles,
+                                                           const int *__restrict__ chunks) {
   constexpr int BM = 32 * WM, BN = 32 * WN, NT = 32 * WM * WN;
   const DTile t = tiles[blockIdx.x];
   const DGemm g = gs[t.e];
@@ -93,7 +75,9 @@ __global__ void __launch_bounds__(32 * WM * WN) k_dgemm_nt(const DGemm *__restri
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c][0] = acc[r][c][1] = 0.0;
-  for (int k0 = 0; k0 < g.K; k0 += GK) {
+  const int nch = t.c_n < 0 ? (g.K + GK - 1) / GK : t.c_n;
+  for (int ci = 0; ci < nch; ++ci) {
+    const int k0 = (t.c_n < 0 ? ci : chunks[t.c_off + ci]) * GK;
 #pragma unroll
     for (int e = tid; e < BM * GK; e += NT) {
       const int row = e / GK, k = e % GK, gm = t.m0 + row, gk = k0 + k;
@@ -141,15 +125,19 @@ constexpr int kNumVariants = 5;
 constexpr int kVarWM[kNumVariants] = {2, 1, 2, 1, 4};
 constexpr int kVarWN[kNumVariants] = {2, 2, 1, 1, 2};
 
-void launch_dgemm_variant(int v, unsigned ntiles, const DGemm *g, const DTile *t, cudaStream_t s) {
+void launch_dgemm_variant(int v, unsigned ntiles, const DGemm *g, const DTile *t, const int *c, cudaStream_t s) {
   switch (v) {
-    case 0: k_dgemm_nt<2, 2><<<ntiles, 128, 0, s>>>(g, t); break;
-    case 1: k_dgemm_nt<1, 2><<<ntiles, 64, 0, s>>>(g, t); break;
-    case 2: k_dgemm_nt<2, 1><<<ntiles, 64, 0, s>>>(g, t); break;
-    case 3: k_dgemm_nt<1, 1><<<ntiles, 32, 0, s>>>(g, t); break;
-    default: k_dgemm_nt<4, 2><<<ntiles, 256, 0, s>>>(g, t); break;
+    case 0: k_dgemm_nt<2, 2><<<ntiles, 128, 0, s>>>(g, t, c); break;
+    case 1: k_dgemm_nt<1, 2><<<ntiles, 64, 0, s>>>(g, t, c); break;
+    case 2: k_dgemm_nt<2, 1><<<ntiles, 64, 0, s>>>(g, t, c); break;
+    case 3: k_dgemm_nt<1, 1><<<ntiles, 32, 0, s>>>(g, t, c); break;
+    default: k_dgemm_nt<4, 2><<<ntiles, 256, 0, s>>>(g, t, c); break;
   }
 }
+
+// K chunks a tile of entry e must sum: chunk_fn(e, m0, rows, n0, cols, chunk size, K, out) appends the
+// needed chunk indices (ascending) and returns true, or returns false for every chunk.
+using ChunkFn = std::function<bool(int, int, int, int, int, int, int, std::vector<int> &)>;
 
 // ---------------------------------------------------------------------------------------
 // gathers.  Column tables hold 6 ints per column: {atom, R0, R1, R2, orbital, ao(atom)+orbital}.
@@ -230,6 +218,8 @@ struct OArgs {
   double *O;                 // [P][sum_U naux n_U m_U]
   const long long *o_off;
   long long o_sz_p;
+  // under screening: 1 where the CTA's O block is exactly zero ([P][U][V][64-column chunk]), else NULL
+  const unsigned char *zero;
 };
 
 // Arithmetic of the O assembly.  ArD: FP64 (FP64 modes).  ArF: FP32, for the mixed modes whose
@@ -259,24 +249,7 @@ struct ArDF {
     const float h = __double2float_rn(v);
     return make_float2(h, __double2float_rn(v - (double)h));
   }
-  // x + y in FP64 by integer instructions (the FP64 pipe of GB300 runs at ~1/64 of the FP32 rate):
-  // both significands on the larger exponent's scale in an int64 (the smaller one truncated when it
-  // lies more than 38 binades lower: a relative error below 2^-61), then one rounding to FP64
-  __device__ static double to(T v) {
-    const unsigned bx = __float_as_uint(v.x), by = __float_as_uint(v.y);
-    const int ex = (int)((bx >> 23) & 0xFF), ey = (int)((by >> 23) & 0xFF);
-    if (ex == 0 || ey == 0 || ex == 255 || ey == 255) return (double)v.x + (double)v.y;   // zero, subnormal, inf
-    long long mx = (long long)((bx & 0x7FFFFFu) | 0x800000u), my = (long long)((by & 0x7FFFFFu) | 0x800000u);
-    if (bx >> 31) mx = -mx;
-    if (by >> 31) my = -my;
-    long long a, b;   // a: the operand with the larger exponent
-    int ea, d;
-    if (ex >= ey) { a = mx; b = my; ea = ex; d = ex - ey; } else { a = my; b = mx; ea = ey; d = ey - ex; }
-    const int up = d < 38 ? d : 38;   // a << up keeps 24 + 38 < 63 bits
-    const long long sum = (a << up) + (d - up < 63 ? (b >> (d - up)) : (b < 0 ? -1 : 0));
-    // value = sum 2^(ea - 127 - 23 - up)
-    return librpa_i64_to_f64(sum, ea - 150 - up);
-  }
+  __device__ static double to(T v) { return (double)v.x + (double)v.y; }
   __device__ static T zero() { return make_float2(0.f, 0.f); }
   // N and X arrive from their GEMMs already as (hi, lo) pairs in 8-byte slots
   __device__ static T load(const double *p) { return *reinterpret_cast<const float2 *>(p); }
@@ -311,6 +284,18 @@ __global__ void __launch_bounds__(256) k_oassemble(OArgs a, int NL) {
   const int c0 = blockIdx.x * 64;
   if (c0 >= mU) return;
   const int nU = a.n_ao[U], nV = a.n_ao[V], two = 2 * nV;
+  if (a.zero && a.zero[((size_t)(p * a.natoms + U) * a.natoms + V) * gridDim.x + blockIdx.x]) {
+    // every term of this block multiplies a dropped G block or an exactly zero N / X block
+    double *Ob = a.O + p * a.o_sz_p + a.o_off[U];
+    const int w = min(64, mU - c0), nauxV = a.n_aux[V];
+    for (long long e = threadIdx.x; e < (long long)nauxV * nU * 64; e += blockDim.x) {
+      const int col = (int)(e % 64);
+      if (col >= w) continue;
+      const long long r = e / 64;
+      Ob[(size_t)(a.aux_off[V] + r / nU) * nU * mU + (size_t)(r % nU) * mU + c0 + col] = 0.0;
+    }
+    return;
+  }
   T *Lm = sm;                  // [nU][two]
   T *RG = Lm + nU * two;       // [two][64]
   T *LX = RG + two * 64;       // [NL][nU][two]
@@ -391,31 +376,57 @@ T *upload(Handle &h, DevBuf &b, const std::vector<T> &v) {
 struct DLaunch {
   const DGemm *g = nullptr;
   const DTile *t = nullptr;
+  const int *c = nullptr;
   unsigned ntiles = 0;
   int v = 0;
   double flops = 0;
 };
 
-DLaunch dgemm_prepare(Handle &h, const std::vector<DGemm> &batch, int v, cudaStream_t s, DevBuf &args) {
+// Descriptors, tiles and (with chunk_fn) each tile's K chunks, resident on the device.  flops:
+// the algorithmic flops of what the tiles sum (2 M N K per entry, or per tile over its chunks).
+DLaunch dgemm_prepare(Handle &h, const std::vector<DGemm> &batch, int v, cudaStream_t s, DevBuf &args,
+                      const ChunkFn *chunk_fn = nullptr) {
   const int BM = 32 * kVarWM[v], BN = 32 * kVarWN[v];
   std::vector<DTile> tiles;
+  std::vector<int> chunks, cl;
   DLaunch L;
   L.v = v;
   for (int e = 0; e < (int)batch.size(); ++e) {
-    L.flops += 2.0 * batch[e].M * batch[e].N * batch[e].K;
-    for (int m0 = 0; m0 < batch[e].M; m0 += BM)
-      for (int n0 = 0; n0 < batch[e].N; n0 += BN) tiles.push_back({e, m0, n0});
+    const DGemm &g = batch[e];
+    for (int m0 = 0; m0 < g.M; m0 += BM)
+      for (int n0 = 0; n0 < g.N; n0 += BN) {
+        const int rows = std::min(BM, g.M - m0), cols = std::min(BN, g.N - n0);
+        cl.clear();
+        if (chunk_fn && (*chunk_fn)(e, m0, rows, n0, cols, GK, g.K, cl)) {
+          if (cl.empty()) {   // nothing to sum: a K = 0 entry writes its zeros
+            tiles.push_back({e, m0, n0, 0, 0});
+            continue;
+          }
+          double kk = 0;
+          for (int c : cl) kk += std::min(GK, g.K - c * GK);
+          L.flops += 2.0 * rows * cols * kk;
+          tiles.push_back({e, m0, n0, (int)chunks.size(), (int)cl.size()});
+          chunks.insert(chunks.end(), cl.begin(), cl.end());
+        } else {
+          L.flops += 2.0 * rows * cols * g.K;
+          tiles.push_back({e, m0, n0, 0, -1});
+        }
+      }
   }
   if (tiles.empty()) return L;
-  const size_t b1 = batch.size() * sizeof(DGemm), off2 = (b1 + 255) / 256 * 256, b2 = tiles.size() * sizeof(DTile);
-  std::vector<char> host(off2 + b2);
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b1 = batch.size() * sizeof(DGemm), off2 = al(b1), b2 = tiles.size() * sizeof(DTile),
+               off3 = off2 + al(b2), b3 = std::max<size_t>(1, chunks.size()) * sizeof(int);
+  std::vector<char> host(off3 + b3);
   std::memcpy(host.data(), batch.data(), b1);
   std::memcpy(host.data() + off2, tiles.data(), b2);
-  h.ensure(args, off2 + b2);
-  LR_CUDA(cudaMemcpyAsync(args.p, host.data(), off2 + b2, cudaMemcpyHostToDevice, s));
+  if (!chunks.empty()) std::memcpy(host.data() + off3, chunks.data(), chunks.size() * sizeof(int));
+  h.ensure(args, off3 + b3);
+  LR_CUDA(cudaMemcpyAsync(args.p, host.data(), off3 + b3, cudaMemcpyHostToDevice, s));
   LR_CUDA(cudaStreamSynchronize(s));   // the host staging goes out of scope
   L.g = (const DGemm *)args.p;
   L.t = (const DTile *)((const char *)args.p + off2);
+  L.c = (const int *)((const char *)args.p + off3);
   L.ntiles = (unsigned)tiles.size();
   return L;
 }
@@ -428,7 +439,7 @@ void dgemm_launch(Handle &h, const DLaunch &L, cudaStream_t s, bool timed) {
     LR_CUDA(cudaEventCreate(&t.b));
     LR_CUDA(cudaEventRecord(t.a, s));
   }
-  launch_dgemm_variant(L.v, L.ntiles, L.g, L.t, s);
+  launch_dgemm_variant(L.v, L.ntiles, L.g, L.t, L.c, s);
   ++launch_counter();
   LR_CUDA(cudaGetLastError());
   if (timed) {
@@ -437,7 +448,8 @@ void dgemm_launch(Handle &h, const DLaunch &L, cudaStream_t s, bool timed) {
   }
 }
 
-int dgemm_autotune(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, DevBuf &args) {
+int dgemm_autotune(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, DevBuf &args,
+                   const ChunkFn *chunk_fn = nullptr) {
   for (const DGemm &g : batch)
     if (g.beta != 0.0) return 0;   // repeated runs would accumulate into C
   int best = 0;
@@ -446,7 +458,7 @@ int dgemm_autotune(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, D
   LR_CUDA(cudaEventCreate(&a));
   LR_CUDA(cudaEventCreate(&b));
   for (int v = 0; v < kNumVariants; ++v) {
-    const DLaunch L = dgemm_prepare(h, batch, v, s, args);
+    const DLaunch L = dgemm_prepare(h, batch, v, s, args, chunk_fn);
     LR_CUDA(cudaEventRecord(a, s));
     dgemm_launch(h, L, s, false);
     LR_CUDA(cudaEventRecord(b, s));
@@ -463,9 +475,13 @@ int dgemm_autotune(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, D
   return best;
 }
 
-void dgemm_batched(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, DevBuf &args, int *var) {
-  if (*var < 0) *var = dgemm_autotune(h, batch, s, args);
-  dgemm_launch(h, dgemm_prepare(h, batch, *var, s, args), s, true);
+// returns the algorithmic flops of the launch
+double dgemm_batched(Handle &h, const std::vector<DGemm> &batch, cudaStream_t s, DevBuf &args, int *var,
+                     const ChunkFn *chunk_fn = nullptr) {
+  if (*var < 0) *var = dgemm_autotune(h, batch, s, args, chunk_fn);
+  const DLaunch L = dgemm_prepare(h, batch, *var, s, args, chunk_fn);
+  dgemm_launch(h, L, s, true);
+  return L.flops;
 }
 
 }  // namespace
@@ -532,10 +548,12 @@ void chi0_shape(const Handle &h, Chi0Plan &P) {
     fl += 2.0 * 2.0 * h.nao * P.m[V] * rowsV;      // X-step, both G
   }
   P.flop_nx_per_point = fl;
+  P.flop_fin_per_point = 0;
   for (int U = 0; U < nat; ++U) {
     const double cols = (double)h.n_ao[U] * P.m[U];
     for (int V = 0; V < nat; ++V) fl += 2.0 * h.n_aux[V] * cols * 4.0 * h.n_ao[V];   // O assembly
     fl += 2.0 * h.n_aux[U] * cols * h.naux;                                        // final
+    P.flop_fin_per_point += 2.0 * h.n_aux[U] * cols * h.naux;
   }
   P.flop_per_point = fl;
   P.bg_sz = P.bg_off[nat];
@@ -636,8 +654,17 @@ void chi0_plan(Handle &h) {
 
 namespace {
 
-// O = M + M* + Z + Z* for the np points of a batch (FP64 pipe).
-void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw, double *Ow) {
+// O = M + M* + Z + Z* for the np points of a batch (FP64 pipe).  zero: device flags of the CTAs
+// whose O block is exactly zero under screening ([np][U][V][64-column chunk]), or NULL.
+// 64-column chunks of the widest packed-column list (the O assembly's grid.x)
+int oasm_chunks(const Handle &h) {
+  int c = 0;
+  for (int a = 0; a < h.natoms; ++a) c = std::max(c, (h.plan.m[a] + 63) / 64);
+  return c;
+}
+
+void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw, double *Ow,
+                   const unsigned char *zero = nullptr) {
   Chi0Plan &P = h.plan;
   const int nat = h.natoms;
   int maxn = 0, max_chunks = 0;
@@ -691,6 +718,7 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
   oa.O = Ow;
   oa.o_off = (const long long *)P.t_o_off.p;
   oa.o_sz_p = P.o_sz;
+  oa.zero = zero;
   dim3 og((unsigned)max_chunks, (unsigned)(np * nat * nat));
   if (ar == 0)
     k_oassemble<ArD><<<og, 64 * NL, osmem, h.stream>>>(oa, NL);
@@ -850,18 +878,197 @@ ScreenSel screen_select(const Handle &h, const std::vector<int> &rl) {
   return sel;
 }
 
-void timed_grouped(Handle &h, const oz::Sliced &a, const oz::Sliced &b, const std::vector<oz::Entry> &es, int *err,
-                   DevBuf &args) {
-  double fl = 0;
-  for (const oz::Entry &e : es) fl += 2.0 * e.M * e.N * e.K;
-  Handle::Timed t{nullptr, nullptr, fl, 0};
+// returns the algorithmic flops of the launch (over the K stages summed)
+double timed_grouped(Handle &h, const oz::Sliced &a, const oz::Sliced &b, const std::vector<oz::Entry> &es, int *err,
+                     DevBuf &args, const oz::StageFn *stage_fn = nullptr) {
+  Handle::Timed t{nullptr, nullptr, 0, 0};
   LR_CUDA(cudaEventCreate(&t.a));
   LR_CUDA(cudaEventCreate(&t.b));
   LR_CUDA(cudaEventRecord(t.a, h.stream));
-  oz::gemm_grouped(a, b, es, err, h.stream, h, args);
+  oz::gemm_grouped(a, b, es, err, h.stream, h, args, stage_fn);
   LR_CUDA(cudaEventRecord(t.b, h.stream));
+  t.flops = h.oz_alg_flops;
   t.exec_flops = h.oz_exec_flops;
   h.timed.push_back(t);
+  return t.flops;
+}
+
+// Block structure of the contraction of a batch of points under Green's-function screening (Sec. 5's
+// threshold; Sec. 2: the decay of G limits what contributes).  For point q:
+//   n(q, g, V, b, l): the N-step block of V for union block b (K, R1) and neighbour l (L, R2) of V
+//                     multiplies the kept G^g block (L, K) at R1 - R_q - R2;
+//   x(q, g, V, I, l): the X-step block of V for atom I and neighbour l multiplies the kept G^g block
+//                     (I, L) at R_q + R2;
+//   o(q, U, V, b'):   the O block of (U, V) on U's neighbour b' (K, R1) can be nonzero: one of its four
+//                     terms pairs a kept G block with an N or X block that is not exactly zero,
+//                     G^vir_UV(R_q) N[G^occ] + G^occ_UV(R_q) N[G^vir] + X[G^vir] G^occ_VK(R1 - R_q)
+//                     + X[G^occ] G^vir_VK(R1 - R_q).
+// The GEMM tiles then sum only the K chunks that meet such blocks, and O blocks without one are
+// written as zeros: every skipped product is an exact zero, so the result is that of the dense
+// contraction on the screened G, and the cost follows the kept blocks inside a point.
+struct BlockSparse {
+  int nat = 0, nuni = 0, maxnb = 1, np = 0;
+  std::vector<int> ublock_of_col;   // union block index at its first union column, -1 elsewhere
+  std::vector<unsigned char> n, x, o;
+  size_t in(int q, int g, int V, int b, int l) const { return ((((size_t)q * 2 + g) * nat + V) * nuni + b) * maxnb + l; }
+  size_t ix(int q, int g, int V, int I, int l) const { return ((((size_t)q * 2 + g) * nat + V) * nat + I) * maxnb + l; }
+  size_t io(int q, int U, int V, int b) const { return (((size_t)q * nat + U) * nat + V) * maxnb + b; }
+};
+
+BlockSparse block_sparse(const Handle &h, const std::vector<Point> &pts) {
+  const Chi0Plan &P = h.plan;
+  const int nat = h.natoms, nR = h.mesh.size(), ntau = h.ntau;
+  const size_t nn = (size_t)nat * nat;
+  BlockSparse B;
+  B.nat = nat;
+  B.nuni = (int)P.uni.size();
+  B.np = (int)pts.size();
+  for (int a = 0; a < nat; ++a) B.maxnb = std::max(B.maxnb, (int)P.nb[a].size());
+  B.ublock_of_col.assign(P.m_all + 1, -1);
+  for (int b = 0; b < B.nuni; ++b) B.ublock_of_col[P.uni_col[b]] = b;
+  B.n.assign((size_t)B.np * 2 * nat * B.nuni * B.maxnb, 0);
+  B.x.assign((size_t)B.np * 2 * nat * nat * B.maxnb, 0);
+  B.o.assign((size_t)B.np * nat * nat * B.maxnb, 0);
+  auto kept = [&](int g, int it, int iR, int I, int J) {
+    return h.gmask[(((size_t)(h.cur_spin * 2 + g) * ntau + it) * nR + iR) * nn + (size_t)I * nat + J];
+  };
+  std::vector<unsigned char> nnz(2 * (size_t)nat * B.nuni), xnz(2 * nn);
+  for (int q = 0; q < B.np; ++q) {
+    const Point &pt = pts[q];
+    const int *R = pt.R, it = pt.itau;
+    std::fill(nnz.begin(), nnz.end(), 0);
+    std::fill(xnz.begin(), xnz.end(), 0);
+    for (int g = 0; g < 2; ++g)
+      for (int V = 0; V < nat; ++V) {
+        const std::vector<NbEntry> &nbV = P.nb[V];
+        for (int b = 0; b < B.nuni; ++b) {
+          const auto &u = P.uni[b];
+          for (int l = 0; l < (int)nbV.size(); ++l) {
+            const unsigned char v = kept(g, it, h.mesh.index(std::get<1>(u) - R[0] - nbV[l].R[0], std::get<2>(u) - R[1] - nbV[l].R[1],
+                                                             std::get<3>(u) - R[2] - nbV[l].R[2]),
+                                         nbV[l].K, std::get<0>(u));
+            B.n[B.in(q, g, V, b, l)] = v;
+            nnz[((size_t)g * nat + V) * B.nuni + b] |= v;
+          }
+        }
+        for (int l = 0; l < (int)nbV.size(); ++l) {
+          const int iR = h.mesh.index(R[0] + nbV[l].R[0], R[1] + nbV[l].R[1], R[2] + nbV[l].R[2]);
+          for (int I = 0; I < nat; ++I) {
+            const unsigned char v = kept(g, it, iR, I, nbV[l].K);
+            B.x[B.ix(q, g, V, I, l)] = v;
+            xnz[((size_t)g * nat + V) * nat + I] |= v;
+          }
+        }
+      }
+    for (int U = 0; U < nat; ++U)
+      for (int V = 0; V < nat; ++V) {
+        const bool vir_uv = kept(1, it, pt.iR, U, V), occ_uv = kept(0, it, pt.iR, U, V);
+        const bool xv = xnz[((size_t)1 * nat + V) * nat + U], xo = xnz[((size_t)0 * nat + V) * nat + U];
+        for (int b = 0; b < (int)P.nb[U].size(); ++b) {
+          const NbEntry &e = P.nb[U][b];
+          const int ub = B.ublock_of_col[e.ucol];
+          const int iRk = h.mesh.index(e.R[0] - R[0], e.R[1] - R[1], e.R[2] - R[2]);
+          const bool nz = (vir_uv && nnz[((size_t)0 * nat + V) * B.nuni + ub]) ||
+                          (occ_uv && nnz[((size_t)1 * nat + V) * B.nuni + ub]) ||
+                          (xv && kept(0, it, iRk, V, e.K)) || (xo && kept(1, it, iRk, V, e.K));
+          B.o[B.io(q, U, V, b)] = nz;
+        }
+      }
+  }
+  return B;
+}
+
+// the needed chunks of [0, K) in units of cs, given which of `blocks` (start, width) are live
+void chunks_from_blocks(const std::vector<std::pair<int, int>> &blocks, const std::vector<char> &live, int cs, int K,
+                        std::vector<int> &out) {
+  std::vector<int> pre(K + 1, 0);   // prefix count of live columns
+  std::vector<char> col(K, 0);
+  for (size_t l = 0; l < blocks.size(); ++l)
+    if (live[l])
+      for (int c = blocks[l].first; c < std::min(K, blocks[l].first + blocks[l].second); ++c) col[c] = 1;
+  for (int c = 0; c < K; ++c) pre[c + 1] = pre[c] + col[c];
+  for (int c = 0; c * cs < K; ++c)
+    if (pre[std::min(K, (c + 1) * cs)] > pre[c * cs]) out.push_back(c);
+}
+
+// N-step tile of (q, g, V): columns [n0, n0 + cols) of the union list, K = V's packed columns
+void chunks_n(const Handle &h, const BlockSparse &B, int q, int g, int V, int n0, int cols, int cs, int K,
+              std::vector<int> &out) {
+  const Chi0Plan &P = h.plan;
+  const std::vector<NbEntry> &nbV = P.nb[V];
+  std::vector<std::pair<int, int>> blocks;
+  std::vector<char> live(nbV.size(), 0);
+  const int b0 = (int)(std::upper_bound(P.uni_col.begin(), P.uni_col.end(), n0) - P.uni_col.begin()) - 1;
+  for (int l = 0; l < (int)nbV.size(); ++l) {
+    blocks.push_back({nbV[l].col, h.n_ao[nbV[l].K]});
+    for (int b = std::max(0, b0); b < B.nuni && P.uni_col[b] < n0 + cols; ++b)
+      if (B.n[B.in(q, g, V, b, l)]) {
+        live[l] = 1;
+        break;
+      }
+  }
+  chunks_from_blocks(blocks, live, cs, K, out);
+}
+
+// X-step tile of (q, g, V): rows [m0, m0 + rows) of all NAOs, K = V's packed columns
+void chunks_x(const Handle &h, const BlockSparse &B, int q, int g, int V, int m0, int rows, int cs, int K,
+              std::vector<int> &out) {
+  const Chi0Plan &P = h.plan;
+  const std::vector<NbEntry> &nbV = P.nb[V];
+  std::vector<std::pair<int, int>> blocks;
+  std::vector<char> live(nbV.size(), 0);
+  for (int l = 0; l < (int)nbV.size(); ++l) {
+    blocks.push_back({nbV[l].col, h.n_ao[nbV[l].K]});
+    for (int I = 0; I < B.nat; ++I)
+      if (h.ao_off[I] < m0 + rows && h.ao_off[I] + h.n_ao[I] > m0 && B.x[B.ix(q, g, V, I, l)]) {
+        live[l] = 1;
+        break;
+      }
+  }
+  chunks_from_blocks(blocks, live, cs, K, out);
+}
+
+// final-contraction tile of (q, U): columns nu in [n0, n0 + cols), K = (i, k) over U's n_U x m_U
+void chunks_f(const Handle &h, const BlockSparse &B, int q, int U, int n0, int cols, int cs, int K,
+              std::vector<int> &out) {
+  const Chi0Plan &P = h.plan;
+  const std::vector<NbEntry> &nbU = P.nb[U];
+  const int mU = P.m[U];
+  std::vector<char> liveb(nbU.size(), 0);
+  for (int b = 0; b < (int)nbU.size(); ++b)
+    for (int V = 0; V < B.nat; ++V)
+      if (h.aux_off[V] < n0 + cols && h.aux_off[V] + h.n_aux[V] > n0 && B.o[B.io(q, U, V, b)]) {
+        liveb[b] = 1;
+        break;
+      }
+  std::vector<std::pair<int, int>> blocks;
+  std::vector<char> live;
+  for (int i = 0; i < h.n_ao[U]; ++i)
+    for (int b = 0; b < (int)nbU.size(); ++b) {
+      blocks.push_back({i * mU + nbU[b].col, h.n_ao[nbU[b].K]});
+      live.push_back(liveb[b]);
+    }
+  chunks_from_blocks(blocks, live, cs, K, out);
+}
+
+// O-assembly flags [q][U][V][64-column chunk]: 1 where the block is exactly zero; and the
+// algorithmic flops of the blocks that are not
+std::vector<unsigned char> ozero_flags(const Handle &h, const BlockSparse &B, int max_chunks, double *flops) {
+  const Chi0Plan &P = h.plan;
+  const int nat = B.nat;
+  std::vector<unsigned char> z((size_t)B.np * nat * nat * max_chunks, 1);
+  *flops = 0;
+  for (int q = 0; q < B.np; ++q)
+    for (int U = 0; U < nat; ++U)
+      for (int V = 0; V < nat; ++V)
+        for (int b = 0; b < (int)P.nb[U].size(); ++b) {
+          if (!B.o[B.io(q, U, V, b)]) continue;
+          const NbEntry &e = P.nb[U][b];
+          for (int c = e.col / 64; c <= (e.col + h.n_ao[e.K] - 1) / 64; ++c)
+            z[(((size_t)q * nat + U) * nat + V) * max_chunks + c] = 0;
+          *flops += 8.0 * h.n_aux[V] * h.n_ao[U] * h.n_ao[V] * h.n_ao[e.K];
+        }
+  return z;
 }
 
 // FP64 route, one batch of np points whose workspace starts at P.ws: gathered G operands Bg, Ag,
@@ -992,6 +1199,7 @@ DpWs dp_ws(const Handle &h, const Chi0Plan &P, long long cap_doubles = 1LL << 27
 void chi0_run_tc(Handle &h) {
   Chi0Plan &P = h.plan;
   const int nat = h.natoms, nR = h.mesh.size(), ntau = h.ntau, naux = h.naux, nao = h.nao, S = h.chi0_S;
+  const bool scr = h.g_screen > 0;
   cudaStream_t s = h.stream;
   h.ensure(h.d_chi_tau, (size_t)ntau * nR * naux * naux * sizeof(double));
   const int rows_bg = 2 * nat * P.m_all, rows_ag = 2 * nat * nao, rows_o = nat * naux;
@@ -1022,7 +1230,6 @@ void chi0_run_tc(Handle &h) {
     const long long total_pts = (long long)sel.pts.size();
     h.stats.n_points_chi0 += total_pts;
     h.stats.n_points_skipped += sel.skipped;
-    h.flop_chi0_run += total_pts * P.flop_per_point;
     for (long long p0 = 0; p0 < total_pts; p0 += npb) {
       const int np = (int)std::min(npb, total_pts - p0);
       std::vector<Point> pts(sel.pts.begin() + p0, sel.pts.begin() + p0 + np);
@@ -1084,9 +1291,34 @@ void chi0_run_tc(Handle &h) {
             b.alpha = 1.0;
             ex.push_back(b);
           }
-      timed_grouped(h, cpnx, sbg, en, err, P.gargs1);
-      timed_grouped(h, sag, cpnx, ex, err, P.gargs2);
-      run_oassemble(h, (const Point *)P.t_pts.p, np, Nw, Xw, Ow);
+      // screening: tiles sum only the K stages that meet kept G blocks, O blocks without a kept
+      // contribution are written as zeros (see BlockSparse)
+      BlockSparse B;
+      if (scr) B = block_sparse(h, pts);
+      const oz::StageFn fn_n = [&](int e, int, int, int n0, int cols, int cs, int K, std::vector<int> &out) {
+        chunks_n(h, B, e / (2 * nat), (e / nat) % 2, e % nat, n0, cols, cs, K, out);
+        return true;
+      };
+      const oz::StageFn fn_x = [&](int e, int m0, int rows, int, int, int cs, int K, std::vector<int> &out) {
+        chunks_x(h, B, e / (2 * nat), (e / nat) % 2, e % nat, m0, rows, cs, K, out);
+        return true;
+      };
+      const oz::StageFn fn_f = [&](int e, int, int, int n0, int cols, int cs, int K, std::vector<int> &out) {
+        chunks_f(h, B, e / nat, e % nat, n0, cols, cs, K, out);
+        return true;
+      };
+      h.flop_chi0_run += timed_grouped(h, cpnx, sbg, en, err, P.gargs1, scr ? &fn_n : nullptr);
+      h.flop_chi0_run += timed_grouped(h, sag, cpnx, ex, err, P.gargs2, scr ? &fn_x : nullptr);
+      std::vector<unsigned char> zf;
+      if (scr) {
+        double fo = 0;
+        zf = ozero_flags(h, B, oasm_chunks(h), &fo);
+        upload(h, P.t_ozero, zf);
+        h.flop_chi0_run += fo;
+      } else {
+        h.flop_chi0_run += np * (P.flop_per_point - P.flop_nx_per_point - P.flop_fin_per_point);
+      }
+      run_oassemble(h, (const Point *)P.t_pts.p, np, Nw, Xw, Ow, scr ? (const unsigned char *)P.t_ozero.p : nullptr);
       // digit planes of O (rows nu per (point, U), K = n_U m_U), then the final contraction
       {
         std::vector<long long> off(np * nat);
@@ -1120,7 +1352,7 @@ void chi0_run_tc(Handle &h) {
           ef.push_back(f);
         }
       }
-      timed_grouped(h, cpf, sod, ef, err, P.gargs3);
+      h.flop_chi0_run += timed_grouped(h, cpf, sod, ef, err, P.gargs3, scr ? &fn_f : nullptr);
     }
   }
   h.cur_spin = 0;
@@ -1166,12 +1398,40 @@ void chi0_run(Handle &h, double *ms_gemm) {
       fp64_gather(h, dpts, np, w);
       std::vector<DGemm> b1, b2;
       const size_t z = (size_t)p0 * 2 * h.natoms;
-      h.flop_chi0_run += fp64_nx(h, np, w, b1, scr ? sel.nzN.data() + z : nullptr, scr ? sel.nzX.data() + z : nullptr);
-      h.flop_chi0_run += np * (P.flop_per_point - P.flop_nx_per_point);
-      dgemm_batched(h, b1, s, P.gargs1, &P.var_nx);
-      run_oassemble(h, dpts, np, w.Nw, w.Xw, w.Ow);
+      if (!scr) {
+        h.flop_chi0_run += fp64_nx(h, np, w, b1);
+        h.flop_chi0_run += np * (P.flop_per_point - P.flop_nx_per_point);
+        dgemm_batched(h, b1, s, P.gargs1, &P.var_nx);
+        run_oassemble(h, dpts, np, w.Nw, w.Xw, w.Ow);
+        fp64_final(h, pts, w, b2);
+        dgemm_batched(h, b2, s, P.gargs2, &P.var_fin);
+        continue;
+      }
+      // screening: the GEMM tiles sum only the K chunks that meet kept G blocks, and O blocks with
+      // no kept contribution are written as zeros
+      const BlockSparse B = block_sparse(h, pts);
+      const int nat = h.natoms;
+      const ChunkFn fnx = [&](int e, int m0, int rows, int n0, int cols, int cs, int K, std::vector<int> &out) {
+        const int r = e / 2, V = r % nat, g = (r / nat) % 2, q = r / (2 * nat);
+        if (e % 2 == 0)
+          chunks_n(h, B, q, g, V, n0, cols, cs, K, out);
+        else
+          chunks_x(h, B, q, g, V, m0, rows, cs, K, out);
+        return true;
+      };
+      const ChunkFn ff = [&](int e, int, int, int n0, int cols, int cs, int K, std::vector<int> &out) {
+        chunks_f(h, B, e / nat, e % nat, n0, cols, cs, K, out);
+        return true;
+      };
+      fp64_nx(h, np, w, b1, sel.nzN.data() + z, sel.nzX.data() + z);
+      h.flop_chi0_run += dgemm_batched(h, b1, s, P.gargs1, &P.var_nx, &fnx);
+      double fo = 0;
+      const std::vector<unsigned char> zf = ozero_flags(h, B, oasm_chunks(h), &fo);
+      upload(h, P.t_ozero, zf);
+      run_oassemble(h, dpts, np, w.Nw, w.Xw, w.Ow, (const unsigned char *)P.t_ozero.p);
+      h.flop_chi0_run += fo;
       fp64_final(h, pts, w, b2);
-      dgemm_batched(h, b2, s, P.gargs2, &P.var_fin);
+      h.flop_chi0_run += dgemm_batched(h, b2, s, P.gargs2, &P.var_fin, &ff);
     }
   }
   h.cur_spin = 0;

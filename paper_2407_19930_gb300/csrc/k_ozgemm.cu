@@ -15,8 +15,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "internal.h"
 #include "ozgemm.h"
@@ -318,8 +320,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// An output tile; c_n >= 0: only the K stages listed at chunks[c_off .. + c_n) (in units of the
+// stage's K) are summed -- block-sparse operands, the others multiply exact zeros.
 struct Tile {
-  int e, m0, n0;
+  int e, m0, n0, c_off, c_n;
 };
 
 // ------------------------------------------------------------------ epilogue conversions
@@ -444,15 +448,36 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// stall_ns > 0 (testing only): the MMA issuer first waits that long on an mbarrier nothing
-// arrives at, so the tile takes the bounded-wait failure path.  On any failure the CTA sets
-// *err, stops issuing, waits (with the full limit) for the TMA copies and MMAs it has already
-// issued, frees its TMEM and returns.
+// Operands of the entries of one launch that share them: tensor maps of the A and B digit planes
+// (global memory, 128-byte aligned) and their row exponents.
+struct alignas(128) MapPair {
+  CUtensorMap a, b;
+  const int *ea, *eb;
+};
+
+// Pipelined, warp-specialised kernel: CTA c takes tiles c, c + gridDim.x, ... (128 x 64 output
+// tiles of the launch's entries, sorted by decreasing K range on the host), keeping its barriers and
+// TMEM across them (the launch uses one CTA per tile; the loop also serves a persistent grid).
+//   warp EW (one lane): TMA producer over a ring of NST shared-memory stages (each the NP digit
+//     planes of a 128 x 32 A slice and a 64 x 32 B slice, SWIZZLE_64B, K-major); the ring runs on
+//     across tiles, so the next tile's loads overlap this tile's MMAs and epilogue;
+//   warp EW + 1 (one lane): tcgen05.mma issuer; commits free a stage when its MMAs complete and, at
+//     the end of a flush group, signal the epilogue; the next group (of this or the next tile)
+//     starts once the epilogue has drained the accumulators;
+//   warps 0..EW-1: epilogue; warp w owns TMEM lanes 32 (w % 4) .. + 31 (= tile rows).  With EW = 8
+//     (digit planes) warp w takes columns 32 (w / 4) .. + 31 and after each flush group moves the
+//     diagonal accumulators into exact int64 register sums (32 per thread); with EW = 4 (plain
+//     BF16 / TF32, one group) each warp takes all 64 columns into registers.  The TMEM columns go
+//     back to the issuer before the values are converted and stored, so conversion and stores
+//     overlap the next tile's MMAs.
+// stall_ns > 0 (testing only): the MMA issuer first waits that long on an mbarrier nothing arrives
+// at, so the CTA takes the bounded-wait failure path.  On any failure the CTA sets *err, stops
+// issuing, waits (with the full limit) for the TMA copies and MMAs it has already issued, frees its
+// TMEM and returns.
 template <int S>
 __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
-    k_ozgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-             const Entry *__restrict__ entries, const Tile *__restrict__ tiles, const int *__restrict__ expoA,
-             const int *__restrict__ expoB, int *err, uint64_t stall_ns) {
+    k_ozgemm(const MapPair *__restrict__ maps, const Entry *__restrict__ entries, const Tile *__restrict__ tiles,
+             const int *__restrict__ chunks, int ntiles, int *err, uint64_t stall_ns) {
   constexpr bool TF = S == S_TF32 || S == S_TF32X3;   // kind::tf32
   constexpr bool PLAIN = S == 0 || TF;                 // one FP32 accumulator over all K
   constexpr int NP = S == S_TF32X3 ? 2 : PLAIN ? 1 : S;   // planes per operand
@@ -460,19 +485,18 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
   constexpr uint32_t A_BYTES = BM * 64, B_BYTES = BN * 64;
   constexpr uint32_t STAGE = NP * (A_BYTES + B_BYTES);
   // K steps per flush group: NP pairs x (32 G) x 2^14 <= 2^24 keeps the FP32 sums exact; plain
-  // BF16 accumulates over the whole K in FP32
+  // forms accumulate over the whole K in FP32
   constexpr int G = PLAIN ? (1 << 30) : 32 / NP;
   constexpr int EPI_WARPS = epi_warps(S), HALF = BN * 4 / EPI_WARPS;   // HALF: columns per epilogue warp
   constexpr uint32_t TMEM_COLS = tmem_cols<PLAIN ? 1 : NP>();
+  constexpr int SPITCH = 17;   // staging: 32 rows x 16 columns (+1) of 8-byte values per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[NST], empty[NST], tfull, tempty, mdone, never;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const Tile tl = tiles[blockIdx.x];
-  const Entry en = entries[tl.e];
-  const int n0 = tl.n0, m0 = tl.m0;
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  double *stage_out = reinterpret_cast<double *>(smem + NST * STAGE);
   if (tid == 0) {
 #pragma unroll
     for (int s = 0; s < NST; ++s) {
@@ -491,38 +515,44 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  int kbeg = m0 * en.km + n0 * en.kn;
-  kbeg = kbeg / KS * KS;
-  const int nsteps = en.K > kbeg ? (en.K - kbeg + KS - 1) / KS : 0;
-  const int ngroups = (nsteps + G - 1) / G;
-  const int arow = en.a_row0 + m0, brow = en.b_row0 + n0;
-  long long acc[HALF];
-#pragma unroll
-  for (int j = 0; j < HALF; ++j) acc[j] = 0;
-  bool failed = false;
-  const int quad = warp & 3, half = warp >> 2;   // epilogue: TMEM lane quadrant, column half
+  // K range of a tile: from (m0 km + n0 kn) rounded down to the stage size (triangular operands),
+  // or the tile's list of stages
+  auto steps_of = [&](const Entry &en, const Tile &tl, int &kbeg) {
+    kbeg = (tl.m0 * en.km + tl.n0 * en.kn) / KS * KS;
+    if (tl.c_n >= 0) return tl.c_n;
+    return en.K > kbeg ? (en.K - kbeg + KS - 1) / KS : 0;
+  };
+  auto k_of = [&](const Tile &tl, int kbeg, int i) { return tl.c_n >= 0 ? chunks[tl.c_off + i] * KS : kbeg + i * KS; };
   if (warp == EPI_WARPS) {
     if (lane == 0) {
-      int issued = 0;
-      for (int i = 0; i < nsteps; ++i) {
-        const int st = i % NST;
-        if (abort_flag || !mbar_wait(&empty[st], ((i / NST) & 1) ^ 1, WAIT_NS, &abort_flag)) {
-          abort_flag = 1;
-          break;
+      long long it = 0;   // stages issued so far (all tiles)
+      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const Entry en = entries[tl.e];
+        const MapPair *mp = maps + en.pair;
+        int kbeg;
+        const int nsteps = steps_of(en, tl, kbeg);
+        const int arow = en.a_row0 + tl.m0, brow = en.b_row0 + tl.n0;
+        for (int i = 0; i < nsteps; ++i, ++it) {
+          const int st = (int)(it % NST);
+          if (abort_flag || !mbar_wait(&empty[st], (uint32_t)(((it / NST) & 1) ^ 1), WAIT_NS, &abort_flag)) {
+            abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(&full[st], STAGE);
+          uint8_t *sa = smem + st * STAGE, *sb = sa + NP * A_BYTES;
+          const int k0 = k_of(tl, kbeg, i);
+#pragma unroll
+          for (int p = 0; p < NP; ++p) tma_load_3d(sa + p * A_BYTES, &mp->a, &full[st], k0, arow, p);
+#pragma unroll
+          for (int p = 0; p < NP; ++p) tma_load_3d(sb + p * B_BYTES, &mp->b, &full[st], k0, brow, p);
         }
-        mbar_expect_tx(&full[st], STAGE);
-        uint8_t *sa = smem + st * STAGE, *sb = sa + NP * A_BYTES;
-        const int k0 = kbeg + i * KS;
-#pragma unroll
-        for (int p = 0; p < NP; ++p) tma_load_3d(sa + p * A_BYTES, &tmA, &full[st], k0, arow, p);
-#pragma unroll
-        for (int p = 0; p < NP; ++p) tma_load_3d(sb + p * B_BYTES, &tmB, &full[st], k0, brow, p);
-        issued = i + 1;
       }
-      // after a failure: the copies of the last NST issued stages may still be in flight
-      // (earlier ones were consumed); wait for each to land before the CTA exits
+      // after a failure: the copies of the last NST issued stages may still be in flight (earlier
+      // ones were consumed); wait for each to land before the CTA exits
       if (abort_flag)
-        for (int i = issued > NST ? issued - NST : 0; i < issued; ++i) mbar_wait(&full[i % NST], (i / NST) & 1, WAIT_NS);
+        for (long long i = it > NST ? it - NST : 0; i < it; ++i)
+          mbar_wait(&full[i % NST], (uint32_t)((i / NST) & 1), WAIT_NS);
     }
   } else if (warp == EPI_WARPS + 1) {
     if (lane == 0) {
@@ -530,36 +560,47 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
         mbar_wait(&never, 0, stall_ns, &abort_flag);
         abort_flag = 1;
       }
-      for (int i = 0; i < nsteps; ++i) {
-        const int st = i % NST, gi = i / G, c = i % G;
-        if (c == 0 && gi > 0 && (abort_flag || !mbar_wait(&tempty, (gi - 1) & 1, WAIT_NS, &abort_flag))) {
-          abort_flag = 1;
-          break;
+      long long it = 0, g = 0;   // stages consumed, flush groups committed (all tiles)
+      for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const Entry en = entries[tl.e];
+        int kbeg;
+        const int nsteps = steps_of(en, tl, kbeg);
+        for (int i = 0; i < nsteps; ++i, ++it) {
+          const int st = (int)(it % NST), c = i % G;
+          // a new group needs the accumulators drained by the epilogue (previous group, any tile)
+          if (c == 0 && g > 0 && (abort_flag || !mbar_wait(&tempty, (uint32_t)((g - 1) & 1), WAIT_NS, &abort_flag))) {
+            abort_flag = 1;
+            break;
+          }
+          if (abort_flag || !mbar_wait(&full[st], (uint32_t)((it / NST) & 1), WAIT_NS, &abort_flag)) {
+            abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + NP * A_BYTES;
+#pragma unroll
+          for (int s = 1; s <= NP; ++s)
+#pragma unroll
+            for (int u = 1; u + s <= NP + 1; ++u)
+#pragma unroll
+              for (int j = 0; j < 2; ++j) {   // two MMAs of 32 bytes of K per 64-byte row
+                const uint64_t da = smem_desc64(sa + (s - 1) * A_BYTES + 32 * j);
+                const uint64_t db = smem_desc64(sb + (u - 1) * B_BYTES + 32 * j);
+                // digit planes: one accumulator per diagonal s + u; plain forms: one for all
+                const uint32_t col = PLAIN ? 0u : (uint32_t)(s + u - 2) * BN;
+                const uint32_t accum = (c == 0 && j == 0 && s == 1 && (!PLAIN || u == 1)) ? 0u : 1u;
+                if constexpr (TF)
+                  umma_tf32(tmem + col, da, db, accum);
+                else
+                  umma(tmem + col, da, db, accum);
+              }
+          umma_commit(&empty[st]);
+          if (c == G - 1 || i == nsteps - 1) {
+            umma_commit(&tfull);
+            ++g;
+          }
         }
-        if (abort_flag || !mbar_wait(&full[st], (i / NST) & 1, WAIT_NS, &abort_flag)) {
-          abort_flag = 1;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + NP * A_BYTES;
-#pragma unroll
-        for (int s = 1; s <= NP; ++s)
-#pragma unroll
-          for (int t = 1; t + s <= NP + 1; ++t)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {   // two MMAs of 32 bytes of K per 64-byte row
-              const uint64_t da = smem_desc64(sa + (s - 1) * A_BYTES + 32 * j);
-              const uint64_t db = smem_desc64(sb + (t - 1) * B_BYTES + 32 * j);
-              // digit planes: one accumulator per diagonal s + t; plain forms: one for all
-              const uint32_t col = PLAIN ? 0u : (uint32_t)(s + t - 2) * BN;
-              const uint32_t accum = (c == 0 && j == 0 && s == 1 && (!PLAIN || t == 1)) ? 0u : 1u;
-              if constexpr (TF)
-                umma_tf32(tmem + col, da, db, accum);
-              else
-                umma(tmem + col, da, db, accum);
-            }
-        umma_commit(&empty[st]);
-        if (c == G - 1 || i == nsteps - 1) umma_commit(&tfull);
       }
       // after a failure: wait until every MMA this thread issued has completed (they read the
       // shared-memory stages and write TMEM)
@@ -569,52 +610,72 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
       }
     }
   } else {
-    for (int gi = 0; gi < ngroups; ++gi) {
-      bool ok = !abort_flag && mbar_wait(&tfull, gi & 1, WAIT_NS, &abort_flag);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) {
-        abort_flag = 1;
-        failed = true;
-        break;
-      }
-      tc_fence_after();
-      if constexpr (!PLAIN) {
+    const int quad = warp & 3, half = warp >> 2;   // TMEM lane quadrant, column half
+    double *stg = stage_out + (size_t)warp * 32 * SPITCH;
+    long long g = 0;   // flush groups drained (all tiles)
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const Tile tl = tiles[t];
+      const Entry en = entries[tl.e];
+      int kbeg;
+      const int nsteps = steps_of(en, tl, kbeg);
+      const int ngroups = (nsteps + G - 1) / G;
+      const int m0 = tl.m0, n0 = tl.n0;
+      long long acc[HALF];       // digit planes: exact int64 sums of the diagonals
+      uint32_t fa[PLAIN ? HALF : 1];   // plain forms: the FP32 accumulators
+#pragma unroll
+      for (int j = 0; j < HALF; ++j) acc[j] = 0;
+      bool ok_all = true;
+      for (int gi = 0; gi < ngroups; ++gi, ++g) {
+        bool ok = !abort_flag && mbar_wait(&tfull, (uint32_t)(g & 1), WAIT_NS, &abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+          abort_flag = 1;
+          ok_all = false;
+          break;
+        }
+        tc_fence_after();
+        if constexpr (!PLAIN) {
 #pragma unroll 1
-        for (int d = 2; d <= S + 1; ++d) {
-          const long long mul = 1LL << (8 * (S + 1 - d));
+          for (int d = 2; d <= S + 1; ++d) {
+            const long long mul = 1LL << (8 * (S + 1 - d));
+#pragma unroll
+            for (int cb = 0; cb < HALF / 16; ++cb) {
+              uint32_t r[16];
+              tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d - 2) * BN + half * HALF + cb * 16, r);
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) * mul;
+            }
+          }
+        } else {
 #pragma unroll
           for (int cb = 0; cb < HALF / 16; ++cb) {
             uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d - 2) * BN + half * HALF + cb * 16, r);
+            tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + half * HALF + cb * 16, r);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) * mul;
+            for (int j = 0; j < 16; ++j) fa[cb * 16 + j] = r[j];
           }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty);
+        if (lane == 0) mbar_arrive(&tempty);   // the accumulators may be overwritten now
       }
-    }
-    if (!failed) {
+      if (!ok_all) break;
       // Values are formed with thread = tile row (the TMEM lane layout).  Row-major outputs
-      // (modes 0, 1, 3) go through a per-warp staging area in shared memory (the pipeline's stages,
-      // idle once the last MMA completed) and are written with lane = column, so that each warp
-      // store covers consecutive addresses; the transposed complex output (mode 2) is already
-      // consecutive along rows and is stored directly.
-      const int rl = 32 * quad + lane, row = m0 + rl;
+      // (modes 0, 1, 3) go through a per-warp staging area, 16 columns at a time, and are written
+      // with lanes along the row (two rows of 16 columns per warp store); the transposed complex
+      // output (mode 2) is consecutive along rows already and is stored directly.
+      const int row = m0 + 32 * quad + lane;
       const bool row_ok = row < en.M;
-      const int ea = (!PLAIN && row_ok) ? expoA[en.a_row0 + row] : 0;
+      const int ea = (!PLAIN && row_ok) ? maps[en.pair].ea[en.a_row0 + row] : 0;
+      const int *eb = maps[en.pair].eb;
       const int cbase = n0 + half * HALF;
       const bool pow2 = en.alpha_shift != kNoShift;   // alpha = +-2^alpha_shift: folded into the exponent
       const int ash = pow2 ? en.alpha_shift : 0;
       const bool aneg = pow2 && en.alpha < 0.0;
       const bool staged = en.mode != 2;
-      constexpr int PITCH = HALF + 1;
-      double *stg = reinterpret_cast<double *>(smem) + (size_t)warp * 32 * PITCH;
 #pragma unroll
       for (int cb = 0; cb < HALF / 16; ++cb) {
-        uint32_t r[16];
-        if constexpr (PLAIN) tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + half * HALF + cb * 16, r);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int c = cb * 16 + j, col = cbase + c;
@@ -623,16 +684,15 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
           float2 pr = make_float2(0.f, 0.f);
           if (ok) {
             if constexpr (PLAIN) {
-              if (nsteps > 0) v = f32_to_f64(__uint_as_float(r[j]), ash);
+              if (nsteps > 0) v = f32_to_f64(__uint_as_float(fa[c]), ash);
               if (aneg) v = -v;
               if (!pow2) v *= en.alpha;
               if (en.mode == 3) {
-                pr.x = __double2float_rn(v);   // exact: a rounded FP32 sum times +-1
-                pr.y = 0.f;
+                pr.x = __double2float_rn(v);   // exact: a rounded FP32 sum times +-2^k
                 if (!pow2) pr.y = __double2float_rn(v - (double)pr.x);
               }
             } else {
-              const int sh = ea + expoB[en.b_row0 + col] - 14 - 8 * (S - 1) + ash;
+              const int sh = ea + eb[en.b_row0 + col] - 14 - 8 * (S - 1) + ash;
               const long long a = aneg ? -acc[c] : acc[c];
               if (en.mode == 3 && pow2) {
                 pr = i64_to_f32x2(a, sh);
@@ -646,34 +706,33 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
               }
             }
           }
-          if (en.mode == 3) v = __longlong_as_double((long long)(((unsigned long long)__float_as_uint(pr.y) << 32) |
-                                                                 __float_as_uint(pr.x)));
+          if (en.mode == 3)
+            v = __longlong_as_double(
+                (long long)(((unsigned long long)__float_as_uint(pr.y) << 32) | __float_as_uint(pr.x)));
           if (staged) {
-            stg[lane * PITCH + c] = v;
+            stg[lane * SPITCH + j] = v;
           } else if (ok) {
             double *p = en.C + 2 * ((long long)col * en.ldc + (row >> 1)) + (row & 1);
             *p = en.beta == 0.0 ? v : v + en.beta * *p;
           }
         }
-      }
-      if (staged) {
-        __syncwarp();
-        for (int rr = 0; rr < 32; ++rr) {
-          const int grow = m0 + 32 * quad + rr;
-          if (grow >= en.M) break;
-#pragma unroll
-          for (int c0 = 0; c0 < HALF; c0 += 32) {
-            const int c = c0 + lane, col = cbase + c;
-            if (col >= en.N) continue;
-            const double v = stg[rr * PITCH + c];
-            if (en.mode == 3) {   // the 8 bytes already hold the pair (hi, lo)
-              reinterpret_cast<double *>(en.C)[(long long)grow * en.ldc + col] = v;
-              continue;
+        if (staged) {
+          __syncwarp();
+          const int cl = lane & 15, col = cbase + cb * 16 + cl;
+          for (int rr = lane >> 4; rr < 32; rr += 2) {
+            const int grow = m0 + 32 * quad + rr;
+            if (grow < en.M && col < en.N) {
+              const double v = stg[rr * SPITCH + cl];
+              if (en.mode == 3) {   // the 8 bytes already hold the pair (hi, lo)
+                reinterpret_cast<double *>(en.C)[(long long)grow * en.ldc + col] = v;
+              } else {
+                double *p = en.mode == 0 ? en.C + (long long)grow * en.ldc + col
+                                         : en.C + 2 * ((long long)(grow >> 1) * en.ldc + col) + (grow & 1);
+                *p = en.beta == 0.0 ? v : v + en.beta * *p;
+              }
             }
-            double *p = en.mode == 0 ? en.C + (long long)grow * en.ldc + col
-                                     : en.C + 2 * ((long long)(grow >> 1) * en.ldc + col) + (grow & 1);
-            *p = en.beta == 0.0 ? v : v + en.beta * *p;
           }
+          __syncwarp();
         }
       }
     }
@@ -704,15 +763,12 @@ CUtensorMap make_map(const Sliced &o, int box_rows) {
 }
 
 template <int S>
-void launch(const CUtensorMap &ma, const CUtensorMap &mb, const Entry *e, const Tile *t, unsigned ntiles,
-            const int *ea, const int *eb, int *err, uint64_t stall_ns, cudaStream_t s) {
-  // the pipeline's stages, large enough to hold the epilogue's staging area (32 rows x (HALF + 1)
-  // doubles per epilogue warp) once the mainloop is done
-  const int ring = NST * planes(S) * (BM + BN) * 64;
-  const int stage_out = epi_warps(S) * 32 * (BN * 4 / epi_warps(S) + 1) * 8;
-  const int smem = std::max(ring, stage_out) + 1024;
+void launch(const MapPair *mp, const Entry *e, const Tile *t, const int *c, int ntiles, int grid, int *err,
+            uint64_t stall_ns, cudaStream_t s) {
+  // the pipeline's stages, then the epilogue's staging area (32 rows x 17 doubles per epilogue warp)
+  const int smem = NST * planes(S) * (BM + BN) * 64 + epi_warps(S) * 32 * 17 * 8 + 1024;
   LR_CUDA(cudaFuncSetAttribute(k_ozgemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k_ozgemm<S><<<ntiles, 32 * (epi_warps(S) + 2), smem, s>>>(ma, mb, e, t, ea, eb, err, stall_ns);
+  k_ozgemm<S><<<grid, 32 * (epi_warps(S) + 2), smem, s>>>(mp, e, t, c, ntiles, err, stall_ns);
 }
 
 }  // namespace
@@ -768,70 +824,120 @@ void split_ragged(const double *base, const long long *off, const int *Ke, int r
   split_any(r, rows_per_entry * n_entries, Kmax, 0, out, s);
 }
 
-long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry> &entries, int *err,
-                       cudaStream_t s, Handle &h, DevBuf &args) {
-  if (a.S != b.S || a.S < 0 || (a.S > SMAX && a.S != S_TF32 && a.S != S_TF32X3))
-    throw Error{LIBRPA_E_ARG, "oz::gemm: operand mismatch"};
+long long gemm_multi(const std::vector<std::pair<const Sliced *, const Sliced *>> &ops, const std::vector<Entry> &entries,
+                     int *err, cudaStream_t s, Handle &h, DevBuf &args, const StageFn *stage_fn) {
+  if (ops.empty()) return 0;
+  const int S = ops[0].first->S;
+  for (const auto &o : ops)
+    if (o.first->S != S || o.second->S != S || S < 0 || (S > SMAX && S != S_TF32 && S != S_TF32X3))
+      throw Error{LIBRPA_E_ARG, "oz::gemm: operand mismatch"};
   init();
-  std::vector<Tile> tiles;
-  // MMA flops issued: per tile BM x BN x (K rounded up to the K step) per digit-plane product
-  const double prods = (a.S == 0 || a.S == S_TF32) ? 1.0 : a.S == S_TF32X3 ? 3.0 : a.S * (a.S + 1) / 2.0;
-  const int ks = elem_bytes(a.S) == 4 ? PBK / 2 : PBK;   // K elements per pipeline stage
+  // tiles with their K range in stages; MMA flops issued: per tile BM x BN x (K rounded up to the
+  // K step) per digit-plane product
+  const double prods = (S == 0 || S == S_TF32) ? 1.0 : S == S_TF32X3 ? 3.0 : S * (S + 1) / 2.0;
+  const int ks = elem_bytes(S) == 4 ? PBK / 2 : PBK;   // K elements per pipeline stage
+  std::vector<std::pair<int, Tile>> tk;
+  std::vector<int> chunks, cl;
   double exec = 0;
   h.oz_exec_flops = 0;
+  h.oz_alg_flops = 0;
   for (int e = 0; e < (int)entries.size(); ++e) {
     const Entry &en = entries[e];
     if (en.M <= 0 || en.N <= 0) continue;
+    if (en.pair < 0 || en.pair >= (int)ops.size()) throw Error{LIBRPA_E_ARG, "oz::gemm: entry without operands"};
+    const Sliced &a = *ops[en.pair].first, &b = *ops[en.pair].second;
     if (en.K > a.kpad || en.K > b.kpad || en.a_row0 < 0 || en.b_row0 < 0 || en.a_row0 + en.M > a.rows ||
         en.b_row0 + en.N > b.rows)
       throw Error{LIBRPA_E_ARG, "oz::gemm: entry outside its operands"};
     for (int m0 = 0; m0 < en.M; m0 += BM)
       for (int n0 = 0; n0 < en.N; n0 += BN) {
         if (en.lower_div > 0 && n0 > m0 / en.lower_div) continue;
-        tiles.push_back({e, m0, n0});
+        const int rows = std::min(BM, en.M - m0), cols = std::min(BN, en.N - n0);
+        cl.clear();
+        if (stage_fn && (*stage_fn)(e, m0, rows, n0, cols, ks, en.K, cl)) {
+          double kk = 0;
+          for (int c : cl) kk += std::min(ks, en.K - c * ks);
+          h.oz_alg_flops += 2.0 * rows * cols * kk;
+          tk.push_back({(int)cl.size(), Tile{e, m0, n0, (int)chunks.size(), (int)cl.size()}});
+          chunks.insert(chunks.end(), cl.begin(), cl.end());
+          exec += 2.0 * BM * BN * (double)cl.size() * ks * prods;
+          continue;
+        }
         const int kbeg = (m0 * en.km + n0 * en.kn) / ks * ks;   // as in the kernel
-        if (en.K > kbeg) exec += 2.0 * BM * BN * (double)((en.K - kbeg + ks - 1) / ks * ks) * prods;
+        const int nst = en.K > kbeg ? (en.K - kbeg + ks - 1) / ks : 0;
+        tk.push_back({nst, Tile{e, m0, n0, 0, -1}});
+        h.oz_alg_flops += 2.0 * rows * cols * std::max(0, en.K - kbeg);
+        exec += 2.0 * BM * BN * (double)nst * ks * prods;
       }
   }
-  if (tiles.empty()) return 0;
-  const size_t b1 = entries.size() * sizeof(Entry), off2 = (b1 + 255) / 256 * 256, b2 = tiles.size() * sizeof(Tile);
-  std::vector<char> host(off2 + b2);
-  std::memcpy(host.data(), entries.data(), b1);
+  if (tk.empty()) return 0;
+  // the longest K ranges first: CTAs take tiles round-robin, so this evens out their work
+  std::stable_sort(tk.begin(), tk.end(), [](const std::pair<int, Tile> &x, const std::pair<int, Tile> &y) {
+    return x.first > y.first;
+  });
+  std::vector<MapPair> mp(ops.size());
+  for (size_t i = 0; i < ops.size(); ++i) {
+    mp[i].a = make_map(*ops[i].first, BM);
+    mp[i].b = make_map(*ops[i].second, BN);
+    mp[i].ea = ops[i].first->expo;
+    mp[i].eb = ops[i].second->expo;
+  }
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b0 = mp.size() * sizeof(MapPair), off1 = al(b0), b1 = entries.size() * sizeof(Entry),
+               off2 = off1 + al(b1), b2 = tk.size() * sizeof(Tile), off3 = off2 + al(b2),
+               b3 = std::max<size_t>(1, chunks.size()) * sizeof(int);
+  std::vector<char> host(off3 + b3);
+  std::memcpy(host.data(), mp.data(), b0);
+  std::memcpy(host.data() + off1, entries.data(), b1);
   // alpha = +-2^k goes into the epilogue's exponent arithmetic (every GEMM of the path), other
   // values are multiplied in FP64
   for (size_t e = 0; e < entries.size(); ++e) {
-    Entry &en = reinterpret_cast<Entry *>(host.data())[e];
+    Entry &en = reinterpret_cast<Entry *>(host.data() + off1)[e];
     int ex = 0;
     const double fr = std::frexp(std::fabs(en.alpha), &ex);
     en.alpha_shift = (en.alpha != 0.0 && fr == 0.5) ? ex - 1 : kNoShift;
   }
-  std::memcpy(host.data() + off2, tiles.data(), b2);
-  h.ensure(args, off2 + b2);
-  LR_CUDA(cudaMemcpyAsync(args.p, host.data(), off2 + b2, cudaMemcpyHostToDevice, s));
-  const Entry *de = (const Entry *)args.p;
+  Tile *ht = reinterpret_cast<Tile *>(host.data() + off2);
+  for (size_t i = 0; i < tk.size(); ++i) ht[i] = tk[i].second;
+  if (!chunks.empty()) std::memcpy(host.data() + off3, chunks.data(), chunks.size() * sizeof(int));
+  h.ensure(args, off3 + b3);
+  LR_CUDA(cudaMemcpyAsync(args.p, host.data(), off3 + b3, cudaMemcpyHostToDevice, s));
+  LR_CUDA(cudaStreamSynchronize(s));   // the host staging goes out of scope
+  const MapPair *dm = (const MapPair *)args.p;
+  const Entry *de = (const Entry *)((const char *)args.p + off1);
   const Tile *dt = (const Tile *)((const char *)args.p + off2);
-  const CUtensorMap ma = make_map(a, BM), mb = make_map(b, BN);
-  const unsigned nt = (unsigned)tiles.size();
+  const int *dc = (const int *)((const char *)args.p + off3);
+  // One CTA per tile: measured on GB300, these GEMMs (short K, many tiles) run faster with the tiles
+  // spread over as many CTAs as fit on an SM than with one persistent CTA per SM, which leaves the
+  // TMA loads and the epilogue of a single CTA exposed; the tile loop then runs once per CTA.
+  const int nt = (int)tk.size(), grid = nt;
   // testing only: the handle's first opts.test_stall_gemms launches take the failure path
   uint64_t stall = 0;
   if (h.stalls_left > 0) {
     --h.stalls_left;
-    stall = 100000;   // 100 us per tile
+    stall = 100000;   // 100 us per CTA
   }
-  switch (a.S) {
-    case 0: launch<0>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
-    case 1: launch<1>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
-    case 2: launch<2>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
-    case 3: launch<3>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
-    case 4: launch<4>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
-    case S_TF32: launch<S_TF32>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
-    case S_TF32X3: launch<S_TF32X3>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
-    default: launch<5>(ma, mb, de, dt, nt, a.expo, b.expo, err, stall, s); break;
+  switch (S) {
+    case 0: launch<0>(dm, de, dt, dc, nt, grid, err, stall, s); break;
+    case 1: launch<1>(dm, de, dt, dc, nt, grid, err, stall, s); break;
+    case 2: launch<2>(dm, de, dt, dc, nt, grid, err, stall, s); break;
+    case 3: launch<3>(dm, de, dt, dc, nt, grid, err, stall, s); break;
+    case 4: launch<4>(dm, de, dt, dc, nt, grid, err, stall, s); break;
+    case S_TF32: launch<S_TF32>(dm, de, dt, dc, nt, grid, err, stall, s); break;
+    case S_TF32X3: launch<S_TF32X3>(dm, de, dt, dc, nt, grid, err, stall, s); break;
+    default: launch<5>(dm, de, dt, dc, nt, grid, err, stall, s); break;
   }
   ++launch_counter();
   LR_CUDA(cudaGetLastError());
   h.oz_exec_flops = exec;
-  return (long long)tiles.size();
+  return nt;
+}
+
+long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry> &entries, int *err,
+                       cudaStream_t s, Handle &h, DevBuf &args, const StageFn *stage_fn) {
+  std::vector<Entry> es(entries);
+  for (Entry &e : es) e.pair = 0;
+  return gemm_multi({{&a, &b}}, es, err, s, h, args, stage_fn);
 }
 
 long long gemm(const Sliced &a, const Sliced &b, int M, int N, int batch, const Out &out, int km, int kn,

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <functional>
+#include <utility>
 #include <vector>
 
 namespace librpa {
@@ -99,14 +101,25 @@ struct Entry {
   long long ldc;
   int mode;
   double alpha, beta;
-  int alpha_shift;   // set by gemm_grouped: k when alpha = +-2^k, else kNoShift
+  int alpha_shift;   // set by the launch: k when alpha = +-2^k, else kNoShift
+  int pair;          // gemm_multi: index of the entry's operand pair (gemm_grouped sets 0)
 };
+
+// K stages a tile of entry e must sum (block-sparse operands): stage_fn(e, m0, rows, n0, cols, stage K,
+// K, out) appends the needed stage indices (ascending) and returns true, or returns false for all.
+using StageFn = std::function<bool(int, int, int, int, int, int, int, std::vector<int> &)>;
 
 // Grouped launch over all tiles of all entries; operand digit planes of the A role in `a`, of
 // the B role in `b` (same S).  `err` (device int) is set to 1 if a bounded wait runs out.
-// `args` is scratch for the descriptor upload.  Returns the number of tiles.
+// `args` is scratch for the descriptor upload.  Returns the number of tiles.  Sets
+// h.oz_exec_flops (MMA flops issued) and h.oz_alg_flops (2 M N K over the summed K).
 long long gemm_grouped(const Sliced &a, const Sliced &b, const std::vector<Entry> &entries, int *err,
-                       cudaStream_t s, Handle &h, DevBuf &args);
+                       cudaStream_t s, Handle &h, DevBuf &args, const StageFn *stage_fn = nullptr);
+
+// The same over several operand pairs (same S): entry e multiplies ops[e.pair].first (A role) by
+// ops[e.pair].second (B role).  All tiles of all entries run in one persistent launch.
+long long gemm_multi(const std::vector<std::pair<const Sliced *, const Sliced *>> &ops, const std::vector<Entry> &entries,
+                     int *err, cudaStream_t s, Handle &h, DevBuf &args, const StageFn *stage_fn = nullptr);
 
 // Uniform batch: A rows m in [0, M) of entry b are rows b * M .. of `a`, B rows likewise with N;
 // an operand with exactly M (N) rows is shared by all entries.

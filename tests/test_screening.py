@@ -148,3 +148,23 @@ def test_set_screening_arguments():
         L.librpa_gpu_set_screening(h, 0.0)
     finally:
         L.librpa_gpu_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [L.LIBRPA_FP64, L.LIBRPA_FP64_TC])
+def test_block_sparse_work_follows_the_kept_blocks(precision):
+    """Inside a contracted point the GEMM tiles sum only the K chunks that meet kept G blocks and the
+    O blocks without a kept contribution are zeros: the algorithmic work falls below that of the
+    contracted points done densely, while the result stays the oracle's on the screened G."""
+    inp = CONFIGS["cubic_3x3x1"]()
+    grid = _grid("cubic_3x3x1", inp)
+    theta = 1e-2   # about a quarter of the G blocks kept
+    ref = pipeline.rpa_energy(inp, grid, screen=theta)
+    full = _run(inp, grid, opts=_opts(precision))
+    scr = _run(inp, grid, opts=_opts(precision), screening=theta)
+    per_point = full["stats"]["flop_chi0"] / full["stats"]["n_points_chi0"]
+    dense_on_points = per_point * scr["stats"]["n_points_chi0"]
+    frac = scr["stats"]["flop_chi0"] / dense_on_points
+    print("block-sparse chi0 work: %.3f of the contracted points done densely (%s)" % (frac, precision))
+    assert frac < 0.9
+    assert _rel(scr["chi_tau"], ref["chi_tau"]) < TOL_CHI
+    assert abs(scr["ec"] - ref["ec"]) < TOL_EC
