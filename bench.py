@@ -55,7 +55,7 @@ TRAFFIC = {
     # Gamma case of the graphene slab, one (R, tau) point per launch as at 4x4x1: N/X group 0.681 GB,
     # final contraction 1.225 GB, averaged (profiles/k_dgemm_nt_dram_graphene_gamma.md)
     "k_dgemm_nt": {"bytes_per_launch": 0.953e9, "src": "paper_2407_19930_gb300/csrc/k_chi0.cu",
-                   "begin": "template <int WM, int WN>", "end": "// tile variants {WM, WN}", "src_sha": "d413a0b3da389a16"},
+                   "begin": "template <int WM, int WN>", "end": "// tile variants {WM, WN}", "src_sha": "431079ebc2084c1e"},
 }
 
 

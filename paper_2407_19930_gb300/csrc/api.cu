@@ -68,6 +68,41 @@ void Handle::release(DevBuf &b) {
   b.bytes = 0;
 }
 
+void Handle::upload_async(DevBuf &dst, const void *src, size_t bytes) {
+  ensure(dst, std::max<size_t>(bytes, 1));
+  if (!bytes) return;
+  const size_t need = (bytes + 255) / 256 * 256;
+  if (need > pin_bytes) {   // grow: wait for every copy from the old ring, then replace it
+    if (pin_done) LR_CUDA(cudaEventSynchronize(pin_done));
+    if (pin) cudaFreeHost(pin);
+    pin = nullptr;
+    pin_bytes = std::max(need, (size_t)32 << 20);
+    LR_CUDA(cudaMallocHost(&pin, pin_bytes));
+    pin_head = 0;
+  } else if (pin_head + need > pin_bytes || (pin_stream && pin_stream != stream)) {
+    if (pin_done) LR_CUDA(cudaEventSynchronize(pin_done));
+    pin_head = 0;
+  }
+  if (!pin_done) LR_CUDA(cudaEventCreateWithFlags(&pin_done, cudaEventDisableTiming));
+  std::memcpy(pin + pin_head, src, bytes);
+  LR_CUDA(cudaMemcpyAsync(dst.p, pin + pin_head, bytes, cudaMemcpyHostToDevice, stream));
+  LR_CUDA(cudaEventRecord(pin_done, stream));
+  pin_stream = stream;
+  pin_head += need;
+}
+
+void Handle::free_pinned() {
+  if (pin_done) {
+    cudaEventSynchronize(pin_done);
+    cudaEventDestroy(pin_done);
+  }
+  if (pin) cudaFreeHost(pin);
+  pin = nullptr;
+  pin_done = nullptr;
+  pin_bytes = pin_head = 0;
+  pin_stream = nullptr;
+}
+
 void Handle::resolve_timers() {
   for (auto &t : timed) {
     float ms = 0;
@@ -709,6 +744,7 @@ void librpa_gpu_destroy(librpa_gpu_t h) {
       cudaFree(kv.first);
   }
   h->allocs.clear();
+  h->free_pinned();
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }

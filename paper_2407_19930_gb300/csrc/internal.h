@@ -181,6 +181,16 @@ struct Handle {
   void dfree(void *p);
   void ensure(DevBuf &b, size_t bytes);
   void release(DevBuf &b);
+  // Host -> device upload of small tables (launch descriptors, tile and point lists) through a
+  // pinned staging ring, so the copy is asynchronous: a copy from pageable memory would first
+  // synchronise the stream and leave the GPU idle between launches.  The ring is reused after the
+  // last copy from it has completed (an event), at a wrap or a change of stream.
+  void upload_async(DevBuf &dst, const void *src, size_t bytes);
+  void free_pinned();
+  char *pin = nullptr;
+  size_t pin_bytes = 0, pin_head = 0;
+  cudaEvent_t pin_done = nullptr;
+  cudaStream_t pin_stream = nullptr;
 };
 
 // ----------------------------------------------------------------- grid (host, grid.cpp)

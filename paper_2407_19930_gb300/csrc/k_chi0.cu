@@ -421,9 +421,7 @@ DLaunch dgemm_prepare(Handle &h, const std::vector<DGemm> &batch, int v, cudaStr
   std::memcpy(host.data(), batch.data(), b1);
   std::memcpy(host.data() + off2, tiles.data(), b2);
   if (!chunks.empty()) std::memcpy(host.data() + off3, chunks.data(), chunks.size() * sizeof(int));
-  h.ensure(args, off3 + b3);
-  LR_CUDA(cudaMemcpyAsync(args.p, host.data(), off3 + b3, cudaMemcpyHostToDevice, s));
-  LR_CUDA(cudaStreamSynchronize(s));   // the host staging goes out of scope
+  h.upload_async(args, host.data(), off3 + b3);
   L.g = (const DGemm *)args.p;
   L.t = (const DTile *)((const char *)args.p + off2);
   L.c = (const int *)((const char *)args.p + off3);
@@ -1233,8 +1231,7 @@ void chi0_run_tc(Handle &h) {
     for (long long p0 = 0; p0 < total_pts; p0 += npb) {
       const int np = (int)std::min(npb, total_pts - p0);
       std::vector<Point> pts(sel.pts.begin() + p0, sel.pts.begin() + p0 + np);
-      h.ensure(P.t_pts, np * sizeof(Point));
-      LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
+      h.upload_async(P.t_pts, pts.data(), np * sizeof(Point));
       // digit planes of the gathered Green's-function operands, straight from G
       oz::GatherSrc gs;
       gs.kind = 0;
@@ -1313,7 +1310,7 @@ void chi0_run_tc(Handle &h) {
       if (scr) {
         double fo = 0;
         zf = ozero_flags(h, B, oasm_chunks(h), &fo);
-        upload(h, P.t_ozero, zf);
+        h.upload_async(P.t_ozero, zf.data(), zf.size());
         h.flop_chi0_run += fo;
       } else {
         h.flop_chi0_run += np * (P.flop_per_point - P.flop_nx_per_point - P.flop_fin_per_point);
@@ -1328,12 +1325,9 @@ void chi0_run_tc(Handle &h) {
             off[q * nat + U] = (long long)q * P.o_sz + P.o_off[U];
             ke[q * nat + U] = h.n_ao[U] * P.m[U];
           }
-        h.ensure(P.t_oe_off, off.size() * 8);
-        h.ensure(P.t_oe_k, ke.size() * 4);
-        LR_CUDA(cudaMemcpyAsync(P.t_oe_off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s));
-        LR_CUDA(cudaMemcpyAsync(P.t_oe_k.p, ke.data(), ke.size() * 4, cudaMemcpyHostToDevice, s));
+        h.upload_async(P.t_oe_off, off.data(), off.size() * 8);
+        h.upload_async(P.t_oe_k, ke.data(), ke.size() * 4);
         oz::split_ragged(Ow, (const long long *)P.t_oe_off.p, (const int *)P.t_oe_k.p, naux, np * nat, P.max_nm, sod, s);
-        LR_CUDA(cudaStreamSynchronize(s));   // the host tables above are temporaries
       }
       std::vector<oz::Entry> ef;
       for (int q = 0; q < np; ++q) {
@@ -1392,8 +1386,7 @@ void chi0_run(Handle &h, double *ms_gemm) {
     for (long long p0 = 0; p0 < total_pts; p0 += npb) {
       const int np = (int)std::min(npb, total_pts - p0);
       std::vector<Point> pts(sel.pts.begin() + p0, sel.pts.begin() + p0 + np);
-      h.ensure(P.t_pts, np * sizeof(Point));
-      LR_CUDA(cudaMemcpyAsync(P.t_pts.p, pts.data(), np * sizeof(Point), cudaMemcpyHostToDevice, s));
+      h.upload_async(P.t_pts, pts.data(), np * sizeof(Point));
       const Point *dpts = (const Point *)P.t_pts.p;
       fp64_gather(h, dpts, np, w);
       std::vector<DGemm> b1, b2;
@@ -1427,7 +1420,7 @@ void chi0_run(Handle &h, double *ms_gemm) {
       h.flop_chi0_run += dgemm_batched(h, b1, s, P.gargs1, &P.var_nx, &fnx);
       double fo = 0;
       const std::vector<unsigned char> zf = ozero_flags(h, B, oasm_chunks(h), &fo);
-      upload(h, P.t_ozero, zf);
+      h.upload_async(P.t_ozero, zf.data(), zf.size());
       run_oassemble(h, dpts, np, w.Nw, w.Xw, w.Ow, (const unsigned char *)P.t_ozero.p);
       h.flop_chi0_run += fo;
       fp64_final(h, pts, w, b2);

@@ -477,7 +477,7 @@ struct alignas(128) MapPair {
 template <int S>
 __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
     k_ozgemm(const MapPair *__restrict__ maps, const Entry *__restrict__ entries, const Tile *__restrict__ tiles,
-             const int *__restrict__ chunks, int ntiles, int *err, uint64_t stall_ns) {
+             const int *__restrict__ chunks, int ntiles, int *err, uint64_t stall_ns, int stage_in_ring) {
   constexpr bool TF = S == S_TF32 || S == S_TF32X3;   // kind::tf32
   constexpr bool PLAIN = S == 0 || TF;                 // one FP32 accumulator over all K
   constexpr int NP = S == S_TF32X3 ? 2 : PLAIN ? 1 : S;   // planes per operand
@@ -496,7 +496,9 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  double *stage_out = reinterpret_cast<double *>(smem + NST * STAGE);
+  // the epilogue's staging area: in the pipeline's stages when the CTA has a single tile (they are
+  // idle once its last MMA completed), else after them
+  double *stage_out = reinterpret_cast<double *>(stage_in_ring ? smem : smem + NST * STAGE);
   if (tid == 0) {
 #pragma unroll
     for (int s = 0; s < NST; ++s) {
@@ -765,10 +767,14 @@ CUtensorMap make_map(const Sliced &o, int box_rows) {
 template <int S>
 void launch(const MapPair *mp, const Entry *e, const Tile *t, const int *c, int ntiles, int grid, int *err,
             uint64_t stall_ns, cudaStream_t s) {
-  // the pipeline's stages, then the epilogue's staging area (32 rows x 17 doubles per epilogue warp)
-  const int smem = NST * planes(S) * (BM + BN) * 64 + epi_warps(S) * 32 * 17 * 8 + 1024;
+  // the pipeline's stages and the epilogue's staging area (32 rows x 17 doubles per epilogue warp),
+  // overlapping when every CTA has one tile (the shared memory, and so the CTAs an SM holds at
+  // once, stay those of the stages alone)
+  const int ring = NST * planes(S) * (BM + BN) * 64, staging = epi_warps(S) * 32 * 17 * 8;
+  const int in_ring = grid >= ntiles ? 1 : 0;
+  const int smem = (in_ring ? std::max(ring, staging) : ring + staging) + 1024;
   LR_CUDA(cudaFuncSetAttribute(k_ozgemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k_ozgemm<S><<<grid, 32 * (epi_warps(S) + 2), smem, s>>>(mp, e, t, c, ntiles, err, stall_ns);
+  k_ozgemm<S><<<grid, 32 * (epi_warps(S) + 2), smem, s>>>(mp, e, t, c, ntiles, err, stall_ns, in_ring);
 }
 
 }  // namespace
@@ -900,9 +906,8 @@ long long gemm_multi(const std::vector<std::pair<const Sliced *, const Sliced *>
   Tile *ht = reinterpret_cast<Tile *>(host.data() + off2);
   for (size_t i = 0; i < tk.size(); ++i) ht[i] = tk[i].second;
   if (!chunks.empty()) std::memcpy(host.data() + off3, chunks.data(), chunks.size() * sizeof(int));
-  h.ensure(args, off3 + b3);
-  LR_CUDA(cudaMemcpyAsync(args.p, host.data(), off3 + b3, cudaMemcpyHostToDevice, s));
-  LR_CUDA(cudaStreamSynchronize(s));   // the host staging goes out of scope
+  if (s != h.stream) throw Error{LIBRPA_E_ARG, "oz::gemm: launch on a stream other than the handle's"};
+  h.upload_async(args, host.data(), off3 + b3);
   const MapPair *dm = (const MapPair *)args.p;
   const Entry *de = (const Entry *)((const char *)args.p + off1);
   const Tile *dt = (const Tile *)((const char *)args.p + off2);
