@@ -976,6 +976,22 @@ BlockSparse block_sparse(const Handle &h, const std::vector<Point> &pts) {
   return B;
 }
 
+// chunk lists computed once per (entry, tile row or column, chunk size) and reused by the other tiles
+// that share them
+struct ChunkMemo {
+  std::map<std::tuple<int, int, int>, std::vector<int>> m;
+  template <class F>
+  void get(int e, int pos, int cs, std::vector<int> &out, F &&make) {
+    auto it = m.find(std::make_tuple(e, pos, cs));
+    if (it == m.end()) {
+      std::vector<int> v;
+      make(v);
+      it = m.emplace(std::make_tuple(e, pos, cs), std::move(v)).first;
+    }
+    out.insert(out.end(), it->second.begin(), it->second.end());
+  }
+};
+
 // the needed chunks of [0, K) in units of cs, given which of `blocks` (start, width) are live
 void chunks_from_blocks(const std::vector<std::pair<int, int>> &blocks, const std::vector<char> &live, int cs, int K,
                         std::vector<int> &out) {
@@ -1026,27 +1042,33 @@ void chunks_x(const Handle &h, const BlockSparse &B, int q, int g, int V, int m0
   chunks_from_blocks(blocks, live, cs, K, out);
 }
 
-// final-contraction tile of (q, U): columns nu in [n0, n0 + cols), K = (i, k) over U's n_U x m_U
+// final-contraction tile of (q, U): columns nu in [n0, n0 + cols), K = (i, k) over U's n_U x m_U.
+// Whether a K index is live depends on k only (its block of U's packed columns), so one prefix
+// count over the m_U columns answers every chunk.
 void chunks_f(const Handle &h, const BlockSparse &B, int q, int U, int n0, int cols, int cs, int K,
               std::vector<int> &out) {
   const Chi0Plan &P = h.plan;
   const std::vector<NbEntry> &nbU = P.nb[U];
   const int mU = P.m[U];
-  std::vector<char> liveb(nbU.size(), 0);
-  for (int b = 0; b < (int)nbU.size(); ++b)
-    for (int V = 0; V < B.nat; ++V)
-      if (h.aux_off[V] < n0 + cols && h.aux_off[V] + h.n_aux[V] > n0 && B.o[B.io(q, U, V, b)]) {
-        liveb[b] = 1;
-        break;
-      }
-  std::vector<std::pair<int, int>> blocks;
-  std::vector<char> live;
-  for (int i = 0; i < h.n_ao[U]; ++i)
-    for (int b = 0; b < (int)nbU.size(); ++b) {
-      blocks.push_back({i * mU + nbU[b].col, h.n_ao[nbU[b].K]});
-      live.push_back(liveb[b]);
+  std::vector<int> pre(mU + 1, 0);
+  for (int b = 0; b < (int)nbU.size(); ++b) {
+    bool live = false;
+    for (int V = 0; V < B.nat && !live; ++V)
+      live = h.aux_off[V] < n0 + cols && h.aux_off[V] + h.n_aux[V] > n0 && B.o[B.io(q, U, V, b)];
+    if (live)
+      for (int k = nbU[b].col; k < nbU[b].col + h.n_ao[nbU[b].K]; ++k) pre[k + 1] = 1;
+  }
+  for (int k = 0; k < mU; ++k) pre[k + 1] += pre[k];
+  auto live_in = [&](int lo, int hi) {   // any live column among K indices [lo, hi)
+    while (lo < hi) {
+      const int i = lo / mU, k0 = lo - i * mU, k1 = std::min(mU, hi - i * mU);
+      if (pre[k1] > pre[k0]) return true;
+      lo = (i + 1) * mU;
     }
-  chunks_from_blocks(blocks, live, cs, K, out);
+    return false;
+  };
+  for (int c = 0; c * cs < K; ++c)
+    if (live_in(c * cs, std::min(K, (c + 1) * cs))) out.push_back(c);
 }
 
 // O-assembly flags [q][U][V][64-column chunk]: 1 where the block is exactly zero; and the
@@ -1292,16 +1314,21 @@ void chi0_run_tc(Handle &h) {
       // contribution are written as zeros (see BlockSparse)
       BlockSparse B;
       if (scr) B = block_sparse(h, pts);
+      ChunkMemo memo_n, memo_x, memo_f;
       const oz::StageFn fn_n = [&](int e, int, int, int n0, int cols, int cs, int K, std::vector<int> &out) {
-        chunks_n(h, B, e / (2 * nat), (e / nat) % 2, e % nat, n0, cols, cs, K, out);
+        memo_n.get(e, n0, cs, out, [&](std::vector<int> &o) {
+          chunks_n(h, B, e / (2 * nat), (e / nat) % 2, e % nat, n0, cols, cs, K, o);
+        });
         return true;
       };
       const oz::StageFn fn_x = [&](int e, int m0, int rows, int, int, int cs, int K, std::vector<int> &out) {
-        chunks_x(h, B, e / (2 * nat), (e / nat) % 2, e % nat, m0, rows, cs, K, out);
+        memo_x.get(e, m0, cs, out, [&](std::vector<int> &o) {
+          chunks_x(h, B, e / (2 * nat), (e / nat) % 2, e % nat, m0, rows, cs, K, o);
+        });
         return true;
       };
       const oz::StageFn fn_f = [&](int e, int, int, int n0, int cols, int cs, int K, std::vector<int> &out) {
-        chunks_f(h, B, e / nat, e % nat, n0, cols, cs, K, out);
+        memo_f.get(e, n0, cs, out, [&](std::vector<int> &o) { chunks_f(h, B, e / nat, e % nat, n0, cols, cs, K, o); });
         return true;
       };
       h.flop_chi0_run += timed_grouped(h, cpnx, sbg, en, err, P.gargs1, scr ? &fn_n : nullptr);
@@ -1404,16 +1431,21 @@ void chi0_run(Handle &h, double *ms_gemm) {
       // no kept contribution are written as zeros
       const BlockSparse B = block_sparse(h, pts);
       const int nat = h.natoms;
+      // an N-step tile's chunks depend on its columns only, an X-step tile's on its rows, a final
+      // tile's on its columns: one list per (entry, tile column or row)
+      ChunkMemo memo_nx, memo_f;
       const ChunkFn fnx = [&](int e, int m0, int rows, int n0, int cols, int cs, int K, std::vector<int> &out) {
         const int r = e / 2, V = r % nat, g = (r / nat) % 2, q = r / (2 * nat);
-        if (e % 2 == 0)
-          chunks_n(h, B, q, g, V, n0, cols, cs, K, out);
-        else
-          chunks_x(h, B, q, g, V, m0, rows, cs, K, out);
+        memo_nx.get(e, e % 2 == 0 ? n0 : m0, cs, out, [&](std::vector<int> &o) {
+          if (e % 2 == 0)
+            chunks_n(h, B, q, g, V, n0, cols, cs, K, o);
+          else
+            chunks_x(h, B, q, g, V, m0, rows, cs, K, o);
+        });
         return true;
       };
       const ChunkFn ff = [&](int e, int, int, int n0, int cols, int cs, int K, std::vector<int> &out) {
-        chunks_f(h, B, e / nat, e % nat, n0, cols, cs, K, out);
+        memo_f.get(e, n0, cs, out, [&](std::vector<int> &o) { chunks_f(h, B, e / nat, e % nat, n0, cols, cs, K, o); });
         return true;
       };
       fp64_nx(h, np, w, b1, sel.nzN.data() + z, sel.nzX.data() + z);

@@ -663,7 +663,31 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
         if (lane == 0) mbar_arrive(&tempty);   // the accumulators may be overwritten now
       }
       if (!ok_all) break;
-      // Values are formed with thread = tile row (the TMEM lane layout).  Row-major outputs
+      if constexpr (PLAIN) {
+        // plain forms: one FP32 sum per element, scaled in FP64 and stored from the registers,
+        // thread = tile row
+        const int row = m0 + 32 * quad + lane;
+        if (row < en.M) {
+#pragma unroll
+          for (int c = 0; c < HALF; ++c) {
+            const int col = n0 + half * HALF + c;
+            if (col >= en.N) break;
+            const double v = nsteps > 0 ? en.alpha * (double)__uint_as_float(fa[c]) : 0.0;
+            if (en.mode == 3) {   // real, as an unevaluated pair of FP32 numbers (hi, lo)
+              const float hi = __double2float_rn(v);
+              reinterpret_cast<float2 *>(en.C)[(long long)row * en.ldc + col] =
+                  make_float2(hi, __double2float_rn(v - (double)hi));
+              continue;
+            }
+            double *p = en.mode == 0   ? en.C + (long long)row * en.ldc + col
+                        : en.mode == 1 ? en.C + 2 * ((long long)(row >> 1) * en.ldc + col) + (row & 1)
+                                       : en.C + 2 * ((long long)col * en.ldc + (row >> 1)) + (row & 1);
+            *p = en.beta == 0.0 ? v : v + en.beta * *p;
+          }
+        }
+        continue;
+      }
+      // Digit planes: values are formed with thread = tile row (the TMEM lane layout).  Row-major outputs
       // (modes 0, 1, 3) go through a per-warp staging area, 16 columns at a time, and are written
       // with lanes along the row (two rows of 16 columns per warp store); the transposed complex
       // output (mode 2) is consecutive along rows already and is stored directly.
@@ -685,15 +709,7 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
           double v = 0.0;
           float2 pr = make_float2(0.f, 0.f);
           if (ok) {
-            if constexpr (PLAIN) {
-              if (nsteps > 0) v = f32_to_f64(__uint_as_float(fa[c]), ash);
-              if (aneg) v = -v;
-              if (!pow2) v *= en.alpha;
-              if (en.mode == 3) {
-                pr.x = __double2float_rn(v);   // exact: a rounded FP32 sum times +-2^k
-                if (!pow2) pr.y = __double2float_rn(v - (double)pr.x);
-              }
-            } else {
+            {
               const int sh = ea + eb[en.b_row0 + col] - 14 - 8 * (S - 1) + ash;
               const long long a = aneg ? -acc[c] : acc[c];
               if (en.mode == 3 && pow2) {
