@@ -767,7 +767,8 @@ def run_batch(args):
         out[mode] = {"value": len(inputs) / t_batch, "ms_per_batch": 1e3 * t_batch,
                      "one_by_one": len(inputs) / t_one, "speedup": t_one / t_batch,
                      "max_rel_diff_vs_one_by_one": dmax, "repeat_identical": bool((ec0 == ec).all()),
-                     "n_merged": st["n_merged"], "graph": st["graph"], "tile_variants": [st["var_nx"], st["var_fin"]],
+                     "n_merged": st["n_merged"], "n_merged_tc": st["n_merged_tc"], "graph": st["graph"],
+                     "tile_variants": [st["var_nx"], st["var_fin"]],
                      "launches_per_batch": st["launches"],
                      "stage_ms": {"green": st["ms_green"], "chi0": st["ms_chi0"], "freq": st["ms_freq"],
                                   "ec": st["ms_ec"]}}

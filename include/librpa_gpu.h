@@ -327,8 +327,10 @@ int librpa_gpu_get_stats(librpa_gpu_t h, librpa_gpu_stats *s);
  * one of them, and runs its GEMMs as single grouped launches over all those tiles, which
  * have uneven shapes.  The GEMM tile shape is picked by timing the variants on the first
  * run; from the second run on, that launch sequence is replayed from a CUDA graph.  The
- * other handles (tensor-core modes, nspins = 2) run their whole path at the same time on
- * up to four library-owned streams (one host thread each).  While a batch exists, run its
+ * single-channel tensor-core handles without screening are grouped by digit-plane count; a
+ * group's chi0 contraction runs in rounds whose N-step, X-step and final GEMMs are each one
+ * launch over all the group's tiles.  Those groups and the other handles (nspins = 2,
+ * screening) run at the same time on up to four library-owned streams (one host thread each).  While a batch exists, run its
  * handles only through the batch.  After changing a handle's LRI blocks or structure, the
  * next run re-plans and captures again.  Destroy the batch before its handles. */
 typedef struct librpa_gpu_batch *librpa_gpu_batch_t;
@@ -342,6 +344,8 @@ typedef struct {
   double ms_green, ms_chi0, ms_freq, ms_ec;   /* device time of the merged handles' stages */
   double ms_total;         /* wall time of the whole last run */
   long long launches;      /* kernel launches of the last run (graph nodes included) */
+  int n_merged_tc;         /* tensor-core handles whose chi0 GEMMs ran merged with others of their
+                              digit-plane count */
 } librpa_gpu_batch_stats;
 
 /* Group n distinct handles of one device.  Errors: E_ARG, E_NOMEM. */

@@ -2,11 +2,15 @@
 // contraction of all single-channel FP64 handles runs in rounds of point batches on one stream,
 // each round's GEMMs as single grouped launches over all those handles' tiles (uneven block
 // shapes), with tile variants tuned on the first run and the launch sequence replayed from a
-// CUDA graph afterwards.  The other handles (tensor-core modes, nspins = 2) run their whole path
-// at the same time on up to four worker threads, each with its own stream, so that small
-// structures overlap on the device.  G, the transforms and the ln det stage run per handle.
+// CUDA graph afterwards.  The single-channel tensor-core handles are grouped by digit-plane count,
+// and each group's chi0 contraction runs in rounds whose N-step, X-step and final GEMMs are one
+// launch over all the group's tiles (tensor maps per handle).  Those groups and the remaining
+// handles (nspins = 2, screening) run at the same time on up to four worker threads, each with
+// its own stream, so that small structures overlap on the device.  G, the transforms and the ln
+// det stage run per handle.
 #include <algorithm>
 #include <chrono>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -73,6 +77,53 @@ void run_own(Handle &h, cudaStream_t ws, double *ec) {
   if (h.opts.check_level >= 1 && !(imag <= 1e-10)) throw Error{LIBRPA_E_NUMERIC, "batch: G(R, tau) has an imaginary part"};
 }
 
+// A group of tensor-core handles with the same digit-plane count on stream `ws`: G per handle, the
+// chi0 contraction of all of them merged (chi0_run_tc_merged), then transforms and ln det per
+// handle, releasing each one's chi0(q, i omega) and workspace afterwards; throws Error with
+// *failed set to the position in `g` of the handle concerned.
+void run_tc_group(std::vector<Handle *> &g, cudaStream_t ws, double *const *ec, int *failed) {
+  std::vector<cudaStream_t> saved;
+  for (Handle *h : g) {
+    saved.push_back(h->stream);
+    h->stream = ws;
+  }
+  struct Restore {
+    std::vector<Handle *> &g;
+    std::vector<cudaStream_t> &s;
+    ~Restore() {
+      for (size_t i = 0; i < g.size(); ++i) g[i]->stream = s[i];
+    }
+  } restore{g, saved};
+  std::vector<double> imag(g.size());
+  for (size_t i = 0; i < g.size(); ++i) {
+    *failed = (int)i;
+    Handle &h = *g[i];
+    materialize(h);
+    h.stats = librpa_gpu_stats{};
+    imag[i] = green_build(h);
+    if (h.lri_dirty) {
+      chi0_plan(h);
+      h.lri_dirty = false;
+    }
+  }
+  *failed = 0;
+  chi0_run_tc_merged(g);
+  for (size_t i = 0; i < g.size(); ++i) {
+    *failed = (int)i;
+    Handle &h = *g[i];
+    freq_transform(h);
+    h.chi0_done = true;
+    const int rc = ec_run(h, ec[i], nullptr, nullptr);
+    if (rc == LIBRPA_E_NOT_PD) throw Error{rc, "ec: a Cholesky pivot was <= 0"};
+    if (rc) throw Error{rc, "ec: a bounded device wait ran out"};
+    h.release(h.d_chi_qw);
+    h.release(h.work);
+    h.chi0_done = false;
+    h.resolve_timers();
+    if (h.opts.check_level >= 1 && !(imag[i] <= 1e-10)) throw Error{LIBRPA_E_NUMERIC, "batch: G(R, tau) has an imaginary part"};
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -114,12 +165,28 @@ int librpa_gpu_batch_run(librpa_gpu_batch_t b, double *ec) {
   }
   const auto t_start = std::chrono::steady_clock::now();
   std::vector<int> mi, oi;   // merged FP64 handles, handles on their own path
-  for (int i = 0; i < n; ++i) (chi0_fits_one_batch(*hs[i]) ? mi : oi).push_back(i);
-  // own-path handles: up to four workers, each on its own stream
+  std::map<int, std::vector<int>> tcg;   // tensor-core handles by digit-plane count (merged per group)
+  for (int i = 0; i < n; ++i) {
+    if (chi0_fits_one_batch(*hs[i]))
+      mi.push_back(i);
+    else if (chi0_fits_tc_batch(*hs[i]))
+      tcg[hs[i]->chi0_S].push_back(i);
+    else
+      oi.push_back(i);
+  }
+  // worker jobs: a tensor-core group (one merged contraction) or one own-path handle
+  std::vector<std::vector<int>> jobs;
+  int n_tc_merged = 0;
+  for (auto &kv : tcg) {
+    jobs.push_back(kv.second);
+    if (kv.second.size() > 1) n_tc_merged += (int)kv.second.size();
+  }
+  for (int i : oi) jobs.push_back({i});
+  // up to four workers, each on its own stream
   std::mutex fmu;
   Failure own_fail;
   long long own_launches = 0;
-  const int nwk = std::min<int>(4, (int)oi.size());
+  const int nwk = std::min<int>(4, (int)jobs.size());
   std::vector<std::thread> workers;
   for (int w = 0; w < nwk; ++w)
     workers.emplace_back([&, w] {
@@ -129,20 +196,31 @@ int librpa_gpu_batch_run(librpa_gpu_batch_t b, double *ec) {
       if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         std::lock_guard<std::mutex> lk(fmu);
-        if (own_fail.index < 0) own_fail = Failure{oi[w], LIBRPA_E_CUDA, "batch: stream creation failed"};
+        if (own_fail.index < 0) own_fail = Failure{jobs[w][0], LIBRPA_E_CUDA, "batch: stream creation failed"};
         return;
       }
-      for (size_t k = w; k < oi.size(); k += nwk) {
-        const int i = oi[k];
+      for (size_t k = w; k < jobs.size(); k += nwk) {
+        const std::vector<int> &job = jobs[k];
+        int at = 0;   // position in the job of the handle an error concerns
         try {
-          run_own(*hs[i], ws, &ec[i]);
+          if (job.size() == 1 && !chi0_fits_tc_batch(*hs[job[0]])) {
+            run_own(*hs[job[0]], ws, &ec[job[0]]);
+          } else {
+            std::vector<Handle *> g;
+            std::vector<double *> out;
+            for (int i : job) {
+              g.push_back(hs[i]);
+              out.push_back(&ec[i]);
+            }
+            run_tc_group(g, ws, out.data(), &at);
+          }
         } catch (const Error &e) {
           cudaStreamSynchronize(ws);
           std::lock_guard<std::mutex> lk(fmu);
-          if (own_fail.index < 0) own_fail = Failure{i, e.code, e.msg};
+          if (own_fail.index < 0) own_fail = Failure{job[at], e.code, e.msg};
         } catch (const std::bad_alloc &) {
           std::lock_guard<std::mutex> lk(fmu);
-          if (own_fail.index < 0) own_fail = Failure{i, LIBRPA_E_NOMEM, "batch: host allocation failed"};
+          if (own_fail.index < 0) own_fail = Failure{job[at], LIBRPA_E_NOMEM, "batch: host allocation failed"};
         }
       }
       cudaStreamSynchronize(ws);
@@ -230,6 +308,7 @@ int librpa_gpu_batch_run(librpa_gpu_batch_t b, double *ec) {
   if (main_fail.index >= 0) return fail_at(main_fail.index, main_fail.code, main_fail.msg);
   if (own_fail.index >= 0) return fail_at(own_fail.index, own_fail.code, own_fail.msg);
   b->st.n_merged = (int)mi.size();
+  b->st.n_merged_tc = n_tc_merged;
   b->st.graph = replay ? 1 : 0;
   b->st.var_nx = b->m.var_nx;
   b->st.var_fin = b->m.var_fin;

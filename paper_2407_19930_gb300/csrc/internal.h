@@ -227,6 +227,12 @@ struct MergedChi0 {
 bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m);
 // whether h takes part in chi0_run_merged (FP64 route, one spin channel)
 bool chi0_fits_one_batch(const Handle &h);
+// Batched chi0 of several tensor-core handles (same digit-plane count, one spin channel, no
+// screening, all on one stream): in rounds of point batches, each round's N-step, X-step and final
+// GEMMs of all handles as one launch over their tiles (operand pairs per handle); gathers, splits
+// and O assembly per handle.
+bool chi0_fits_tc_batch(const Handle &h);
+void chi0_run_tc_merged(std::vector<Handle *> &hs);
 
 // lattice vectors R whose chi0(R, tau) is computed (R <= -R in the flat BvK order); the others
 // are filled as chi0(-R, tau)^T

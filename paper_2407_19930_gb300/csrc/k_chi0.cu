@@ -1215,35 +1215,162 @@ DpWs dp_ws(const Handle &h, const Chi0Plan &P, long long cap_doubles = 1LL << 27
   return w;
 }
 
+// One point batch of the tensor-core route of a handle: views of its workspace (FP64 N, X, O and the
+// digit planes of Bg, Ag and O), the split operands and the GEMM entries of the three steps.
+struct TcRound {
+  std::vector<Point> pts;
+  int np = 0;
+  double *Nw = nullptr, *Xw = nullptr, *Ow = nullptr;
+  char *wbg = nullptr, *wag = nullptr, *wod = nullptr;
+  int *err = nullptr;
+  oz::Sliced cpnx, cpf, sbg, sag, sod;
+  std::vector<oz::Entry> en, ex, ef;
+};
+
+// workspace of h for its point batches (allocated), the error flag cleared; returns the views
+TcRound tc_views(Handle &h, long long *npb) {
+  Chi0Plan &P = h.plan;
+  const TcWs tw = tc_ws(h, P);
+  *npb = tw.npb;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  h.ensure(h.d_chi_tau, (size_t)h.ntau * h.mesh.size() * h.naux * h.naux * sizeof(double));
+  h.ensure(P.ws, tw.total);
+  TcRound r;
+  char *w = (char *)P.ws.p;
+  r.Nw = (double *)w;
+  r.Xw = (double *)(w + al(tw.b_n));
+  r.Ow = (double *)(w + al(tw.b_n) + al(tw.b_x));
+  r.wbg = w + al(tw.b_n) + al(tw.b_x) + al(tw.b_o);
+  r.wag = r.wbg + al(tw.b_bg);
+  r.wod = r.wag + al(tw.b_ag);
+  r.err = (int *)(r.wod + al(tw.b_od));
+  LR_CUDA(cudaMemsetAsync(r.err, 0, 4, h.stream));
+  oz::sliced_bind(r.cpnx, P.cp_nx.p, P.cpnx_rows, P.max_m, h.chi0_S);
+  oz::sliced_bind(r.cpf, P.cp_f.p, h.naux, P.max_nm, h.chi0_S);
+  return r;
+}
+
+// points r.pts: upload them, split the gathered Green's-function operands into digit planes and
+// build the N- and X-step entries
+void tc_gather(Handle &h, TcRound &r) {
+  Chi0Plan &P = h.plan;
+  const int nat = h.natoms, nR = h.mesh.size(), nao = h.nao, S = h.chi0_S;
+  const int np = r.np = (int)r.pts.size();
+  cudaStream_t s = h.stream;
+  h.upload_async(P.t_pts, r.pts.data(), np * sizeof(Point));
+  oz::GatherSrc gs;
+  gs.kind = 0;
+  gs.G = g_spin(h);
+  gs.g_gstride = (long long)h.ntau * nR * nao * nao;
+  gs.nR = nR;
+  gs.nao = nao;
+  gs.n1 = h.mesh.n1;
+  gs.n2 = h.mesh.n2;
+  gs.n3 = h.mesh.n3;
+  gs.natoms = nat;
+  gs.rows_per_entry = P.m_all;
+  gs.pts = (const int *)P.t_pts.p;
+  gs.uni = (const int *)P.d_uni.p;
+  gs.lam = (const int *)P.d_lam.p;
+  gs.lam_off = (const long long *)P.t_lam_off.p;
+  gs.m = (const int *)P.t_m.p;
+  const int rows_bg = 2 * nat * P.m_all, rows_ag = 2 * nat * nao, rows_o = nat * h.naux;
+  oz::sliced_bind(r.sbg, r.wbg, np * rows_bg, P.max_m, S);
+  oz::sliced_bind(r.sag, r.wag, np * rows_ag, P.max_m, S);
+  oz::sliced_bind(r.sod, r.wod, np * rows_o, P.max_nm, S);
+  oz::split_gather(gs, np * rows_bg, P.max_m, r.sbg, s);
+  gs.kind = 1;
+  gs.rows_per_entry = nao;
+  oz::split_gather(gs, np * rows_ag, P.max_m, r.sag, s);
+  // N-step: N_V = Cpack_V Bg_V^T;  X-step: X_V = Ag_V Cpack_V^T (as FP32 pairs when the O assembly
+  // runs in FP32 pairs)
+  const bool pairs = S >= 4 && S <= oz::SMAX;
+  r.en.clear();
+  r.ex.clear();
+  for (int q = 0; q < np; ++q)
+    for (int g = 0; g < 2; ++g)
+      for (int V = 0; V < nat; ++V) {
+        const int rowsV = h.n_aux[V] * h.n_ao[V], e = (q * 2 + g) * nat + V;
+        oz::Entry a{};
+        a.a_row0 = P.cpnx_off[V];
+        a.b_row0 = e * P.m_all;
+        a.M = rowsV;
+        a.N = P.m_all;
+        a.K = P.m[V];
+        a.C = r.Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V];
+        a.ldc = P.m_all;
+        a.alpha = 1.0;
+        a.mode = pairs ? 3 : 0;
+        r.en.push_back(a);
+        oz::Entry b{};
+        b.a_row0 = e * nao;
+        b.b_row0 = P.cpnx_off[V];
+        b.M = nao;
+        b.N = rowsV;
+        b.K = P.m[V];
+        b.C = r.Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V];
+        b.mode = pairs ? 3 : 0;
+        b.ldc = rowsV;
+        b.alpha = 1.0;
+        r.ex.push_back(b);
+      }
+}
+
+// O = M + M* + Z + Z* of the round (zero: screening flags or NULL), its digit planes (rows nu per
+// (point, U), K = n_U m_U), and the final-contraction entries
+void tc_assemble(Handle &h, TcRound &r, const unsigned char *zero) {
+  Chi0Plan &P = h.plan;
+  const int nat = h.natoms, nR = h.mesh.size(), naux = h.naux, np = r.np;
+  run_oassemble(h, (const Point *)P.t_pts.p, np, r.Nw, r.Xw, r.Ow, zero);
+  std::vector<long long> off(np * nat);
+  std::vector<int> ke(np * nat);
+  for (int q = 0; q < np; ++q)
+    for (int U = 0; U < nat; ++U) {
+      off[q * nat + U] = (long long)q * P.o_sz + P.o_off[U];
+      ke[q * nat + U] = h.n_ao[U] * P.m[U];
+    }
+  h.upload_async(P.t_oe_off, off.data(), off.size() * 8);
+  h.upload_async(P.t_oe_k, ke.data(), ke.size() * 4);
+  oz::split_ragged(r.Ow, (const long long *)P.t_oe_off.p, (const int *)P.t_oe_k.p, naux, np * nat, P.max_nm, r.sod,
+                   h.stream);
+  const double spin = spin_factor(h);
+  r.ef.clear();
+  for (int q = 0; q < np; ++q) {
+    double *chi = (double *)h.d_chi_tau.p + ((size_t)r.pts[q].itau * nR + r.pts[q].iR) * naux * naux;
+    for (int U = 0; U < nat; ++U) {
+      oz::Entry f{};
+      f.a_row0 = h.aux_off[U];
+      f.b_row0 = (q * nat + U) * naux;
+      f.M = h.n_aux[U];
+      f.N = naux;
+      f.K = h.n_ao[U] * P.m[U];
+      f.C = chi + (size_t)h.aux_off[U] * naux;
+      f.ldc = naux;
+      f.alpha = -spin;
+      f.beta = h.cur_spin > 0 ? 1.0 : 0.0;
+      r.ef.push_back(f);
+    }
+  }
+}
+
+void tc_check(Handle &h, const int *err) {
+  int e_host = 0;
+  LR_CUDA(cudaMemcpyAsync(&e_host, err, 4, cudaMemcpyDeviceToHost, h.stream));
+  LR_CUDA(cudaStreamSynchronize(h.stream));
+  if (e_host) throw Error{LIBRPA_E_TIMEOUT, "chi0: a bounded wait in the tensor-core GEMM ran out"};
+}
+
 // Tensor-core route: the N, X and final GEMMs on digit planes (S = h.chi0_S).
 void chi0_run_tc(Handle &h) {
   Chi0Plan &P = h.plan;
-  const int nat = h.natoms, nR = h.mesh.size(), ntau = h.ntau, naux = h.naux, nao = h.nao, S = h.chi0_S;
+  const int nat = h.natoms, nR = h.mesh.size(), ntau = h.ntau, naux = h.naux;
   const bool scr = h.g_screen > 0;
   cudaStream_t s = h.stream;
-  h.ensure(h.d_chi_tau, (size_t)ntau * nR * naux * naux * sizeof(double));
-  const int rows_bg = 2 * nat * P.m_all, rows_ag = 2 * nat * nao, rows_o = nat * naux;
   const std::vector<int> rl = chi0_r_list(h.mesh);
-  const TcWs tw = tc_ws(h, P);
-  const long long npb = tw.npb;
-  const size_t b_n = tw.b_n, b_x = tw.b_x, b_o = tw.b_o, b_bg = tw.b_bg, b_ag = tw.b_ag, b_od = tw.b_od;
-  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  h.ensure(P.ws, tw.total);
-  char *w = (char *)P.ws.p;
-  double *Nw = (double *)w;
-  double *Xw = (double *)(w + al(b_n));
-  double *Ow = (double *)(w + al(b_n) + al(b_x));
-  char *wbg = w + al(b_n) + al(b_x) + al(b_o);
-  char *wag = wbg + al(b_bg), *wod = wag + al(b_ag);
-  int *err = (int *)(wod + al(b_od));
-  LR_CUDA(cudaMemsetAsync(err, 0, 4, s));
-  oz::Sliced cpnx, cpf;
-  oz::sliced_bind(cpnx, P.cp_nx.p, P.cpnx_rows, P.max_m, S);
-  oz::sliced_bind(cpf, P.cp_f.p, naux, P.max_nm, S);
-  const double spin = spin_factor(h);
-  const size_t g_gstride = (size_t)ntau * nR * nao * nao;
+  long long npb = 1;
+  TcRound r = tc_views(h, &npb);
   // under screening, points left out keep chi0 = 0 (the second spin channel accumulates)
-  if (h.g_screen > 0) LR_CUDA(cudaMemsetAsync(h.d_chi_tau.p, 0, (size_t)ntau * nR * naux * naux * sizeof(double), s));
+  if (scr) LR_CUDA(cudaMemsetAsync(h.d_chi_tau.p, 0, (size_t)ntau * nR * naux * naux * sizeof(double), s));
   h.flop_chi0_run = 0;
   for (h.cur_spin = 0; h.cur_spin < h.nspins; ++h.cur_spin) {
     const ScreenSel sel = screen_select(h, rl);
@@ -1252,68 +1379,12 @@ void chi0_run_tc(Handle &h) {
     h.stats.n_points_skipped += sel.skipped;
     for (long long p0 = 0; p0 < total_pts; p0 += npb) {
       const int np = (int)std::min(npb, total_pts - p0);
-      std::vector<Point> pts(sel.pts.begin() + p0, sel.pts.begin() + p0 + np);
-      h.upload_async(P.t_pts, pts.data(), np * sizeof(Point));
-      // digit planes of the gathered Green's-function operands, straight from G
-      oz::GatherSrc gs;
-      gs.kind = 0;
-      gs.G = g_spin(h);
-      gs.g_gstride = (long long)g_gstride;
-      gs.nR = nR;
-      gs.nao = nao;
-      gs.n1 = h.mesh.n1;
-      gs.n2 = h.mesh.n2;
-      gs.n3 = h.mesh.n3;
-      gs.natoms = nat;
-      gs.rows_per_entry = P.m_all;
-      gs.pts = (const int *)P.t_pts.p;
-      gs.uni = (const int *)P.d_uni.p;
-      gs.lam = (const int *)P.d_lam.p;
-      gs.lam_off = (const long long *)P.t_lam_off.p;
-      gs.m = (const int *)P.t_m.p;
-      oz::Sliced sbg, sag, sod;
-      oz::sliced_bind(sbg, wbg, np * rows_bg, P.max_m, S);
-      oz::sliced_bind(sag, wag, np * rows_ag, P.max_m, S);
-      oz::sliced_bind(sod, wod, np * rows_o, P.max_nm, S);
-      oz::split_gather(gs, np * rows_bg, P.max_m, sbg, s);
-      gs.kind = 1;
-      gs.rows_per_entry = nao;
-      oz::split_gather(gs, np * rows_ag, P.max_m, sag, s);
-      // N-step: N_V = Cpack_V Bg_V^T;  X-step: X_V = Ag_V Cpack_V^T (as FP32 pairs when the O
-      // assembly runs in FP32 pairs)
-      const bool pairs = S >= 4 && S <= oz::SMAX;
-      std::vector<oz::Entry> en, ex;
-      for (int q = 0; q < np; ++q)
-        for (int g = 0; g < 2; ++g)
-          for (int V = 0; V < nat; ++V) {
-            const int rowsV = h.n_aux[V] * h.n_ao[V], e = (q * 2 + g) * nat + V;
-            oz::Entry a{};
-            a.a_row0 = P.cpnx_off[V];
-            a.b_row0 = e * P.m_all;
-            a.M = rowsV;
-            a.N = P.m_all;
-            a.K = P.m[V];
-            a.C = Nw + (size_t)q * 2 * P.n_sz + g * P.n_sz + P.n_off[V];
-            a.ldc = P.m_all;
-            a.alpha = 1.0;
-            a.mode = pairs ? 3 : 0;
-            en.push_back(a);
-            oz::Entry b{};
-            b.a_row0 = e * nao;
-            b.b_row0 = P.cpnx_off[V];
-            b.M = nao;
-            b.N = rowsV;
-            b.K = P.m[V];
-            b.C = Xw + (size_t)q * 2 * P.x_sz + g * P.x_sz + P.x_off[V];
-            b.mode = pairs ? 3 : 0;
-            b.ldc = rowsV;
-            b.alpha = 1.0;
-            ex.push_back(b);
-          }
+      r.pts.assign(sel.pts.begin() + p0, sel.pts.begin() + p0 + np);
+      tc_gather(h, r);
       // screening: tiles sum only the K stages that meet kept G blocks, O blocks without a kept
       // contribution are written as zeros (see BlockSparse)
       BlockSparse B;
-      if (scr) B = block_sparse(h, pts);
+      if (scr) B = block_sparse(h, r.pts);
       ChunkMemo memo_n, memo_x, memo_f;
       const oz::StageFn fn_n = [&](int e, int, int, int n0, int cols, int cs, int K, std::vector<int> &out) {
         memo_n.get(e, n0, cs, out, [&](std::vector<int> &o) {
@@ -1331,8 +1402,8 @@ void chi0_run_tc(Handle &h) {
         memo_f.get(e, n0, cs, out, [&](std::vector<int> &o) { chunks_f(h, B, e / nat, e % nat, n0, cols, cs, K, o); });
         return true;
       };
-      h.flop_chi0_run += timed_grouped(h, cpnx, sbg, en, err, P.gargs1, scr ? &fn_n : nullptr);
-      h.flop_chi0_run += timed_grouped(h, sag, cpnx, ex, err, P.gargs2, scr ? &fn_x : nullptr);
+      h.flop_chi0_run += timed_grouped(h, r.cpnx, r.sbg, r.en, r.err, P.gargs1, scr ? &fn_n : nullptr);
+      h.flop_chi0_run += timed_grouped(h, r.sag, r.cpnx, r.ex, r.err, P.gargs2, scr ? &fn_x : nullptr);
       std::vector<unsigned char> zf;
       if (scr) {
         double fo = 0;
@@ -1342,46 +1413,75 @@ void chi0_run_tc(Handle &h) {
       } else {
         h.flop_chi0_run += np * (P.flop_per_point - P.flop_nx_per_point - P.flop_fin_per_point);
       }
-      run_oassemble(h, (const Point *)P.t_pts.p, np, Nw, Xw, Ow, scr ? (const unsigned char *)P.t_ozero.p : nullptr);
-      // digit planes of O (rows nu per (point, U), K = n_U m_U), then the final contraction
-      {
-        std::vector<long long> off(np * nat);
-        std::vector<int> ke(np * nat);
-        for (int q = 0; q < np; ++q)
-          for (int U = 0; U < nat; ++U) {
-            off[q * nat + U] = (long long)q * P.o_sz + P.o_off[U];
-            ke[q * nat + U] = h.n_ao[U] * P.m[U];
-          }
-        h.upload_async(P.t_oe_off, off.data(), off.size() * 8);
-        h.upload_async(P.t_oe_k, ke.data(), ke.size() * 4);
-        oz::split_ragged(Ow, (const long long *)P.t_oe_off.p, (const int *)P.t_oe_k.p, naux, np * nat, P.max_nm, sod, s);
-      }
-      std::vector<oz::Entry> ef;
-      for (int q = 0; q < np; ++q) {
-        double *chi = (double *)h.d_chi_tau.p + ((size_t)pts[q].itau * nR + pts[q].iR) * naux * naux;
-        for (int U = 0; U < nat; ++U) {
-          oz::Entry f{};
-          f.a_row0 = h.aux_off[U];
-          f.b_row0 = (q * nat + U) * naux;
-          f.M = h.n_aux[U];
-          f.N = naux;
-          f.K = h.n_ao[U] * P.m[U];
-          f.C = chi + (size_t)h.aux_off[U] * naux;
-          f.ldc = naux;
-          f.alpha = -spin;
-          f.beta = h.cur_spin > 0 ? 1.0 : 0.0;
-          ef.push_back(f);
-        }
-      }
-      h.flop_chi0_run += timed_grouped(h, cpf, sod, ef, err, P.gargs3, scr ? &fn_f : nullptr);
+      tc_assemble(h, r, scr ? (const unsigned char *)P.t_ozero.p : nullptr);
+      h.flop_chi0_run += timed_grouped(h, r.cpf, r.sod, r.ef, r.err, P.gargs3, scr ? &fn_f : nullptr);
     }
   }
   h.cur_spin = 0;
   fill_partners(h);
-  int e_host = 0;
-  LR_CUDA(cudaMemcpyAsync(&e_host, err, 4, cudaMemcpyDeviceToHost, s));
-  LR_CUDA(cudaStreamSynchronize(s));
-  if (e_host) throw Error{LIBRPA_E_TIMEOUT, "chi0: a bounded wait in the tensor-core GEMM ran out"};
+  tc_check(h, r.err);
+}
+
+// the same for several handles at once, on hs[0]'s stream (see chi0_run_tc_merged)
+void tc_merged(std::vector<Handle *> &hs) {
+  Handle &h0 = *hs[0];
+  const size_t nh = hs.size();
+  std::vector<TcRound> rs(nh);
+  std::vector<long long> npb(nh);
+  std::vector<std::vector<Point>> pts(nh);
+  int rounds = 0;
+  for (size_t i = 0; i < nh; ++i) {
+    Handle &h = *hs[i];
+    h.cur_spin = 0;
+    rs[i] = tc_views(h, &npb[i]);
+    const std::vector<int> rl = chi0_r_list(h.mesh);
+    pts[i] = make_points(h, rl, 0, (int)(h.ntau * rl.size()));
+    h.stats.n_points_chi0 = (long long)pts[i].size();
+    h.flop_chi0_run = pts[i].size() * h.plan.flop_per_point;
+    rounds = std::max(rounds, (int)((pts[i].size() + npb[i] - 1) / npb[i]));
+  }
+  auto launch = [&](int step) {   // 0: N, 1: X, 2: final; every handle's entries in one launch
+    std::vector<std::pair<const oz::Sliced *, const oz::Sliced *>> ops;
+    std::vector<oz::Entry> es;
+    for (size_t i = 0; i < nh; ++i) {
+      TcRound &r = rs[i];
+      if (!r.np) continue;
+      const int pair = (int)ops.size();
+      if (step == 0) ops.push_back({&r.cpnx, &r.sbg});
+      if (step == 1) ops.push_back({&r.sag, &r.cpnx});
+      if (step == 2) ops.push_back({&r.cpf, &r.sod});
+      for (oz::Entry e : step == 0 ? r.en : step == 1 ? r.ex : r.ef) {
+        e.pair = pair;
+        es.push_back(e);
+      }
+    }
+    Handle::Timed t{nullptr, nullptr, 0, 0};
+    LR_CUDA(cudaEventCreate(&t.a));
+    LR_CUDA(cudaEventCreate(&t.b));
+    LR_CUDA(cudaEventRecord(t.a, h0.stream));
+    DevBuf &args = step == 0 ? h0.plan.gargs1 : step == 1 ? h0.plan.gargs2 : h0.plan.gargs3;
+    oz::gemm_multi(ops, es, rs[0].err, h0.stream, h0, args);
+    LR_CUDA(cudaEventRecord(t.b, h0.stream));
+    t.flops = h0.oz_alg_flops;
+    t.exec_flops = h0.oz_exec_flops;
+    h0.timed.push_back(t);
+  };
+  for (int r = 0; r < rounds; ++r) {
+    for (size_t i = 0; i < nh; ++i) {
+      const long long p0 = (long long)r * npb[i];
+      const long long np = std::max<long long>(0, std::min<long long>(npb[i], (long long)pts[i].size() - p0));
+      rs[i].pts.assign(pts[i].begin() + p0, pts[i].begin() + p0 + np);
+      rs[i].np = (int)np;
+      if (np) tc_gather(*hs[i], rs[i]);
+    }
+    launch(0);
+    launch(1);
+    for (size_t i = 0; i < nh; ++i)
+      if (rs[i].np) tc_assemble(*hs[i], rs[i], nullptr);
+    launch(2);
+  }
+  for (size_t i = 0; i < nh; ++i) fill_partners(*hs[i]);
+  tc_check(h0, rs[0].err);
 }
 
 }  // namespace
@@ -1592,6 +1692,16 @@ bool chi0_run_merged(std::vector<Handle *> &hs, MergedChi0 &m) {
 }
 
 bool chi0_fits_one_batch(const Handle &h) { return h.chi0_S < 0 && h.nspins == 1 && !(h.g_screen > 0); }
+
+bool chi0_fits_tc_batch(const Handle &h) { return h.chi0_S >= 0 && h.nspins == 1 && !(h.g_screen > 0); }
+
+void chi0_run_tc_merged(std::vector<Handle *> &hs) {
+  if (hs.empty()) return;
+  for (Handle *h : hs)
+    if (!chi0_fits_tc_batch(*h) || h->chi0_S != hs[0]->chi0_S || h->stream != hs[0]->stream)
+      throw Error{LIBRPA_E_ARG, "chi0_run_tc_merged: handles of different kinds or streams"};
+  tc_merged(hs);
+}
 
 void MergedChi0::reset() {
   if (exec) cudaGraphExecDestroy(exec);

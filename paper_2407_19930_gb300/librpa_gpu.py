@@ -82,7 +82,7 @@ class librpa_gpu_batch_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("n_merged", ctypes.c_int), ("graph", ctypes.c_int), ("var_nx", ctypes.c_int),
                 ("var_fin", ctypes.c_int), ("failed_index", ctypes.c_int), ("ms_green", ctypes.c_double),
                 ("ms_chi0", ctypes.c_double), ("ms_freq", ctypes.c_double), ("ms_ec", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("launches", ctypes.c_longlong)]
+                ("ms_total", ctypes.c_double), ("launches", ctypes.c_longlong), ("n_merged_tc", ctypes.c_int)]
 
 
 class LibrpaError(RuntimeError):
