@@ -517,6 +517,11 @@ def run_gpu(args):
                                        "request alternating fp64_tc / split"
                                        % (len(reqs), min(sizes), max(sizes), args.ntau),
                            "slots": args.slots, "sweep": sweep}
+    if ws == 1 and args.batch_sample > 0:
+        torch.cuda.empty_cache()
+        binp = _batch_inputs(args.batch_sample)
+        bout, bclk = batch_measure(L, binp, args.ntau, 1, local, torch)
+        line["batch"] = {"workload": _batch_workload(binp, args.ntau), "modes": bout, "clocks": bclk}
     if ws == 1 and not args.no_cpu:
         from oracle import build as obuild, grid as ogrid
         obuild.build()
@@ -706,8 +711,8 @@ def _batch_inputs(n):
 
 def run_batch(args):
     """Batched workload: n independent structures (2-40 atoms, mixed species, 1x1x1 to 3x3x1 k) in
-    one librpa_gpu_batch_run (merged FP64 chi0 launches, graph replay), against the same structures
-    one by one through librpa_gpu_chi0 + librpa_gpu_ec."""
+    one librpa_gpu_batch_run (merged chi0 launches, graph replay for FP64), against the same
+    structures one by one through librpa_gpu_chi0 + librpa_gpu_ec."""
     ws, rank, local = dist_init()
     if ws > 1:
         print(json.dumps({"metric": METRIC, "unavailable": "the batched run is one process on one GPU"}))
@@ -719,11 +724,34 @@ def run_batch(args):
     torch.cuda.set_device(local)
     lbuild.build()
     L.load(build_if_missing=False)
+    out, clk = batch_measure(L, inputs, args.ntau, args.steps, local, torch)
+    sizes = [inp.st.natoms for inp in inputs]
+    line = {
+        "metric": METRIC, "value": out["fp64"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": 1, "ms_per_step": out["fp64"]["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded random cells, tight-binding KS data, LRI coefficients, Coulomb matrices)",
+        "config": {"workload": _batch_workload(inputs, args.ntau)},
+        "modes": out, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _batch_workload(inputs, ntau):
+    sizes = [inp.st.natoms for inp in inputs]
+    return ("batched: %d structures of %d-%d atoms (5/9/13 NAO, 20/40/60 ABF), k-mesh 1x1x1..3x3x1, %d tau, "
+            "one batch run per step" % (len(inputs), min(sizes), max(sizes), ntau))
+
+
+def batch_measure(L, inputs, ntau, steps, local, torch):
+    """The structures in one librpa_gpu_batch_run per step (FP64 and the mixed mode; one run first to
+    tune and capture) against the same structures one by one; returns (per-mode results, clocks)."""
 
     def opts(mode):
         o = L.librpa_gpu_default_opts()
         o.device = local
-        o.n_tau = args.ntau
+        o.n_tau = ntau
         o.precision = PRECISIONS[mode][0]
         return o
 
@@ -740,9 +768,9 @@ def run_batch(args):
             b = L.librpa_gpu_batch_create(hs)
             ec0 = L.librpa_gpu_batch_run(b)             # tunes the tiles, captures the graph
             t0 = time.perf_counter()
-            for _ in range(args.steps):
+            for _ in range(steps):
                 ec = L.librpa_gpu_batch_run(b)
-            t_batch = (time.perf_counter() - t0) / args.steps
+            t_batch = (time.perf_counter() - t0) / steps
             st = L.librpa_gpu_batch_get_stats(b)
         finally:
             L.librpa_gpu_batch_destroy(b)
@@ -773,19 +801,7 @@ def run_batch(args):
                      "stage_ms": {"green": st["ms_green"], "chi0": st["ms_chi0"], "freq": st["ms_freq"],
                                   "ec": st["ms_ec"]}}
     clk = clocks.stop()
-    sizes = [inp.st.natoms for inp in inputs]
-    line = {
-        "metric": METRIC, "value": out["fp64"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": 1, "ms_per_step": out["fp64"]["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded random cells, tight-binding KS data, LRI coefficients, Coulomb matrices)",
-        "config": {"workload": "batched: %d structures of %d-%d atoms (5/9/13 NAO, 20/40/60 ABF), k-mesh "
-                               "1x1x1..3x3x1, %d tau, one batch run per step" % (len(inputs), min(sizes), max(sizes),
-                                                                               args.ntau)},
-        "modes": out, "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
-    return 0
+    return out, clk
 
 
 def main():
@@ -808,6 +824,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving workload instead of the headline")
     ap.add_argument("--batch", action="store_true", help="batched workload instead of the headline")
     ap.add_argument("--batch-n", type=int, default=64)
+    ap.add_argument("--batch-sample", type=int, default=8,
+                    help="structures of the batched sample added to the headline line (0: none)")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-sample", type=int, default=12,
                     help="requests per arrival rate of the serving sweep added to the headline line (0: none)")
