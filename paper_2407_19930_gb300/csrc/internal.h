@@ -90,10 +90,12 @@ struct Chi0Plan {
   std::vector<int> cpnx_off;
   DevBuf cp_nx, cp_f, t_oe_off, t_oe_k, gargs3;
   DevBuf t_ozero;   // screening: O-assembly blocks that are exactly zero, per point batch
+  DevBuf t_ugroups; // atoms grouped by the O assembly's row-block size; group g at [ugroup_off[g], ugroup_off[g+1])
+  std::vector<int> ugroup_off;
   std::vector<DevBuf *> all() {
     return {&d_lam, &d_uni, &d_kap, &t_n_ao, &t_n_aux, &t_ao_off, &t_aux_off, &t_m, &t_lam_off, &t_kap_off,
             &t_bg_off, &t_ag_off, &t_n_off, &t_x_off, &t_o_off, &t_pts, &ws, &gargs1, &gargs2,
-            &cp_nx, &cp_f, &t_oe_off, &t_oe_k, &gargs3, &t_ozero};
+            &cp_nx, &cp_f, &t_oe_off, &t_oe_k, &gargs3, &t_ozero, &t_ugroups};
   }
 };
 

@@ -238,7 +238,8 @@ struct ArD {
 struct ArF {
   using T = float;
   __device__ static T from(double x) { return (float)x; }
-  __device__ static T load(const double *p) { return (float)*p; }
+  // N and X arrive from their GEMMs as (hi, lo) FP32 pairs in 8-byte slots: the hi part
+  __device__ static T load(const double *p) { return reinterpret_cast<const float2 *>(p)->x; }
   __device__ static double to(T x) { return (double)x; }
   __device__ static T zero() { return 0.f; }
   __device__ static T mad(T a, T b, T c) { return fmaf(a, b, c); }
@@ -268,18 +269,25 @@ struct ArDF {
   }
 };
 
-// One CTA per (point, U, V, 64-column chunk of U's packed columns); 64 x NL threads = 64 columns
-// x NL lanes over nu; every thread computes all rows i of U for its (nu, column).  Shared
+// row-block sizes of the O assembly: atoms with up to 5, 9, 13 and more NAOs (13: carbon-like,
+// 5 / 9: light and intermediate species of the workloads)
+constexpr int kOasmRows[4] = {5, 9, 13, 16};
+int oasm_group(int n_ao) { return n_ao <= 5 ? 0 : n_ao <= 9 ? 1 : n_ao <= 13 ? 2 : 3; }
+
+// One CTA per (point, U, V, 64-column chunk of U's packed columns), for the atoms U listed in ulist
+// (those whose NAO count the row block ROWS suits: a launch per such group); 64 x NL threads = 64
+// columns x NL lanes over nu; every thread computes all rows i of U for its (nu, column), ROWS at
+// a time (ROWS = n_U for the 5, 9 and 13 NAOs of the workloads: no predicated-off rows).  Shared
 // memory (type T): Lm[n_U][2 n_V] = [A_UV(R) | B_UV(R)], RG[2 n_V][64] = [B_{V,kap}(R1-R);
 // A_{V,kap}(R1-R)], LX[NL][n_U][2 n_V] = [X^A_nu | X^B_nu] (rows of U) for the NL nu of a step.
-template <class Ar>
-__global__ void __launch_bounds__(256) k_oassemble(OArgs a, int NL) {
+template <class Ar, int ROWS>
+__global__ void __launch_bounds__(256, 2) k_oassemble(OArgs a, int NL, const int *__restrict__ ulist, int nlist) {
   using T = typename Ar::T;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *sm = reinterpret_cast<T *>(smraw);
   const int V = blockIdx.y % a.natoms;
-  const int U = (blockIdx.y / a.natoms) % a.natoms;
-  const int p = blockIdx.y / (a.natoms * a.natoms);
+  const int U = ulist[(blockIdx.y / a.natoms) % nlist];
+  const int p = blockIdx.y / (a.natoms * nlist);
   const int mU = a.m[U];
   const int c0 = blockIdx.x * 64;
   if (c0 >= mU) return;
@@ -343,22 +351,29 @@ __global__ void __launch_bounds__(256) k_oassemble(OArgs a, int NL) {
     if (!live || nu >= nauxV) continue;
     const T *lx = LX + nl * nU * two;
     double *orow = Ob + (size_t)(a.aux_off[V] + nu) * ldo;
-    for (int i0 = 0; i0 < nU; i0 += 16) {
-      T acc[16];
+    for (int i0 = 0; i0 < nU; i0 += ROWS) {
+      T acc[ROWS];
 #pragma unroll
-      for (int r = 0; r < 16; ++r) acc[r] = Ar::zero();
+      for (int r = 0; r < ROWS; ++r) acc[r] = Ar::zero();
+      // the two halves of t (N[G^occ] with A_UV, then N[G^vir] with B_UV) without a select per t
+#pragma unroll 1
+      for (int hlf = 0; hlf < 2; ++hlf) {
+        const double *Nh = (hlf == 0 ? NB : NA) + (size_t)nu * nV * a.m_all + ucol;
 #pragma unroll 2
-      for (int t = 0; t < two; ++t) {
-        const T rn = Ar::load((t < nV ? NB : NA) + (size_t)(nu * nV + (t % nV)) * a.m_all + ucol);
-        const T rgv = RG[t * 64 + col];
+        for (int j = 0; j < nV; ++j) {
+          const int t = hlf * nV + j;
+          const T rn = Ar::load(Nh + (size_t)j * a.m_all);
+          const T rgv = RG[t * 64 + col];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int i = i0 + r;
-          if (i < nU) acc[r] = Ar::mad(Lm[i * two + t], rn, Ar::mad(lx[i * two + t], rgv, acc[r]));
+          for (int r = 0; r < ROWS; ++r) {
+            const int i = i0 + r;
+            if (ROWS == 16 && i >= nU) break;
+            acc[r] = Ar::mad(Lm[i * two + t], rn, Ar::mad(lx[i * two + t], rgv, acc[r]));
+          }
         }
       }
 #pragma unroll
-      for (int r = 0; r < 16; ++r)
+      for (int r = 0; r < ROWS; ++r)
         if (i0 + r < nU) orow[(size_t)(i0 + r) * mU + kc] = Ar::to(acc[r]);
     }
   }
@@ -629,6 +644,17 @@ void chi0_plan(Handle &h) {
   upload(h, P.t_n_off, P.n_off);
   upload(h, P.t_x_off, P.x_off);
   upload(h, P.t_o_off, P.o_off);
+  {   // atoms by the O assembly's row-block size
+    std::vector<int> ug;
+    P.ugroup_off.assign(5, 0);
+    for (int gi = 0; gi < 4; ++gi) {
+      P.ugroup_off[gi] = (int)ug.size();
+      for (int a = 0; a < nat; ++a)
+        if (oasm_group(h.n_ao[a]) == gi) ug.push_back(a);
+    }
+    P.ugroup_off[4] = (int)ug.size();
+    upload(h, P.t_ugroups, ug);
+  }
   // tensor-core route: digit planes of the packed coefficients, split once per plan
   if (P.tc_S >= 0) {
     const int S = P.tc_S;
@@ -654,6 +680,25 @@ namespace {
 
 // O = M + M* + Z + Z* for the np points of a batch (FP64 pipe).  zero: device flags of the CTAs
 // whose O block is exactly zero under screening ([np][U][V][64-column chunk]), or NULL.
+template <class Ar>
+void set_oasm_smem_limits(int bytes) {
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<Ar, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<Ar, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<Ar, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  LR_CUDA(cudaFuncSetAttribute(k_oassemble<Ar, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+}
+
+template <class Ar>
+void launch_oasm(int gi, dim3 grid, int threads, size_t smem, cudaStream_t s, const OArgs &oa, int NL, const int *ul,
+                 int cnt) {
+  switch (kOasmRows[gi]) {
+    case 5: k_oassemble<Ar, 5><<<grid, threads, smem, s>>>(oa, NL, ul, cnt); break;
+    case 9: k_oassemble<Ar, 9><<<grid, threads, smem, s>>>(oa, NL, ul, cnt); break;
+    case 13: k_oassemble<Ar, 13><<<grid, threads, smem, s>>>(oa, NL, ul, cnt); break;
+    default: k_oassemble<Ar, 16><<<grid, threads, smem, s>>>(oa, NL, ul, cnt); break;
+  }
+}
+
 // 64-column chunks of the widest packed-column list (the O assembly's grid.x)
 int oasm_chunks(const Handle &h) {
   int c = 0;
@@ -683,9 +728,9 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
   // in flight on another thread
   constexpr int kOasmSmemLimit = 200 * 1024;
   if (osmem > (size_t)kOasmSmemLimit) throw Error{LIBRPA_E_ARG, "O assembly: atoms with too many NAOs"};
-  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOasmSmemLimit));
-  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOasmSmemLimit));
-  LR_CUDA(cudaFuncSetAttribute(k_oassemble<ArDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOasmSmemLimit));
+  set_oasm_smem_limits<ArD>(kOasmSmemLimit);
+  set_oasm_smem_limits<ArF>(kOasmSmemLimit);
+  set_oasm_smem_limits<ArDF>(kOasmSmemLimit);
   OArgs oa;
   oa.G = g_spin(h);
   oa.g_gstride = (size_t)h.ntau * h.mesh.size() * h.nao * h.nao;
@@ -717,15 +762,21 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
   oa.o_off = (const long long *)P.t_o_off.p;
   oa.o_sz_p = P.o_sz;
   oa.zero = zero;
-  dim3 og((unsigned)max_chunks, (unsigned)(np * nat * nat));
-  if (ar == 0)
-    k_oassemble<ArD><<<og, 64 * NL, osmem, h.stream>>>(oa, NL);
-  else if (ar == 1)
-    k_oassemble<ArF><<<og, 64 * NL, osmem, h.stream>>>(oa, NL);
-  else
-    k_oassemble<ArDF><<<og, 64 * NL, osmem, h.stream>>>(oa, NL);
-  ++launch_counter();
-  LR_CUDA(cudaGetLastError());
+  // one launch per row-block size: the atoms U of each group (listed in the plan's table)
+  for (int gi = 0; gi < 4; ++gi) {
+    const int cnt = P.ugroup_off[gi + 1] - P.ugroup_off[gi];
+    if (!cnt) continue;
+    const int *ul = (const int *)P.t_ugroups.p + P.ugroup_off[gi];
+    dim3 og((unsigned)max_chunks, (unsigned)(np * cnt * nat));
+    if (ar == 0)
+      launch_oasm<ArD>(gi, og, 64 * NL, osmem, h.stream, oa, NL, ul, cnt);
+    else if (ar == 1)
+      launch_oasm<ArF>(gi, og, 64 * NL, osmem, h.stream, oa, NL, ul, cnt);
+    else
+      launch_oasm<ArDF>(gi, og, 64 * NL, osmem, h.stream, oa, NL, ul, cnt);
+    ++launch_counter();
+    LR_CUDA(cudaGetLastError());
+  }
 }
 
 // Points of the (R, tau) grid in flat order: point idx = itau * nR + iR.
@@ -1282,9 +1333,10 @@ void tc_gather(Handle &h, TcRound &r) {
   gs.kind = 1;
   gs.rows_per_entry = nao;
   oz::split_gather(gs, np * rows_ag, P.max_m, r.sag, s);
-  // N-step: N_V = Cpack_V Bg_V^T;  X-step: X_V = Ag_V Cpack_V^T (as FP32 pairs when the O assembly
-  // runs in FP32 pairs)
-  const bool pairs = S >= 4 && S <= oz::SMAX;
+  // N-step: N_V = Cpack_V Bg_V^T;  X-step: X_V = Ag_V Cpack_V^T, both as FP32 pairs (hi, lo): the O
+  // assembly reads the pair (FP32-pair arithmetic) or its hi part (FP32 arithmetic)
+  const bool pairs = true;
+  (void)S;
   r.en.clear();
   r.ex.clear();
   for (int q = 0; q < np; ++q)

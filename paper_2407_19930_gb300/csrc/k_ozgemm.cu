@@ -672,6 +672,11 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
           for (int c = 0; c < HALF; ++c) {
             const int col = n0 + half * HALF + c;
             if (col >= en.N) break;
+            if (en.mode == 3 && en.alpha_shift != kNoShift) {   // the FP32 sum times +-2^k: exact in FP32
+              const float f = nsteps > 0 ? __uint_as_float(fa[c]) * (float)en.alpha : 0.f;
+              reinterpret_cast<float2 *>(en.C)[(long long)row * en.ldc + col] = make_float2(f, 0.f);
+              continue;
+            }
             const double v = nsteps > 0 ? en.alpha * (double)__uint_as_float(fa[c]) : 0.0;
             if (en.mode == 3) {   // real, as an unevaluated pair of FP32 numbers (hi, lo)
               const float hi = __double2float_rn(v);
