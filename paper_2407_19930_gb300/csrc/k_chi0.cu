@@ -276,8 +276,8 @@ int oasm_group(int n_ao) { return n_ao <= 5 ? 0 : n_ao <= 9 ? 1 : n_ao <= 13 ? 2
 
 // One CTA per (point, U, V, 64-column chunk of U's packed columns), for the atoms U listed in ulist
 // (those whose NAO count the row block ROWS suits: a launch per such group); 64 x NL threads = 64
-// columns x NL lanes over nu; every thread computes all rows i of U for its (nu, column), ROWS at
-// a time (ROWS = n_U for the 5, 9 and 13 NAOs of the workloads: no predicated-off rows).  Shared
+// columns x NL lanes over nu; every thread computes all rows i < n_U of U for its (nu, column),
+// ROWS at a time (ROWS = n_U for the 5, 9 and 13 NAOs of the workloads).  Shared
 // memory (type T): Lm[n_U][2 n_V] = [A_UV(R) | B_UV(R)], RG[2 n_V][64] = [B_{V,kap}(R1-R);
 // A_{V,kap}(R1-R)], LX[NL][n_U][2 n_V] = [X^A_nu | X^B_nu] (rows of U) for the NL nu of a step.
 template <class Ar, int ROWS>
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256, 2) k_oassemble(OArgs a, int NL, const int
 #pragma unroll
           for (int r = 0; r < ROWS; ++r) {
             const int i = i0 + r;
-            if (ROWS == 16 && i >= nU) break;
+            if (i >= nU) break;   // rows beyond U's NAOs (ROWS is the group's largest n_U)
             acc[r] = Ar::mad(Lm[i * two + t], rn, Ar::mad(lx[i * two + t], rgv, acc[r]));
           }
         }

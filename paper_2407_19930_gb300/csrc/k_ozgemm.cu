@@ -622,10 +622,15 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
       const int nsteps = steps_of(en, tl, kbeg);
       const int ngroups = (nsteps + G - 1) / G;
       const int m0 = tl.m0, n0 = tl.n0;
-      long long acc[HALF];       // digit planes: exact int64 sums of the diagonals
+      long long acc[HALF];       // digit planes: exact int64 sums of the diagonals, or (fpath) an FP32 pair
       uint32_t fa[PLAIN ? HALF : 1];   // plain forms: the FP32 accumulators
 #pragma unroll
       for (int j = 0; j < HALF; ++j) acc[j] = 0;
+      // FP32-pair outputs of a tile with a single flush group (the short-K GEMMs of the chi0 steps):
+      // the diagonal sums, exact integers below 2^24 times their powers of two, are summed into an
+      // unevaluated FP32 pair (hi, lo) by exact two-sums, held in the int64 slot's two halves --
+      // FP32 arithmetic instead of the int64 sum and its conversion
+      const bool fpath = !PLAIN && ngroups == 1 && en.mode == 3 && en.alpha_shift != kNoShift;
       bool ok_all = true;
       for (int gi = 0; gi < ngroups; ++gi, ++g) {
         bool ok = !abort_flag && mbar_wait(&tfull, (uint32_t)(g & 1), WAIT_NS, &abort_flag);
@@ -637,16 +642,38 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
         }
         tc_fence_after();
         if constexpr (!PLAIN) {
+          if (fpath) {
 #pragma unroll 1
-          for (int d = 2; d <= S + 1; ++d) {
-            const long long mul = 1LL << (8 * (S + 1 - d));
+            for (int d = 2; d <= S + 1; ++d) {
+              const float mulf = __uint_as_float((uint32_t)(127 + 8 * (S + 1 - d)) << 23);   // 2^(8(S+1-d))
 #pragma unroll
-            for (int cb = 0; cb < HALF / 16; ++cb) {
-              uint32_t r[16];
-              tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d - 2) * BN + half * HALF + cb * 16, r);
+              for (int cb = 0; cb < HALF / 16; ++cb) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d - 2) * BN + half * HALF + cb * 16, r);
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) * mul;
+                for (int j = 0; j < 16; ++j) {
+                  const int c = cb * 16 + j;
+                  const float t = __uint_as_float(r[j]) * mulf;   // exact
+                  const float hi = __int_as_float((int)(acc[c] & 0xFFFFFFFFll));
+                  float lo = __int_as_float((int)(acc[c] >> 32));
+                  const float sm = hi + t, bb = sm - hi;
+                  lo += (hi - (sm - bb)) + (t - bb);
+                  acc[c] = ((long long)__float_as_int(lo) << 32) | (long long)(uint32_t)__float_as_int(sm);
+                }
+              }
+            }
+          } else {
+#pragma unroll 1
+            for (int d = 2; d <= S + 1; ++d) {
+              const long long mul = 1LL << (8 * (S + 1 - d));
+#pragma unroll
+              for (int cb = 0; cb < HALF / 16; ++cb) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d - 2) * BN + half * HALF + cb * 16, r);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) * mul;
+              }
             }
           }
         } else {
@@ -717,7 +744,26 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
             {
               const int sh = ea + eb[en.b_row0 + col] - 14 - 8 * (S - 1) + ash;
               const long long a = aneg ? -acc[c] : acc[c];
-              if (en.mode == 3 && pow2) {
+              if (fpath) {
+                // renormalise the pair, then scale it by 2^sh (exact in the normal range)
+                float hi = __int_as_float((int)(acc[c] & 0xFFFFFFFFll)), lo = __int_as_float((int)(acc[c] >> 32));
+                const float sm = hi + lo;
+                lo = lo - (sm - hi);
+                hi = sm;
+                if (aneg) {
+                  hi = -hi;
+                  lo = -lo;
+                }
+                const int eh = (int)((__float_as_uint(hi) >> 23) & 0xFF);
+                if (sh >= -126 && sh <= 127 && (hi == 0.f || (eh + sh >= 1 && eh + sh <= 254))) {
+                  const float sc = __uint_as_float((uint32_t)(sh + 127) << 23);
+                  pr = make_float2(hi * sc, lo * sc);
+                } else {   // outside the FP32 range of a direct scaling: through FP64
+                  const double dv = ldexp((double)hi + (double)lo, sh);
+                  pr.x = __double2float_rn(dv);
+                  pr.y = __double2float_rn(dv - (double)pr.x);
+                }
+              } else if (en.mode == 3 && pow2) {
                 pr = i64_to_f32x2(a, sh);
               } else {
                 v = i64_to_f64(a, sh);
