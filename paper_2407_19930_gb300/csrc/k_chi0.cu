@@ -762,11 +762,13 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
   oa.o_off = (const long long *)P.t_o_off.p;
   oa.o_sz_p = P.o_sz;
   oa.zero = zero;
-  // one launch per row-block size: the atoms U of each group (listed in the plan's table)
-  for (int gi = 0; gi < 4; ++gi) {
-    const int cnt = P.ugroup_off[gi + 1] - P.ugroup_off[gi];
+  // one launch per row-block size: the atoms U of each group (listed in the plan's table).  The
+  // FP64 arithmetic is bound by the FP64 pipe, where rows beyond n_U cost nothing: one launch over
+  // every atom with 16-row blocks (no tail of a second, small launch).
+  for (int gi = ar == 0 ? 3 : 0; gi < 4; ++gi) {
+    const int cnt = ar == 0 ? nat : P.ugroup_off[gi + 1] - P.ugroup_off[gi];
     if (!cnt) continue;
-    const int *ul = (const int *)P.t_ugroups.p + P.ugroup_off[gi];
+    const int *ul = (const int *)P.t_ugroups.p + (ar == 0 ? 0 : P.ugroup_off[gi]);
     dim3 og((unsigned)max_chunks, (unsigned)(np * cnt * nat));
     if (ar == 0)
       launch_oasm<ArD>(gi, og, 64 * NL, osmem, h.stream, oa, NL, ul, cnt);
