@@ -457,7 +457,7 @@ struct alignas(128) MapPair {
 
 // Pipelined, warp-specialised kernel: CTA c takes tiles c, c + gridDim.x, ... (128 x 64 output
 // tiles of the launch's entries, sorted by decreasing K range on the host), keeping its barriers and
-// TMEM across them (the launch uses one CTA per tile; the loop also serves a persistent grid).
+// TMEM across them (one CTA per tile, or a persistent grid of one CTA per SM: see gemm_multi).
 //   warp EW (one lane): TMA producer over a ring of NST shared-memory stages (each the NP digit
 //     planes of a 128 x 32 A slice and a 64 x 32 B slice, SWIZZLE_64B, K-major); the ring runs on
 //     across tiles, so the next tile's loads overlap this tile's MMAs and epilogue;
@@ -979,10 +979,14 @@ long long gemm_multi(const std::vector<std::pair<const Sliced *, const Sliced *>
   const Entry *de = (const Entry *)((const char *)args.p + off1);
   const Tile *dt = (const Tile *)((const char *)args.p + off2);
   const int *dc = (const int *)((const char *)args.p + off3);
-  // One CTA per tile: measured on GB300, these GEMMs (short K, many tiles) run faster with the tiles
-  // spread over as many CTAs as fit on an SM than with one persistent CTA per SM, which leaves the
-  // TMA loads and the epilogue of a single CTA exposed; the tile loop then runs once per CTA.
-  const int nt = (int)tk.size(), grid = nt;
+  // Grid: when two CTAs' stages fit in an SM's shared memory (fewer than 4 digit planes, the plain
+  // forms), one CTA per tile, so that several CTAs per SM hide each other's TMA waits and
+  // epilogues; with 4 or 5 planes only one CTA fits, and a persistent grid of one CTA per SM, its
+  // ring running on across tiles, was measured faster on GB300 (3.5 % on the chi0 GEMMs).
+  const int ring = NST * planes(S) * (BM + BN) * 64;
+  int nsm = 0;
+  LR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h.opts.device));
+  const int nt = (int)tk.size(), grid = 2 * (ring + 1024) > 227 * 1024 ? std::min(nt, nsm) : nt;
   // testing only: the handle's first opts.test_stall_gemms launches take the failure path
   uint64_t stall = 0;
   if (h.stalls_left > 0) {
