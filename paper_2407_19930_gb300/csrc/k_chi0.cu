@@ -379,6 +379,344 @@ __global__ void __launch_bounds__(256, 2) k_oassemble(OArgs a, int NL, const int
   }
 }
 
+// ------------------------------------------------------------ O assembly on the tensor cores
+// The same O = M + M* + Z + Z* for the tensor-core modes, as exact digit-plane products on the
+// BF16 tensor cores (mma.sync m16n8k16, FP32 accumulators).  Per nu of V, O_nu[i][kc] is the sum
+// of two products over K = 2 n_V:
+//   term 1:  Lm[i][t] . Nt_nu[t][kc]   Lm = [A_UV(R) | B_UV(R)],  Nt = [N[G^occ]; N[G^vir]] at ucol(kc)
+//   term 2:  LX_nu[i][t] . RG[t][kc]   LX = [X^A_nu | X^B_nu] (rows of U),  RG = [B_{V,kap}; A_{V,kap}]
+// Each row of an A operand (i, over t) and each column of a B operand (kc, over t) is scaled by a
+// power of two 2^-E (E: its largest |value| < 2^E) and cut into S balanced base-256 digits
+// x = sum_s d_s 2^{-7-8(s-1)}, |d_s| <= 128 (exact in BF16); the digit products of one diagonal
+// s + t are summed exactly on the tensor cores (|sum| <= 5 * 32 * 2^14 < 2^22 for K <= 32), the
+// diagonals folded into one int64 per term, the two terms aligned to the larger scale and
+// converted to FP64 once.  Inputs: N and X as (hi, lo) FP32 pairs, G as FP64 turned into pairs;
+// the low part joins the digits after the second (error below 2^-39 of the row or column
+// maximum).  One CTA of 4 warps per (point, U, V, 64-column chunk of U); warp w owns columns
+// c0 + 16 w .. + 16 (two n8 tiles) and runs over every nu.  Needs n_U, n_V <= 16.
+constexpr int kTcKP = 40;   // row pitch of a digit plane in BF16 elements (80 bytes: ldmatrix rows
+                            // of 8 consecutive planes rows fall in distinct 16-byte bank groups)
+constexpr float kRintMagic = 12582912.0f;   // 1.5 * 2^23: (x + M) - M rounds |x| < 2^22 to an integer
+
+__host__ __device__ constexpr int oasm_tc_smem(int S) {
+  // Lm, LX [S][16][KP]; RG [S][64][KP]; N [4][S][16][KP] (BF16); exponents: e1[16], e2[16], f2[64], f1[4][16]
+  return (S * 16 * kTcKP * 2 + S * 64 * kTcKP + 4 * S * 16 * kTcKP) * 2 + (16 + 16 + 64 + 64) * 4;
+}
+
+// E with max |value| < 2^E from the largest |hi| (0 for an all-zero row), kept in [-100, 100]
+__device__ __forceinline__ int tc_expo(float m) {
+  if (!(m > 0.f)) return 0;
+  const int be = (__float_as_int(m) >> 23) & 0xff;
+  return min(100, max(-100, be - 126));
+}
+__device__ __forceinline__ float tc_pow2(int k) { return __int_as_float((k + 127) << 23); }   // |k| <= 126
+
+// S digits of (h + l) 2^-E into d[] (sc7 = 2^{7-E}, sc15 = 2^{15-E})
+template <int S>
+__device__ __forceinline__ void tc_digits(float h, float l, float sc7, float sc15, float *d) {
+  float t = h * sc7;
+  float dd = (t + kRintMagic) - kRintMagic;
+  float r = t - dd;
+  d[0] = dd;
+#pragma unroll
+  for (int s = 1; s < S; ++s) {
+    if (s == 2) r = fmaf(l, sc15, r);   // the low part, in units of the third digit
+    t = r * 256.f;
+    dd = (t + kRintMagic) - kRintMagic;
+    r = t - dd;
+    d[s] = dd;
+  }
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // small integers: exact
+  return *reinterpret_cast<unsigned *>(&v);
+}
+__device__ __forceinline__ float2 g_pair(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float *c, const unsigned *a, unsigned b0, unsigned b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};\n"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Digit products of one term for the warp's two n8 tiles: A planes [S][16][KP] (rows i), B planes
+// [S][..][KP] (rows kc, from brow0), ks_n k-steps of 16; acc[d][nt][4] for the diagonals d = sa + sb.
+template <int S>
+__device__ __forceinline__ void tc_term(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int bplane, int brow0,
+                                        int ks_n, int lane, float (*acc)[2][4]) {
+#pragma unroll
+  for (int d = 0; d < S; ++d)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[d][nt][r] = 0.f;
+  const int arow = lane & 15, acol = (lane >> 4) * 8;
+  const int brow = brow0 + (lane & 7) + ((lane >> 4) << 3), bcol = ((lane >> 3) & 1) * 8;
+  for (int ks = 0; ks < ks_n; ++ks) {
+    unsigned a[S][4], b[S][4];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      ldsm_x4(smem_u32(A + (s * 16 + arow) * kTcKP + ks * 16 + acol), a[s][0], a[s][1], a[s][2], a[s][3]);
+      ldsm_x4(smem_u32(B + s * bplane + brow * kTcKP + ks * 16 + bcol), b[s][0], b[s][1], b[s][2], b[s][3]);
+    }
+#pragma unroll
+    for (int sa = 0; sa < S; ++sa)
+#pragma unroll
+      for (int sb = 0; sb < S - sa; ++sb) {
+        mma_bf16(acc[sa + sb][0], a[sa], b[sb][0], b[sb][1]);
+        mma_bf16(acc[sa + sb][1], a[sa], b[sb][2], b[sb][3]);
+      }
+  }
+}
+
+// sum_d A_d 2^{8(S-1-d)} of exact integer-valued FP32 diagonal sums (|A_d| < 2^22)
+template <int S>
+__device__ __forceinline__ long long tc_fold(const float *a) {
+  long long T = 0;
+#pragma unroll
+  for (int d = 0; d < S; ++d) {
+    const int v = (int)((unsigned)__float_as_int(a[d] + kRintMagic) - 0x4B400000u);
+    T = T * 256 + v;
+  }
+  return T;
+}
+
+template <int S>
+__global__ void __launch_bounds__(128) k_oassemble_tc(OArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __nv_bfloat16 *sLm = reinterpret_cast<__nv_bfloat16 *>(smraw);   // [S][16][KP]
+  __nv_bfloat16 *sLX = sLm + S * 16 * kTcKP;                        // [S][16][KP]
+  __nv_bfloat16 *sRG = sLX + S * 16 * kTcKP;                        // [S][64][KP]
+  __nv_bfloat16 *sN = sRG + S * 64 * kTcKP;                         // [4][S][16][KP]
+  int *sE1 = reinterpret_cast<int *>(sN + 4 * S * 16 * kTcKP);      // [16]
+  int *sE2 = sE1 + 16;                                              // [16]
+  int *sF2 = sE2 + 16;                                              // [64]
+  int *sF1 = sF2 + 64;                                              // [4][16]
+  const int V = blockIdx.y % a.natoms;
+  const int U = (blockIdx.y / a.natoms) % a.natoms;
+  const int p = blockIdx.y / (a.natoms * a.natoms);
+  const int mU = a.m[U];
+  const int c0 = blockIdx.x * 64;
+  if (c0 >= mU) return;
+  const int nU = a.n_ao[U], nV = a.n_ao[V], two = 2 * nV, nauxV = a.n_aux[V];
+  double *Ob = a.O + p * a.o_sz_p + a.o_off[U];
+  const int ldo = nU * mU;
+  if (a.zero && a.zero[((size_t)(p * a.natoms + U) * a.natoms + V) * gridDim.x + blockIdx.x]) {
+    const int w = min(64, mU - c0);
+    for (long long e = threadIdx.x; e < (long long)nauxV * nU * 64; e += blockDim.x) {
+      const int col = (int)(e % 64);
+      if (col >= w) continue;
+      const long long r = e / 64;
+      Ob[(size_t)(a.aux_off[V] + r / nU) * ldo + (size_t)(r % nU) * mU + c0 + col] = 0.0;
+    }
+    return;
+  }
+  const Point pt = a.pts[p];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const size_t n2 = (size_t)a.nao * a.nao;
+  const double *GB = a.G + ((size_t)pt.itau * a.nR_stride) * n2;                 // G^occ(tau)
+  const double *GA = a.G + a.g_gstride + ((size_t)pt.itau * a.nR_stride) * n2;   // G^vir(tau)
+  const int aoU = a.ao_off[U], aoV = a.ao_off[V];
+  const int ks_n = (two + 15) / 16;
+  // Lm digits (A of term 1): thread = (row i, 4 t); row exponent over the 8 lanes of the row
+  {
+    const int i = tid >> 3, t0 = (tid & 7) * 4;
+    float2 v[4];
+    float m = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = t0 + q;
+      v[q] = make_float2(0.f, 0.f);
+      if (i < nU && t < two) {
+        const double *Gs = t < nV ? GA : GB;
+        v[q] = g_pair(Gs[((size_t)pt.iR) * n2 + (size_t)(aoU + i) * a.nao + aoV + (t % nV)]);
+      }
+      m = fmaxf(m, fabsf(v[q].x));
+    }
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+    const int E = tc_expo(m);
+    if ((tid & 7) == 0) sE1[i] = E;
+    const float sc7 = tc_pow2(7 - E), sc15 = tc_pow2(15 - E);
+    float d[4][S];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tc_digits<S>(v[q].x, v[q].y, sc7, sc15, d[q]);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      uint2 w2 = make_uint2(pack_bf16(d[0][s], d[1][s]), pack_bf16(d[2][s], d[3][s]));
+      *reinterpret_cast<uint2 *>(sLm + (s * 16 + i) * kTcKP + t0) = w2;
+    }
+  }
+  // RG digits (B of term 2, stored [kc][t]): thread = (column, 16 t); column exponent over 2 lanes
+  {
+    const int col = tid >> 1, t0 = (tid & 1) * 16;
+    const int kc = c0 + col;
+    const bool live = kc < mU;
+    const int *kp = a.kap + 6 * (a.kap_off[U] + (live ? kc : 0));
+    auto fold = [](int x, int nn) { int r = x % nn; return r < 0 ? r + nn : r; };
+    const int iR = (fold(kp[1] - pt.R[0], a.n1) * a.n2 + fold(kp[2] - pt.R[1], a.n2)) * a.n3 +
+                   fold(kp[3] - pt.R[2], a.n3);
+    float2 v[16];
+    float m = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int t = t0 + q;
+      v[q] = make_float2(0.f, 0.f);
+      if (live && t < two) {
+        const double *Gs = t < nV ? GB : GA;
+        v[q] = g_pair(Gs[(size_t)iR * n2 + (size_t)(aoV + (t % nV)) * a.nao + kp[4]]);
+      }
+      m = fmaxf(m, fabsf(v[q].x));
+    }
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    const int E = tc_expo(m);
+    if ((tid & 1) == 0) sF2[col] = E;
+    const float sc7 = tc_pow2(7 - E), sc15 = tc_pow2(15 - E);
+#pragma unroll
+    for (int q0 = 0; q0 < 16; q0 += 8) {
+      float d[8][S];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) tc_digits<S>(v[q0 + q].x, v[q0 + q].y, sc7, sc15, d[q]);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        uint4 w4 = make_uint4(pack_bf16(d[0][s], d[1][s]), pack_bf16(d[2][s], d[3][s]), pack_bf16(d[4][s], d[5][s]),
+                              pack_bf16(d[6][s], d[7][s]));
+        *reinterpret_cast<uint4 *>(sRG + (s * 64 + col) * kTcKP + t0 + q0) = w4;
+      }
+    }
+  }
+  // this lane's column of the N operand: (column = lane & 15 of the warp's 16, t half = lane >> 4)
+  const int ncol = lane & 15, nt0 = (lane >> 4) * 16;
+  const int nkc = c0 + warp * 16 + ncol;
+  const bool nlive = nkc < mU;
+  const int ucol = a.kap[6 * (a.kap_off[U] + (nlive ? nkc : 0)) + 5];
+  const double *NB = a.N + p * a.n_sz_p + a.n_off[V];                 // N[G^occ]: g = 0
+  const double *NA = a.N + p * a.n_sz_p + a.n_sz_g + a.n_off[V];      // N[G^vir]: g = 1
+  const double *XB = a.X + p * a.x_sz_p + a.x_off[V];                 // X[G^occ]
+  const double *XA = a.X + p * a.x_sz_p + a.x_sz_g + a.x_off[V];      // X[G^vir]
+  const int ldx = nauxV * nV;
+  __nv_bfloat16 *sNw = sN + warp * S * 16 * kTcKP;
+  const int g = lane >> 2, tig = lane & 3;
+  for (int nu = 0; nu < nauxV; ++nu) {
+    // LX digits (A of term 2), shared by the 4 warps
+    {
+      const int i = tid >> 3, t0 = (tid & 7) * 4;
+      float2 v[4];
+      float m = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = t0 + q;
+        v[q] = make_float2(0.f, 0.f);
+        if (i < nU && t < two)
+          v[q] = *reinterpret_cast<const float2 *>((t < nV ? XA : XB) + (size_t)(aoU + i) * ldx + nu * nV + (t % nV));
+        m = fmaxf(m, fabsf(v[q].x));
+      }
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+      const int E = tc_expo(m);
+      if ((tid & 7) == 0) sE2[i] = E;
+      const float sc7 = tc_pow2(7 - E), sc15 = tc_pow2(15 - E);
+      float d[4][S];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tc_digits<S>(v[q].x, v[q].y, sc7, sc15, d[q]);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        uint2 w2 = make_uint2(pack_bf16(d[0][s], d[1][s]), pack_bf16(d[2][s], d[3][s]));
+        *reinterpret_cast<uint2 *>(sLX + (s * 16 + i) * kTcKP + t0) = w2;
+      }
+    }
+    // N digits (B of term 1) of the warp's 16 columns, stored [kc][t]
+    {
+      const double *Nn = NB + (size_t)nu * nV * a.m_all + ucol;
+      const double *Na = NA + (size_t)nu * nV * a.m_all + ucol;
+      float2 v[16];
+      float m = 0.f;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int t = nt0 + q;
+        v[q] = make_float2(0.f, 0.f);
+        if (nlive && t < two)
+          v[q] = *reinterpret_cast<const float2 *>((t < nV ? Nn : Na) + (size_t)(t % nV) * a.m_all);
+        m = fmaxf(m, fabsf(v[q].x));
+      }
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+      const int E = tc_expo(m);
+      if (lane < 16) sF1[warp * 16 + ncol] = E;
+      const float sc7 = tc_pow2(7 - E), sc15 = tc_pow2(15 - E);
+#pragma unroll
+      for (int q0 = 0; q0 < 16; q0 += 8) {
+        float d[8][S];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) tc_digits<S>(v[q0 + q].x, v[q0 + q].y, sc7, sc15, d[q]);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          uint4 w4 = make_uint4(pack_bf16(d[0][s], d[1][s]), pack_bf16(d[2][s], d[3][s]),
+                                pack_bf16(d[4][s], d[5][s]), pack_bf16(d[6][s], d[7][s]));
+          *reinterpret_cast<uint4 *>(sNw + (s * 16 + ncol) * kTcKP + nt0 + q0) = w4;
+        }
+      }
+    }
+    __syncthreads();   // LX, N and (first pass) Lm, RG digits and exponents written
+    float acc[S][2][4];
+    long long T1[2][4];
+    tc_term<S>(sLm, sNw, 16 * kTcKP, 0, ks_n, lane, acc);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float av[S];
+#pragma unroll
+        for (int d = 0; d < S; ++d) av[d] = acc[d][nt][r];
+        T1[nt][r] = tc_fold<S>(av);
+      }
+    tc_term<S>(sLX, sRG, 64 * kTcKP, warp * 16, ks_n, lane, acc);
+    double *orow = Ob + (size_t)(a.aux_off[V] + nu) * ldo;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = g + (r >> 1) * 8, cw = nt * 8 + 2 * tig + (r & 1), kc = c0 + warp * 16 + cw;
+        float av[S];
+#pragma unroll
+        for (int d = 0; d < S; ++d) av[d] = acc[d][nt][r];
+        const long long T2 = tc_fold<S>(av);
+        const int E1 = sE1[i] + sF1[warp * 16 + cw], E2 = sE2[i] + sF2[warp * 16 + cw];
+        long long T;
+        int E;
+        if (E1 >= E2) {
+          const int sh = E1 - E2;
+          T = T1[nt][r] + (sh == 0 ? T2 : sh >= 62 ? 0 : (T2 + (1LL << (sh - 1))) >> sh);
+          E = E1;
+        } else {
+          const int sh = E2 - E1;
+          T = T2 + (sh >= 62 ? 0 : (T1[nt][r] + (1LL << (sh - 1))) >> sh);
+          E = E2;
+        }
+        double o = (double)T;
+        if (T != 0) {
+          const long long bits = __double_as_longlong(o);
+          const int k = E - 14 - 8 * (S - 1);
+          const int ex = (int)((bits >> 52) & 0x7ff) + k;
+          o = ex <= 0 ? 0.0 : __longlong_as_double(bits + ((long long)k << 52));
+        }
+        if (i < nU && kc < mU) orow[(size_t)i * mU + kc] = o;
+      }
+    __syncthreads();   // every warp done with LX and the exponents before the next nu
+  }
+}
+
 template <class T>
 T *upload(Handle &h, DevBuf &b, const std::vector<T> &v) {
   h.ensure(b, std::max<size_t>(1, v.size()) * sizeof(T));
@@ -762,6 +1100,24 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
   oa.o_off = (const long long *)P.t_o_off.p;
   oa.o_sz_p = P.o_sz;
   oa.zero = zero;
+  if (ar != 0 && maxn <= 16) {
+    // tensor-core modes: digit-plane products on the tensor cores, one launch over every (U, V);
+    // 5 planes (~39 bits) for the FP64-accurate mode, 3 (~23 bits, as FP32) for the mixed modes
+    dim3 og((unsigned)max_chunks, (unsigned)(np * nat * nat));
+    if (ar == 2) {
+      constexpr int kSmem = oasm_tc_smem(5);
+      static_assert(kSmem <= kOasmSmemLimit, "O assembly (tensor cores): shared memory");
+      LR_CUDA(cudaFuncSetAttribute(k_oassemble_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+      k_oassemble_tc<5><<<og, 128, kSmem, h.stream>>>(oa);
+    } else {
+      constexpr int kSmem = oasm_tc_smem(3);
+      LR_CUDA(cudaFuncSetAttribute(k_oassemble_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+      k_oassemble_tc<3><<<og, 128, kSmem, h.stream>>>(oa);
+    }
+    ++launch_counter();
+    LR_CUDA(cudaGetLastError());
+    return;
+  }
   // one launch per row-block size: the atoms U of each group (listed in the plan's table).  The
   // FP64 arithmetic is bound by the FP64 pipe, where rows beyond n_U cost nothing: one launch over
   // every atom with 16-row blocks (no tail of a second, small launch).
