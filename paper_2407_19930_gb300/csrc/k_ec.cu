@@ -34,9 +34,11 @@ constexpr int NB = 64;
 
 // Factor the NB x NB diagonal block at p0 of every matrix in place (lower triangle).  One CTA per
 // matrix.  Adds 2 sum ln d_jj to lndet[b]; sets info[b] = 1 on a non-positive pivot.
+// inv (optional, [matrix][NB][NB]): receives L_pp^{-1} of the factored block (lower triangular,
+// zero elsewhere), computed in shared memory by forward substitution, one column per thread.
 __global__ void __launch_bounds__(256) k_potrf_diag(double2 *const *mats, int n, int ld, int p0, double *lndet,
-                                                    int *info) {
-  extern __shared__ double2 a[];   // [NB][NB + 1]
+                                                    int *info, double2 *inv) {
+  extern __shared__ double2 a[];   // [NB][NB + 1] (and, with inv, a second such array)
   const int b = blockIdx.x;
   double2 *M = mats[b];
   const int nb = min(NB, n - p0);
@@ -87,6 +89,28 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double2 *const *mats, int n,
   if (threadIdx.x == 0) {
     lndet[b] += lsum;
     if (bad) info[b] = 1;
+  }
+  if (inv) {
+    // y = L^{-1}: column j solves L y_j = e_j (y_ij = 0 for i < j); L's diagonal is real
+    double2 *y = a + NB * lda;
+    for (int j = threadIdx.x; j < NB; j += blockDim.x)
+      for (int i = 0; i < NB; ++i) {
+        double2 v = make_double2(0.0, 0.0);
+        if (j < nb && i < nb && i >= j) {
+          double sr = i == j ? 1.0 : 0.0, si = 0.0;
+          for (int k = j; k < i; ++k) {
+            const double2 l = a[i * lda + k], z = y[k * lda + j];
+            sr -= l.x * z.x - l.y * z.y;
+            si -= l.x * z.y + l.y * z.x;
+          }
+          const double d = a[i * lda + i].x;
+          v = make_double2(sr / d, si / d);
+        }
+        y[i * lda + j] = v;
+      }
+    __syncthreads();
+    double2 *Y = inv + (size_t)b * NB * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Y[e] = y[(e / NB) * lda + e % NB];
   }
 }
 
@@ -415,27 +439,58 @@ __global__ void k_energy(const double *lndet, const double *trace, const double 
 // Sliced-operand scratch of the tensor-core route.
 struct TcScratch {
   oz::Sliced pa, pb;      // panel of the trailing updates (as A' and as B'^T)
+  oz::Sliced pi;          // L_pp^{-H} of the panel solves (as B'^T)
+  double2 *inv = nullptr; // [matrix][NB][NB]: L_pp^{-1} of every matrix's current diagonal block
   int *err = nullptr;
   int S = 0;
 };
 
 // Blocked Cholesky of `mats` (n x n, lower, in place, uniform stride when tc != nullptr), in step.
+// inv_panel (tensor-core route, matrices whose diagonal blocks are well conditioned, such as
+// I - L^H chi0 L >= I): the panel solve X L_pp^H = B as the product X = B L_pp^{-H} on the tensor
+// cores, with L_pp^{-1} from the diagonal-block kernel; otherwise by substitution (FP64).
 void potrf_batched(Handle &h, double2 *const *d_mats, const std::vector<double2 *> &mats, int n, int ld,
-                   double *lndet, int *info, TcScratch *tc) {
+                   double *lndet, int *info, TcScratch *tc, bool inv_panel = false) {
   cudaStream_t s = h.stream;
   const int B = (int)mats.size();
   const size_t smem = (size_t)NB * (NB + 1) * sizeof(double2);
-  LR_CUDA(cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const bool use_inv = tc && inv_panel && tc->inv;
+  LR_CUDA(cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smem)));
   LR_CUDA(cudaFuncSetAttribute(k_trsm_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smem)));
   const long long bstride = B > 1 ? (long long)(mats[1] - mats[0]) : 0;
   for (int p0 = 0; p0 < n; p0 += NB) {
-    k_potrf_diag<<<B, 256, smem, s>>>(d_mats, n, ld, p0, lndet, info);
-    ++launch_counter();
     const int nb = std::min(NB, n - p0), rest = n - p0 - nb;
-    if (rest <= 0) break;
-    dim3 g((unsigned)((rest + 63) / 64), (unsigned)B);
-    k_trsm_panel<<<g, 64, 2 * smem, s>>>(d_mats, n, ld, p0);
+    const bool inv_now = use_inv && rest > 0;
+    k_potrf_diag<<<B, 256, inv_now ? 2 * smem : smem, s>>>(d_mats, n, ld, p0, lndet, info,
+                                                          inv_now ? tc->inv : nullptr);
     ++launch_counter();
+    if (rest <= 0) break;
+    if (inv_now) {
+      // X = B L_pp^{-H}: stacked real GEMM over the B matrices, K' = 2 nb, written over B
+      double2 *P = mats[0] + (size_t)(p0 + nb) * ld + p0;
+      oz::sliced_bind(tc->pa, tc->pa.digits, 2 * rest * B, 2 * nb, tc->S);
+      oz::sliced_bind(tc->pi, tc->pi.digits, nb * B, 2 * nb, tc->S);
+      oz::split_complex(P, ld, oz::OP_N, true, rest, nb, B, bstride, tc->pa, s);
+      oz::split_complex(tc->inv, NB, oz::OP_H, false, nb, nb, B, (long long)NB * NB, tc->pi, s);
+      oz::Out o;
+      o.C = (double *)P;
+      o.ldc = ld;
+      o.batch_stride = bstride;
+      o.mode = 1;
+      o.alpha = 1.0;
+      o.beta = 0.0;
+      Handle::Timed tm{nullptr, nullptr, 8.0 * B * rest * 0.5 * nb * nb, 1};
+      LR_CUDA(cudaEventCreate(&tm.a));
+      LR_CUDA(cudaEventCreate(&tm.b));
+      LR_CUDA(cudaEventRecord(tm.a, s));
+      oz::gemm(tc->pa, tc->pi, 2 * rest, nb, B, o, 0, 0, 0, tc->err, s, h);
+      LR_CUDA(cudaEventRecord(tm.b, s));
+      h.timed.push_back(tm);
+    } else {
+      dim3 g((unsigned)((rest + 63) / 64), (unsigned)B);
+      k_trsm_panel<<<g, 64, 2 * smem, s>>>(d_mats, n, ld, p0);
+      ++launch_counter();
+    }
     // algorithmic work: the lower triangle (with diagonal) of a rest x rest update of rank nb
     const double fl = 8.0 * B * (0.5 * rest * (rest + 1.0)) * nb;
     if (tc) {
@@ -559,7 +614,7 @@ size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 // lndet/trace/info, output, and for the tensor-core route the digit planes.
 struct EcLayout {
   size_t o_L, o_W, o_A, o_ptr, o_ld, o_tr, o_ldc, o_trc, o_inf, o_out, o_wo, o_wq, o_err;
-  size_t o_sx = 0, o_sw = 0, o_sl = 0, o_slh = 0, o_pa = 0, o_pb = 0;
+  size_t o_sx = 0, o_sw = 0, o_sl = 0, o_slh = 0, o_pa = 0, o_pb = 0, o_inv = 0, o_pi = 0;
   size_t total = 0;
 };
 
@@ -598,6 +653,8 @@ EcLayout ec_layout(const Handle &h) {
     l.o_slh = take(oz::sliced_bytes(2 * n, 2 * n, S));
     l.o_pa = take(oz::sliced_bytes(bmax * 2 * n, 2 * NB, S));
     l.o_pb = take(oz::sliced_bytes(bmax * n, 2 * NB, S));
+    l.o_inv = take((size_t)bmax * NB * NB * sizeof(double2));
+    l.o_pi = take(oz::sliced_bytes(bmax * NB, 2 * NB, S));
   }
   l.total = off;
   return l;
@@ -643,6 +700,8 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     tcs.err = err;
     oz::sliced_bind(tcs.pa, w + o_pa, bmax * 2 * n, 2 * NB, S);
     oz::sliced_bind(tcs.pb, w + o_pb, bmax * n, 2 * NB, S);
+    oz::sliced_bind(tcs.pi, w + lay.o_pi, bmax * NB, 2 * NB, S);
+    tcs.inv = (double2 *)(w + lay.o_inv);
     oz::sliced_bind(sx, w + o_sx, nw * 2 * n, 2 * n, S);
     oz::sliced_bind(sw, w + o_sw, nw * n, 2 * n, S);
     oz::sliced_bind(sl, w + o_sl, n, 2 * n, S);
@@ -789,7 +848,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     // A = I - L^H chi0 L of the chunk's (q, omega): trace, then one lockstep Cholesky of all
     k_diag_shift<<<(unsigned)ap.size(), 256, 0, s>>>(aptr, n, n, trace_c + (size_t)c0 * nw);
     ++launch_counter();
-    potrf_batched(h, aptr, ap, n, n, lndet_c + (size_t)c0 * nw, info + nq + (size_t)c0 * nw, tc);
+    potrf_batched(h, aptr, ap, n, n, lndet_c + (size_t)c0 * nw, info + nq + (size_t)c0 * nw, tc, true);
   }
   if (nql > nx) {
     // real route, all its (q, omega) in one lockstep batch, in the A region (real matrices take
