@@ -146,17 +146,28 @@ __global__ void k_row_expo(Src src, int rows, int K, int row0, int *expo) {
   if (lane == 0) expo[row0 + w] = m - 1022;
 }
 
+// one row per blockIdx.x, 4 consecutive k per thread (kpad is a multiple of 8): the row's scale and
+// source offsets are fetched once, each plane is written 8 bytes per thread
 template <int S, class Src>
-__global__ void k_digits(Src src, int rows, int K, int kpad, int row0, long long plane, const int *expo,
-                         __nv_bfloat16 *dig) {
-  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= (long long)rows * kpad) return;
-  const int r = (int)(x / kpad), k = (int)(x % kpad);
-  int d[S];
-  make_digits<S>(k < K ? src.get(r, k) : 0.0, expo[row0 + r], d);
-  const long long o = (long long)row0 * kpad + x;
+__global__ void __launch_bounds__(256) k_digits(Src src, int K, int kpad, int row0, long long plane, const int *expo,
+                                                __nv_bfloat16 *dig) {
+  const int r = blockIdx.x;
+  const int k0 = (blockIdx.y * 256 + threadIdx.x) * 4;
+  if (k0 >= kpad) return;
+  const int E = expo[row0 + r];
+  int d[4][S];
 #pragma unroll
-  for (int s = 0; s < S; ++s) dig[s * plane + o] = __float2bfloat16_rn((float)d[s]);
+  for (int q = 0; q < 4; ++q) make_digits<S>(k0 + q < K ? src.get(r, k0 + q) : 0.0, E, d[q]);
+  const long long o = ((long long)row0 + r) * kpad + k0;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn((float)d[0][s], (float)d[1][s]);
+    __nv_bfloat162 hi = __floats2bfloat162_rn((float)d[2][s], (float)d[3][s]);
+    uint2 w;
+    w.x = *reinterpret_cast<unsigned *>(&lo);
+    w.y = *reinterpret_cast<unsigned *>(&hi);
+    *reinterpret_cast<uint2 *>(dig + s * plane + o) = w;
+  }
 }
 
 template <class Src>
@@ -198,6 +209,7 @@ __global__ void k_plain_tf32(Src src, int rows, int K, int kpad, int row0, float
 template <class Src>
 void split_any(const Src &src, int rows, int K, int row0, Sliced &o, cudaStream_t s) {
   if (row0 < 0 || row0 + rows > o.rows || K > o.kpad) throw Error{LIBRPA_E_ARG, "split: rows or K exceed the operand"};
+  if (rows <= 0) return;
   const int kpad = o.kpad;
   const long long plane = (long long)o.rows * kpad;
   const long long n = (long long)rows * kpad;
@@ -219,12 +231,13 @@ void split_any(const Src &src, int rows, int K, int row0, Sliced &o, cudaStream_
   }
   __nv_bfloat16 *dig = (__nv_bfloat16 *)o.digits;
   k_row_expo<Src><<<(unsigned)(((long long)rows * 32 + 255) / 256), 256, 0, s>>>(src, rows, K, row0, o.expo);
+  const dim3 gd((unsigned)rows, (unsigned)((kpad + 1023) / 1024));
   switch (o.S) {
-    case 1: k_digits<1, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, dig); break;
-    case 2: k_digits<2, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, dig); break;
-    case 3: k_digits<3, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, dig); break;
-    case 4: k_digits<4, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, dig); break;
-    default: k_digits<5, Src><<<g, 256, 0, s>>>(src, rows, K, kpad, row0, plane, o.expo, dig); break;
+    case 1: k_digits<1, Src><<<gd, 256, 0, s>>>(src, K, kpad, row0, plane, o.expo, dig); break;
+    case 2: k_digits<2, Src><<<gd, 256, 0, s>>>(src, K, kpad, row0, plane, o.expo, dig); break;
+    case 3: k_digits<3, Src><<<gd, 256, 0, s>>>(src, K, kpad, row0, plane, o.expo, dig); break;
+    case 4: k_digits<4, Src><<<gd, 256, 0, s>>>(src, K, kpad, row0, plane, o.expo, dig); break;
+    default: k_digits<5, Src><<<gd, 256, 0, s>>>(src, K, kpad, row0, plane, o.expo, dig); break;
   }
   launch_counter() += 2;
   LR_CUDA(cudaGetLastError());
