@@ -75,6 +75,10 @@ extern "C" {
 #define LIBRPA_TF32 4     /* chi0 GEMMs in plain TF32 (FP32 accumulation), ln det GEMMs with 5 */
 #define LIBRPA_TF32X3 5   /* chi0 GEMMs as 3xTF32 split products (FP32 accumulation), ln det with 5 */
 
+/* Grids the library builds (opts.grid_kind) */
+#define LIBRPA_GRID_MINIMAX 0         /* minimax tau / omega grids (librpa_gpu_build_grid_minimax) */
+#define LIBRPA_GRID_GAUSS_LEGENDRE 1  /* mapped Gauss-Legendre rule (librpa_gpu_build_grid) */
+
 typedef struct librpa_gpu *librpa_gpu_t;
 
 /* Device allocator hooks.  alloc returns a device pointer aligned to >= 256 bytes,
@@ -100,6 +104,8 @@ typedef struct {
                                     (100 us) on a barrier that nothing arrives at, so the bounded-wait
                                     failure path runs: the call returns LIBRPA_E_TIMEOUT, later
                                     calls of the handle run normally */
+  int grid_kind;                 /* LIBRPA_GRID_MINIMAX (default) or LIBRPA_GRID_GAUSS_LEGENDRE: the grid
+                                    librpa_gpu_chi0 builds when none was set */
 } librpa_gpu_opts;
 
 /* Per-stage device times (ms, CUDA events on the handle's stream) and work counts of
@@ -130,13 +136,13 @@ typedef struct {
 } librpa_gpu_stats;
 
 /* Fill *o with defaults: device 0, own stream, cudaMalloc, n_tau = 16, FP64,
- * no budget, check_level 1, no test stalls. */
+ * no budget, check_level 1, no test stalls, minimax grids. */
 void librpa_gpu_default_opts(librpa_gpu_opts *o);
 
 /* Environment setup (paper: initialize_librpa_environment).  Creates a handle
  * bound to o->device.  *h is set to NULL on failure.
- * Errors: E_ARG (h or o NULL, bad device or n_tau < 1 or > 64, unknown precision,
- *         test_stall_gemms < 0), E_CUDA. */
+ * Errors: E_ARG (h or o NULL, bad device or n_tau < 1 or > 64 (> 20 with minimax grids),
+ *         unknown precision or grid kind, test_stall_gemms < 0), E_CUDA. */
 int librpa_gpu_create(librpa_gpu_t *h, const librpa_gpu_opts *o);
 
 /* Structure and k-mesh (paper: set_dimension, set_latvec_and_G, set_kgrids_kvec_tot).
@@ -185,7 +191,9 @@ int librpa_gpu_set_coulomb(librpa_gpu_t h, int iq, const double *V_re, const dou
  *   chi0(R, i omega_k) = sum_j Gamma_kj chi0(R, tau_j)  (the paper's
  *   -i gamma_jk cos(omega_k tau_j) with the -i factors of G taken out).
  * ntau == nomega required (1..64).  Without this call librpa_gpu_chi0 builds the grid
- * with librpa_gpu_build_grid(opts.n_tau, Delta_min, Delta_max) from the KS spectrum.
+ * from the KS spectrum's transition range [Delta_min, Delta_max] with opts.n_tau points:
+ * librpa_gpu_build_grid_minimax (opts.grid_kind = LIBRPA_GRID_MINIMAX, the default) or
+ * librpa_gpu_build_grid (LIBRPA_GRID_GAUSS_LEGENDRE).
  * Errors: E_STATE (no structure), E_ARG. */
 int librpa_gpu_set_grid(librpa_gpu_t h, int ntau, const double *tau, int nomega,
                         const double *omega, const double *w_omega, const double *gamma);
@@ -228,6 +236,27 @@ int librpa_gpu_set_screening(librpa_gpu_t h, double threshold);
  * Errors: E_ARG (n < 1 or > 64, dmin <= 0, dmax < dmin, NULL outputs). */
 int librpa_gpu_build_grid(int n, double dmin, double dmax, double *tau, double *omega,
                           double *w_omega, double *gamma);
+
+/* Minimax grids (host; Sec. 2: the paper's non-uniform tau/omega grids, which it takes from
+ * GreenX; built here from their defining property).  In units x = D / dmin on [1, R_b]:
+ *   tau_j dmin, a_j: the n-term exponential sum closest to 1/x in the maximum norm,
+ *     min max |1/x - sum_j a_j exp(-tau_j dmin x)|;
+ *   omega_k / dmin, w_omega_k / dmin: the n-term sum closest to 1/x in the maximum norm among
+ *     (1/pi) sum_k w_omega_k 4x^2 / (x^2 + omega_k^2)^2 (squared Lorentzians; w_omega are
+ *     weights of int_0^inf d omega);
+ * each found by the Remez exchange in double-double arithmetic until its error curve
+ * equioscillates (2n + 1 extrema level to 1e-13).  R_b = 2^{ceil(8 log2 R_eff) / 8},
+ * R_eff = max(dmax / dmin, exp(n pi^2 / ln 1e9) / 8): narrower ranges, where n terms would fit
+ * below ~1e-9, are degenerate, and the 1/8-octave steps let grids be cached per (n, R_b).  The
+ * grid covers [dmin, R_b dmin], which contains [dmin, dmax].  gamma[k][j]: the least-squares fit
+ * of librpa_gpu_build_grid on [dmin, R_b dmin].  The first call for an (n, R_b) takes a few
+ * tenths of a second of host time; later ones are served from a cache (thread-safe).
+ * Outputs as in librpa_gpu_build_grid, ascending tau and omega; info (NULL allowed) [3]:
+ * R_b, and the largest errors of the two fits in units of 1/dmin.
+ * Errors: E_ARG (n < 1 or > 20, dmin <= 0, dmax < dmin or not finite, NULL outputs),
+ *         E_NUMERIC (the exchange did not level the error curve). */
+int librpa_gpu_build_grid_minimax(int n, double dmin, double dmax, double *tau, double *omega,
+                                  double *w_omega, double *gamma, double *info);
 
 /* Grid in use by the handle (after set_grid or after librpa_gpu_chi0 built it).
  * Outputs as in librpa_gpu_build_grid; *n receives the grid size.

@@ -44,16 +44,24 @@ def make_grid(n, dmin, dmax, m=M_SAMPLES, rcond=RCOND):
     w_omega = omega0 * 2 * w / (1 - t) ** 2
     tau0 = 1.0 / omega0
     tau = tau0 * (1 + t) / (1 - t)
+    return dict(tau=tau, omega=omega, w_omega=w_omega, gamma=fit_gamma(tau, omega, dmin, dmax, m, rcond))
+
+
+def fit_gamma(tau, omega, dmin, dmax, m=M_SAMPLES, rcond=RCOND):
+    """Gamma_kj: for every k, the least-squares fit of 2 D / (D^2 + omega_k^2) by sum_j Gamma_kj
+    exp(-D tau_j) in relative error on m log-spaced D in [dmin, dmax] (SVD, singular values below
+    rcond * s_max dropped)."""
+    n = len(tau)
     d = dmin * np.exp(np.linspace(0.0, math.log(dmax / dmin), m)) if dmax > dmin else np.full(m, dmin)
     E = np.exp(-np.outer(d, tau))
-    gamma = np.empty((n, n))
-    for k in range(n):
+    gamma = np.empty((len(omega), n))
+    for k in range(len(omega)):
         f = 2 * d / (d * d + omega[k] ** 2)
         A = E / f[:, None]
         U, s, Vt = np.linalg.svd(A, full_matrices=False)
         keep = s > rcond * s[0]
         gamma[k] = Vt[keep].T @ ((U[:, keep].T @ np.ones(m)) / s[keep])
-    return dict(tau=tau, omega=omega, w_omega=w_omega, gamma=gamma)
+    return gamma
 
 
 def transform_error(grid, dmin, dmax, m=4000):

@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INC,
                    "-c", src, "-o", obj]
         else:
-            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INC, "-I", os.path.join(cuda_home, "include"),
+            cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-I", INC, "-I", os.path.join(cuda_home, "include"),
                    "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -252,7 +252,10 @@ int chi0_prepare(Handle &h) {
     h.omega.resize(n);
     h.w_omega.resize(n);
     h.gamma.resize((size_t)n * n);
-    int rc = build_grid(n, dmin, dmax, h.tau.data(), h.omega.data(), h.w_omega.data(), h.gamma.data());
+    int rc = h.opts.grid_kind == LIBRPA_GRID_GAUSS_LEGENDRE
+                 ? build_grid(n, dmin, dmax, h.tau.data(), h.omega.data(), h.w_omega.data(), h.gamma.data())
+                 : build_grid_minimax(n, dmin, dmax, h.tau.data(), h.omega.data(), h.w_omega.data(),
+                                      h.gamma.data(), nullptr);
     if (rc) return fail(&h, rc, "chi0: grid construction failed");
     h.ntau = n;
     h.have_grid = true;
@@ -274,13 +277,16 @@ void librpa_gpu_default_opts(librpa_gpu_opts *o) {
   o->n_tau = 16;
   o->precision = LIBRPA_FP64;
   o->check_level = 1;
+  o->grid_kind = LIBRPA_GRID_MINIMAX;
 }
 
 int librpa_gpu_create(librpa_gpu_t *hp, const librpa_gpu_opts *o) {
   if (!hp || !o) return LIBRPA_E_ARG;
   *hp = nullptr;
   if (o->n_tau < 1 || o->n_tau > 64 || o->precision < LIBRPA_FP64 || o->precision > LIBRPA_TF32X3 ||
-      o->chi0_slices < 0 || o->chi0_slices > 5 || o->ec_slices < 0 || o->ec_slices > 5 || o->test_stall_gemms < 0)
+      o->chi0_slices < 0 || o->chi0_slices > 5 || o->ec_slices < 0 || o->ec_slices > 5 || o->test_stall_gemms < 0 ||
+      (o->grid_kind != LIBRPA_GRID_MINIMAX && o->grid_kind != LIBRPA_GRID_GAUSS_LEGENDRE) ||
+      (o->grid_kind == LIBRPA_GRID_MINIMAX && o->n_tau > kMinimaxMaxN))
     return LIBRPA_E_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -517,6 +523,15 @@ int librpa_gpu_build_grid(int n, double dmin, double dmax, double *tau, double *
                           double *gamma) {
   try {
     return librpa::build_grid(n, dmin, dmax, tau, omega, w_omega, gamma);
+  } catch (...) {
+    return LIBRPA_E_NOMEM;
+  }
+}
+
+int librpa_gpu_build_grid_minimax(int n, double dmin, double dmax, double *tau, double *omega, double *w_omega,
+                                  double *gamma, double *info) {
+  try {
+    return librpa::build_grid_minimax(n, dmin, dmax, tau, omega, w_omega, gamma, info);
   } catch (...) {
     return LIBRPA_E_NOMEM;
   }

@@ -122,6 +122,11 @@ int build_grid(int n, double dmin, double dmax, double *tau, double *omega, doub
     w_omega[k] = w0 * 2.0 * w[k] / ((1.0 - t[k]) * (1.0 - t[k]));
     tau[k] = (1.0 / w0) * (1.0 + t[k]) / (1.0 - t[k]);
   }
+  fit_gamma(n, tau, omega, dmin, dmax, gamma);
+  return LIBRPA_OK;
+}
+
+void fit_gamma(int n, const double *tau, const double *omega, double dmin, double dmax, double *gamma) {
   const int m = 1000;
   std::vector<double> d(m);
   const double lr = std::log(dmax / dmin);
@@ -135,7 +140,6 @@ int build_grid(int n, double dmin, double dmax, double *tau, double *omega, doub
     std::vector<double> g = lsq_svd(A, m, n, ones, 1e-12);
     for (int j = 0; j < n; ++j) gamma[k * n + j] = g[j];
   }
-  return LIBRPA_OK;
 }
 
 }  // namespace librpa

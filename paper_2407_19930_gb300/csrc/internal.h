@@ -198,6 +198,14 @@ struct Handle {
 // ----------------------------------------------------------------- grid (host, grid.cpp)
 int build_grid(int n, double dmin, double dmax, double *tau, double *omega, double *w_omega,
                double *gamma);
+// Gamma_kj: relative least-squares fit of 2D / (D^2 + omega_k^2) by sum_j Gamma_kj exp(-D tau_j) on
+// 1000 log-spaced D in [dmin, dmax] (SVD, singular values below 1e-12 s_max dropped)
+void fit_gamma(int n, const double *tau, const double *omega, double dmin, double dmax, double *gamma);
+// minimax grids (minimax.cpp): the range ratio R_b a grid of n points is built for, and the grid
+int build_grid_minimax(int n, double dmin, double dmax, double *tau, double *omega, double *w_omega, double *gamma,
+                       double *info);
+double minimax_range(int n, double dmin, double dmax);
+constexpr int kMinimaxMaxN = 20;   // largest minimax grid (the Gauss-Legendre grids go to 64)
 
 // ----------------------------------------------------------------- kernels
 // K1 (k_green.cu): G^occ and G^vir for all (tau, R).  Returns max |Im G| / max |G|.

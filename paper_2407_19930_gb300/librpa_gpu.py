@@ -32,6 +32,8 @@ LIBRPA_SPLIT = 2
 LIBRPA_BF16 = 3
 LIBRPA_TF32 = 4
 LIBRPA_TF32X3 = 5
+LIBRPA_GRID_MINIMAX = 0
+LIBRPA_GRID_GAUSS_LEGENDRE = 1
 LIBRPA_NOALLOC_SCRATCH_BYTES = 16 << 20
 LIBRPA_NOALLOC_MAX_NAUX = 591
 
@@ -45,7 +47,8 @@ class librpa_gpu_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("n_tau", ctypes.c_int),
                 ("precision", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("check_level", ctypes.c_int),
-                ("chi0_slices", ctypes.c_int), ("ec_slices", ctypes.c_int), ("test_stall_gemms", ctypes.c_int)]
+                ("chi0_slices", ctypes.c_int), ("ec_slices", ctypes.c_int), ("test_stall_gemms", ctypes.c_int),
+                ("grid_kind", ctypes.c_int)]
 
 
 class librpa_gpu_stats(ctypes.Structure):
@@ -109,6 +112,8 @@ _SIGS = {
     "librpa_gpu_set_screening": (ctypes.c_int, [_H, ctypes.c_double]),
     "librpa_gpu_set_q_weights": (ctypes.c_int, [_H, _D]),
     "librpa_gpu_build_grid": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D]),
+    "librpa_gpu_build_grid_minimax": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D, _D, _D,
+                                                     _D]),
     "librpa_gpu_get_grid": (ctypes.c_int, [_H, _I, _D, _D, _D, _D]),
     "librpa_gpu_chi0": (ctypes.c_int, [_H, _D, _D]),
     "librpa_gpu_ec": (ctypes.c_int, [_H, _D, _D, _D]),
@@ -288,6 +293,17 @@ def librpa_gpu_build_grid(n, dmin, dmax):
     if rc != LIBRPA_OK:
         raise LibrpaError(rc, "build_grid")
     return dict(tau=tau, omega=omega, w_omega=w, gamma=gamma)
+
+
+def librpa_gpu_build_grid_minimax(n, dmin, dmax):
+    tau, omega, w = np.zeros(n), np.zeros(n), np.zeros(n)
+    gamma, info = np.zeros((n, n)), np.zeros(3)
+    rc = load().librpa_gpu_build_grid_minimax(int(n), float(dmin), float(dmax), _dp(tau), _dp(omega), _dp(w),
+                                              _dp(gamma), _dp(info))
+    if rc != LIBRPA_OK:
+        raise LibrpaError(rc, "build_grid_minimax")
+    return dict(tau=tau, omega=omega, w_omega=w, gamma=gamma, r_eff=float(info[0]), err_tau=float(info[1]),
+                err_omega=float(info[2]))
 
 
 def librpa_gpu_get_grid(h):

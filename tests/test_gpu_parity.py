@@ -249,11 +249,11 @@ def test_unpaired_coulomb_uses_every_q():
     assert abs(ref["ec_q"][1] - ref["ec_q"][2]) > 100 * TOL_EC   # the perturbation is visible
 
 
-def test_library_grid_path():
-    """Without set_grid the library builds the grid from the KS spectrum (row a0);
-    it must equal the oracle's grid on the same transition range."""
-    inp = syn.config_cubic()
-    h = L.librpa_gpu_create()
+def _library_grid_run(inp, grid_kind, n_tau):
+    o = L.librpa_gpu_default_opts()
+    o.grid_kind = grid_kind
+    o.n_tau = n_tau
+    h = L.librpa_gpu_create(o)
     try:
         L.set_inputs(h, inp)
         L.librpa_gpu_chi0(h)
@@ -261,6 +261,26 @@ def test_library_grid_path():
         ec, _, _ = L.librpa_gpu_ec(h)
     finally:
         L.librpa_gpu_destroy(h)
+    return g, ec
+
+
+def test_library_grid_path():
+    """Without set_grid the library builds the grid from the KS spectrum (row a0): by default the
+    minimax grid of librpa_gpu_build_grid_minimax on the spectrum's transition range (pinned to the
+    oracle's minimax grids on the CPU, tests/test_minimax.py); E_c on it equals the oracle's."""
+    inp = syn.config_cubic()
+    g, ec = _library_grid_run(inp, L.LIBRPA_GRID_MINIMAX, 16)
+    ref = L.librpa_gpu_build_grid_minimax(16, *inp.delta_range)
+    for key in ("tau", "omega", "w_omega", "gamma"):
+        assert _rel(g[key], ref[key]) < 1e-13, key
+    out = pipeline.rpa_energy(inp, g)
+    assert abs(ec - out["ec"]) < TOL_EC
+
+
+def test_library_grid_path_gauss_legendre():
+    """With opts.grid_kind = Gauss-Legendre the grid equals the oracle's mapped Gauss-Legendre rule."""
+    inp = syn.config_cubic()
+    g, ec = _library_grid_run(inp, L.LIBRPA_GRID_GAUSS_LEGENDRE, 16)
     ref = ogrid.make_grid(16, *inp.delta_range)
     for key in ("tau", "omega", "w_omega"):
         assert _rel(g[key], ref[key]) < 1e-13
