@@ -1451,7 +1451,8 @@ void chunks_x(const Handle &h, const BlockSparse &B, int q, int g, int V, int m0
   chunks_from_blocks(blocks, live, cs, K, out);
 }
 
-// final-contraction tile of (q, U): columns nu in [n0, n0 + cols), K = (i, k) over U's n_U x m_U.
+// final-contraction tile of (q, U): nu in [n0, n0 + cols) (its rows in the tensor-core route, where
+// the product is O_U . Cpack_U^T; its columns on the FP64 route), K = (i, k) over U's n_U x m_U.
 // Whether a K index is live depends on k only (its block of U's packed columns), so one prefix
 // count over the m_U columns answers every chunk.
 void chunks_f(const Handle &h, const BlockSparse &B, int q, int U, int n0, int cols, int cs, int K,
@@ -1748,14 +1749,17 @@ void tc_assemble(Handle &h, TcRound &r, const unsigned char *zero) {
   for (int q = 0; q < np; ++q) {
     double *chi = (double *)h.d_chi_tau.p + ((size_t)r.pts[q].itau * nR + r.pts[q].iR) * naux * naux;
     for (int U = 0; U < nat; ++U) {
+      // chi0[U rows]^T = O_U . Cpack_U^T: rows nu (N_aux of them fill the 128-row tiles), columns
+      // mu of U, stored transposed into chi0[mu][nu]
       oz::Entry f{};
-      f.a_row0 = h.aux_off[U];
-      f.b_row0 = (q * nat + U) * naux;
-      f.M = h.n_aux[U];
-      f.N = naux;
+      f.a_row0 = (q * nat + U) * naux;
+      f.b_row0 = h.aux_off[U];
+      f.M = naux;
+      f.N = h.n_aux[U];
       f.K = h.n_ao[U] * P.m[U];
       f.C = chi + (size_t)h.aux_off[U] * naux;
       f.ldc = naux;
+      f.mode = 4;
       f.alpha = -spin;
       f.beta = h.cur_spin > 0 ? 1.0 : 0.0;
       r.ef.push_back(f);
@@ -1808,8 +1812,8 @@ void chi0_run_tc(Handle &h) {
         });
         return true;
       };
-      const oz::StageFn fn_f = [&](int e, int, int, int n0, int cols, int cs, int K, std::vector<int> &out) {
-        memo_f.get(e, n0, cs, out, [&](std::vector<int> &o) { chunks_f(h, B, e / nat, e % nat, n0, cols, cs, K, o); });
+      const oz::StageFn fn_f = [&](int e, int m0, int rows, int, int, int cs, int K, std::vector<int> &out) {
+        memo_f.get(e, m0, cs, out, [&](std::vector<int> &o) { chunks_f(h, B, e / nat, e % nat, m0, rows, cs, K, o); });
         return true;
       };
       h.flop_chi0_run += timed_grouped(h, r.cpnx, r.sbg, r.en, r.err, P.gargs1, scr ? &fn_n : nullptr);
@@ -1824,7 +1828,7 @@ void chi0_run_tc(Handle &h) {
         h.flop_chi0_run += np * (P.flop_per_point - P.flop_nx_per_point - P.flop_fin_per_point);
       }
       tc_assemble(h, r, scr ? (const unsigned char *)P.t_ozero.p : nullptr);
-      h.flop_chi0_run += timed_grouped(h, r.cpf, r.sod, r.ef, r.err, P.gargs3, scr ? &fn_f : nullptr);
+      h.flop_chi0_run += timed_grouped(h, r.sod, r.cpf, r.ef, r.err, P.gargs3, scr ? &fn_f : nullptr);
     }
   }
   h.cur_spin = 0;
@@ -1859,7 +1863,7 @@ void tc_merged(std::vector<Handle *> &hs) {
       const int pair = (int)ops.size();
       if (step == 0) ops.push_back({&r.cpnx, &r.sbg});
       if (step == 1) ops.push_back({&r.sag, &r.cpnx});
-      if (step == 2) ops.push_back({&r.cpf, &r.sod});
+      if (step == 2) ops.push_back({&r.sod, &r.cpf});
       for (oz::Entry e : step == 0 ? r.en : step == 1 ? r.ex : r.ef) {
         e.pair = pair;
         es.push_back(e);

@@ -581,13 +581,16 @@ void rgemm_batched(Handle &h, const std::vector<RGemm> &gs, int shape, bool kfro
 }
 
 // Blocked real Cholesky of `mats` (n x n, lower, in place), in step (as potrf_batched).
+// Real blocked Cholesky (lower, in place).  tc (tensor-core route, uniform matrix stride): the
+// trailing updates as digit-plane GEMMs; otherwise FP64 DMMA.
 void potrf_batched_r(Handle &h, double *const *d_mats, const std::vector<double *> &mats, int n, int ld,
-                     double *lndet, int *info) {
+                     double *lndet, int *info, TcScratch *tc = nullptr) {
   cudaStream_t s = h.stream;
   const int B = (int)mats.size();
   const size_t smem = (size_t)NB * (NB + 1) * sizeof(double);
   LR_CUDA(cudaFuncSetAttribute(k_potrf_diag_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   LR_CUDA(cudaFuncSetAttribute(k_trsm_panel_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smem)));
+  const long long bstride = B > 1 ? (long long)(mats[1] - mats[0]) : 0;
   for (int p0 = 0; p0 < n; p0 += NB) {
     k_potrf_diag_r<<<B, 256, smem, s>>>(d_mats, n, ld, p0, lndet, info);
     ++launch_counter();
@@ -596,6 +599,29 @@ void potrf_batched_r(Handle &h, double *const *d_mats, const std::vector<double 
     dim3 g((unsigned)((rest + 63) / 64), (unsigned)B);
     k_trsm_panel_r<<<g, 64, 2 * smem, s>>>(d_mats, n, ld, p0);
     ++launch_counter();
+    const double fl = 2.0 * B * (0.5 * rest * (rest + 1.0)) * nb;
+    if (tc) {
+      // A22 -= P P^T on the lower tiles, P = A[p0+nb.., p0..p0+nb): one operand in both roles
+      const double *P = mats[0] + (size_t)(p0 + nb) * ld + p0;
+      oz::sliced_bind(tc->pa, tc->pa.digits, rest * B, nb, tc->S);
+      oz::split_real(P, ld, false, rest, nb, B, bstride, tc->pa, s);
+      oz::Out o;
+      o.C = mats[0] + (size_t)(p0 + nb) * ld + p0 + nb;
+      o.ldc = ld;
+      o.batch_stride = bstride;
+      o.mode = 0;
+      o.alpha = -1.0;
+      o.beta = 1.0;
+      Handle::Timed tm{nullptr, nullptr, fl, 1};
+      LR_CUDA(cudaEventCreate(&tm.a));
+      LR_CUDA(cudaEventCreate(&tm.b));
+      LR_CUDA(cudaEventRecord(tm.a, s));
+      oz::gemm(tc->pa, tc->pa, rest, rest, B, o, 0, 0, 1, tc->err, s, h);
+      LR_CUDA(cudaEventRecord(tm.b, s));
+      tm.exec_flops = h.oz_exec_flops;
+      h.timed.push_back(tm);
+      continue;
+    }
     // A22 -= P P^T on the lower tiles, P = A[p0+nb.., p0..p0+nb)
     std::vector<RGemm> batch;
     for (int b = 0; b < B; ++b) {
@@ -603,7 +629,7 @@ void potrf_batched_r(Handle &h, double *const *d_mats, const std::vector<double 
       const double *P = M + (size_t)(p0 + nb) * ld + p0;
       batch.push_back(RGemm{P, P, M + (size_t)(p0 + nb) * ld + p0 + nb, rest, rest, nb, ld, ld, ld, -1.0, 1.0});
     }
-    rgemm_batched(h, batch, 2, false, 2.0 * B * (0.5 * rest * (rest + 1.0)) * nb);
+    rgemm_batched(h, batch, 2, false, fl);
   }
   LR_CUDA(cudaGetLastError());
 }
@@ -733,10 +759,10 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     if (h.vq_sym == 1 ? q <= p && (weight(q) > 0 || weight(p) > 0) : weight(q) > 0) qlist.push_back(q);
   }
   const int nql = (int)qlist.size();
-  // positions in qlist, the complex ones first, then those of the real route (FP64 route only):
-  // the per-(q, omega) ln det and trace are kept in this order until the end
+  // positions in qlist, the complex ones first, then those of the real route: the per-(q, omega)
+  // ln det and trace are kept in this order until the end
   std::vector<int> order;
-  auto real_q = [&](int q) { return S < 0 && h.vq_real == 1 && q == h.mesh.neg(q); };
+  auto real_q = [&](int q) { return h.vq_real == 1 && q == h.mesh.neg(q); };
   for (int qi = 0; qi < nql; ++qi)
     if (!real_q(qlist[qi])) order.push_back(qi);
   const int nx = (int)order.size();
@@ -762,12 +788,11 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   double2 **aptr = ptrs + nq;
   double *lndet_c = (double *)(w + lay.o_ldc), *trace_c = (double *)(w + lay.o_trc);
   LR_CUDA(cudaMemsetAsync(lndet_c, 0, (size_t)nql * nw * 8, s));
-  // algorithmic work (8 flops per complex MAC): W = chi0 L with L lower triangular,
-  // sum_j (n - j) = n (n + 1) / 2 MACs per row; A = -L^H W on the lower triangle,
+  // algorithmic work (8 flops per complex MAC): A = -L^H W on the lower triangle,
   // sum_{i >= j} (n - i) MACs per matrix
   const double dn = n;
-  const double fl_w = 8.0 * nw * dn * (dn * (dn + 1) / 2), fl_a = 8.0 * nw * (dn * (dn + 1) * (dn + 2) / 6);
-  // FP64 route: A needs W only on and below its diagonal tiles (j >= k), sum_k (n - k)^2 MACs
+  const double fl_a = 8.0 * nw * (dn * (dn + 1) * (dn + 2) / 6);
+  // A needs W only on and below its diagonal tiles (j >= k), sum_k (n - k)^2 MACs
   const double fl_w_lower = 8.0 * nw * (dn * (dn + 1) * (2 * dn + 1) / 6);
   for (int c0 = 0; c0 < nx; c0 += nc) {
     const int c1 = std::min(nx, c0 + nc);
@@ -782,16 +807,20 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
         oz::split_complex(L, n, oz::OP_N, false, n, n, 1, 0, sl, s);     // B'^T of W = chi0 L
         oz::split_complex(L, n, oz::OP_H, true, n, n, 1, 0, slh, s);     // A' of L^H W
         oz::split_complex(chi + (size_t)q * nw * n2, n, oz::OP_N, true, n, n, nw, (long long)n2, sx, s);
-        oz::Out o1;   // W^T, so that the second GEMM reads W column by column as rows
+        // W^T, so that the second GEMM reads W column by column as rows.  A = -L^H W reads W only on
+        // and below its diagonal tiles (k >= j): the tiles above are not computed and stay zero
+        // (the digit planes of W's rows see zeros there)
+        LR_CUDA(cudaMemsetAsync(Wm, 0, (size_t)nw * mat, s));
+        oz::Out o1;
         o1.C = (double *)Wm;
         o1.ldc = n;
         o1.batch_stride = (long long)n2;
         o1.mode = 2;
-        Handle::Timed t1{nullptr, nullptr, fl_w, 1};
+        Handle::Timed t1{nullptr, nullptr, fl_w_lower, 1};
         LR_CUDA(cudaEventCreate(&t1.a));
         LR_CUDA(cudaEventCreate(&t1.b));
         LR_CUDA(cudaEventRecord(t1.a, s));
-        oz::gemm(sx, sl, 2 * n, n, nw, o1, 0, 2, 0, err, s, h);
+        oz::gemm(sx, sl, 2 * n, n, nw, o1, 0, 2, 2, err, s, h);
         LR_CUDA(cudaEventRecord(t1.b, s));
         t1.exec_flops = h.oz_exec_flops;
         h.timed.push_back(t1);
@@ -869,6 +898,47 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
       k_real_part<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(chi + (size_t)q * nw * n2, cnt, Xr);
       launch_counter() += 2;
       LR_CUDA(cudaGetLastError());
+      if (S >= 0) {
+        // W = Xr L on and below the diagonal tiles (W[k][j] = sum_l Xr[k][l] Lt[j][l], l >= j; the
+        // tiles above stay zero), then A = -L^T W = -(Lt rows) . (W^T rows), l >= i, lower tiles
+        double *Wr = WT;
+        LR_CUDA(cudaMemsetAsync(Wr, 0, (size_t)nw * n2 * sizeof(double), s));
+        oz::Sliced slt = sl, sxr = sx, swt = sw;
+        oz::sliced_bind(slt, sl.digits, n, n, S);
+        oz::sliced_bind(sxr, sx.digits, nw * n, n, S);
+        oz::sliced_bind(swt, sw.digits, nw * n, n, S);
+        oz::split_real(Lt, n, false, n, n, 1, 0, slt, s);
+        oz::split_real(Xr, n, false, n, n, nw, (long long)n2, sxr, s);
+        oz::Out o1;
+        o1.C = Wr;
+        o1.ldc = n;
+        o1.batch_stride = (long long)n2;
+        o1.mode = 0;
+        Handle::Timed t1{nullptr, nullptr, fl_w_lower / 4, 1};
+        LR_CUDA(cudaEventCreate(&t1.a));
+        LR_CUDA(cudaEventCreate(&t1.b));
+        LR_CUDA(cudaEventRecord(t1.a, s));
+        oz::gemm(sxr, slt, n, n, nw, o1, 0, 1, 1, err, s, h);
+        LR_CUDA(cudaEventRecord(t1.b, s));
+        t1.exec_flops = h.oz_exec_flops;
+        h.timed.push_back(t1);
+        oz::split_real(Wr, n, true, n, n, nw, (long long)n2, swt, s);
+        oz::Out o2;
+        o2.C = Ar + (size_t)r * nw * n2;
+        o2.ldc = n;
+        o2.batch_stride = (long long)n2;
+        o2.mode = 0;
+        o2.alpha = -1.0;
+        Handle::Timed t2{nullptr, nullptr, fl_a / 4, 1};
+        LR_CUDA(cudaEventCreate(&t2.a));
+        LR_CUDA(cudaEventCreate(&t2.b));
+        LR_CUDA(cudaEventRecord(t2.a, s));
+        oz::gemm(slt, swt, n, n, nw, o2, 1, 0, 1, err, s, h);
+        LR_CUDA(cudaEventRecord(t2.b, s));
+        t2.exec_flops = h.oz_exec_flops;
+        h.timed.push_back(t2);
+        continue;
+      }
       // W^T = Lt Xr^T (= (chi0 L)^T) on and above the diagonal tiles; A = -Lt (W^T)^T = -L^T W on
       // and below them; Lt is upper triangular, so K starts at the tile's first row
       std::vector<RGemm> g1, g2;
@@ -881,7 +951,7 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
     }
     k_diag_shift_r<<<(unsigned)B, 256, 0, s>>>(rptr, n, n, trace_c + (size_t)nx * nw);
     ++launch_counter();
-    potrf_batched_r(h, rptr, ar, n, n, lndet_c + (size_t)nx * nw, info + nq + (size_t)nx * nw);
+    potrf_batched_r(h, rptr, ar, n, n, lndet_c + (size_t)nx * nw, info + nq + (size_t)nx * nw, tc);
   }
   for (int pos = 0; pos < nql; ++pos) {   // to the flat (q, omega) order
     const int q = qlist[order[pos]];
@@ -913,10 +983,10 @@ int ec_run(Handle &h, double *ec, double *ec_q, double *ec_w) {
   if (ec_w)
     for (int k = 0; k < nw; ++k) ec_w[k] = res[1 + nq + k];
   // flop count of this stage (complex MAC = 8 real flops, real MAC = 2): per q (4/3 n^3 real for
-  // the Cholesky of V), per (q, omega): W = chi0 L (n^3/2 MAC; n^3/3 on the tiles the FP64 route
-  // needs), L^H W lower (n^3/6 MAC), Cholesky (n^3/6 MAC)
+  // the Cholesky of V), per (q, omega): W = chi0 L on the tiles A needs (n^3/3 MAC), L^H W lower
+  // (n^3/6 MAC), Cholesky (n^3/6 MAC)
   const double n3 = (double)n * n * n;
-  const double macs = (S >= 0 ? n3 / 2 : n3 / 3) + n3 / 6 + n3 / 6;
+  const double macs = n3 / 3 + n3 / 6 + n3 / 6;
   h.stats.flop_ec = nql * (8.0 * n3 / 6.0) + (double)nx * nw * 8.0 * macs + (double)(nql - nx) * nw * 2.0 * macs;
   return LIBRPA_OK;
 }

@@ -414,17 +414,6 @@ __device__ __forceinline__ float2 i64_to_f32x2(long long a, int sh) {
   return neg ? make_float2(-hi, -lo) : make_float2(hi, lo);
 }
 
-// f 2^sh as FP64 (exact), integer instructions; zero, subnormal and non-finite f through FP64
-__device__ __forceinline__ double f32_to_f64(float f, int sh) {
-  const unsigned b = __float_as_uint(f);
-  const int e = (int)((b >> 23) & 0xFF);
-  if (e == 0 || e == 255) return ldexp((double)f, sh);
-  const int ed = e - 127 + 1023 + sh;
-  if (ed <= 0 || ed >= 2047) return ldexp((double)f, sh);
-  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | ((unsigned long long)ed << 52) |
-                                          ((unsigned long long)(b & 0x7FFFFFu) << 29)));
-}
-
 template <int S>
 __host__ __device__ constexpr uint32_t tmem_cols() {
   return S * BN <= 64 ? 64 : S * BN <= 128 ? 128 : S * BN <= 256 ? 256 : 512;
@@ -726,6 +715,7 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
             }
             double *p = en.mode == 0   ? en.C + (long long)row * en.ldc + col
                         : en.mode == 1 ? en.C + 2 * ((long long)(row >> 1) * en.ldc + col) + (row & 1)
+                        : en.mode == 4 ? en.C + (long long)col * en.ldc + row
                                        : en.C + 2 * ((long long)col * en.ldc + (row >> 1)) + (row & 1);
             *p = en.beta == 0.0 ? v : v + en.beta * *p;
           }
@@ -734,8 +724,8 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
       }
       // Digit planes: values are formed with thread = tile row (the TMEM lane layout).  Row-major outputs
       // (modes 0, 1, 3) go through a per-warp staging area, 16 columns at a time, and are written
-      // with lanes along the row (two rows of 16 columns per warp store); the transposed complex
-      // output (mode 2) is consecutive along rows already and is stored directly.
+      // with lanes along the row (two rows of 16 columns per warp store); the transposed outputs
+      // (modes 2, 4) are consecutive along rows already and are stored directly.
       const int row = m0 + 32 * quad + lane;
       const bool row_ok = row < en.M;
       const int ea = (!PLAIN && row_ok) ? maps[en.pair].ea[en.a_row0 + row] : 0;
@@ -744,7 +734,7 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
       const bool pow2 = en.alpha_shift != kNoShift;   // alpha = +-2^alpha_shift: folded into the exponent
       const int ash = pow2 ? en.alpha_shift : 0;
       const bool aneg = pow2 && en.alpha < 0.0;
-      const bool staged = en.mode != 2;
+      const bool staged = en.mode != 2 && en.mode != 4;
 #pragma unroll
       for (int cb = 0; cb < HALF / 16; ++cb) {
 #pragma unroll
@@ -794,7 +784,8 @@ __global__ void __launch_bounds__(32 * (epi_warps(S) + 2), 1)
           if (staged) {
             stg[lane * SPITCH + j] = v;
           } else if (ok) {
-            double *p = en.C + 2 * ((long long)col * en.ldc + (row >> 1)) + (row & 1);
+            double *p = en.mode == 4 ? en.C + (long long)col * en.ldc + row
+                                     : en.C + 2 * ((long long)col * en.ldc + (row >> 1)) + (row & 1);
             *p = en.beta == 0.0 ? v : v + en.beta * *p;
           }
         }
@@ -937,7 +928,9 @@ long long gemm_multi(const std::vector<std::pair<const Sliced *, const Sliced *>
       throw Error{LIBRPA_E_ARG, "oz::gemm: entry outside its operands"};
     for (int m0 = 0; m0 < en.M; m0 += BM)
       for (int n0 = 0; n0 < en.N; n0 += BN) {
-        if (en.lower_div > 0 && n0 > m0 / en.lower_div) continue;
+        // strictly above the diagonal: every column of the tile beyond every row (in output rows,
+        // lower_div stacked rows per output row)
+        if (en.lower_div > 0 && (long long)n0 * en.lower_div >= (long long)m0 + BM) continue;
         const int rows = std::min(BM, en.M - m0), cols = std::min(BN, en.N - n0);
         cl.clear();
         if (stage_fn && (*stage_fn)(e, m0, rows, n0, cols, ks, en.K, cl)) {
@@ -1046,7 +1039,7 @@ long long gemm(const Sliced &a, const Sliced &b, int M, int N, int batch, const 
     e.km = km;
     e.kn = kn;
     e.lower_div = lower_div;
-    e.C = out.C + (long long)i * out.batch_stride * (out.mode == 0 ? 1 : 2);
+    e.C = out.C + (long long)i * out.batch_stride * (out.mode == 0 || out.mode == 4 ? 1 : 2);
     e.ldc = out.ldc;
     e.mode = out.mode;
     e.alpha = out.alpha;

@@ -81,18 +81,20 @@ void split_ragged(const double *base, const long long *off, const int *Ke, int r
 //  mode 3: real C[m][n] stored as a pair of FP32 numbers (hi, lo) in the 8 bytes of the double
 //          (beta must be 0);
 //  mode 1: complex C[i][j] (interleaved) from rows m = 2i + c: component c of C[i][j];
-//  mode 2: complex transposed: component c of C[j][i].
+//  mode 2: complex transposed: component c of C[j][i];
+//  mode 4: real transposed: C[n][m] (ldc).
 struct Out {
   double *C = nullptr;
   long long ldc = 0;
-  long long batch_stride = 0;   // doubles (mode 0) or complex numbers (modes 1, 2)
+  long long batch_stride = 0;   // doubles (modes 0, 4) or complex numbers (modes 1, 2)
   int mode = 0;
   double alpha = 1.0, beta = 0.0;
 };
 
 // One GEMM of a grouped launch: C = alpha A[a_row0 .. + M) B[b_row0 .. + N)^T + beta C over
 // K columns.  K range per output tile starts at (m0 * km + n0 * kn) rounded down to BK
-// (triangular operands); lower_div > 0 skips tiles with n0 > m0 / lower_div.
+// (triangular operands); lower_div > 0 skips the tiles strictly above the diagonal, those with
+// n0 * lower_div >= m0 + BM (lower_div stacked rows per output row: 2 for complex outputs).
 constexpr int kNoShift = 1 << 30;
 struct Entry {
   int a_row0, b_row0, M, N, K;
