@@ -482,13 +482,19 @@ __device__ __forceinline__ void tc_term(const __nv_bfloat16 *A, const __nv_bfloa
 // sum_d A_d 2^{8(S-1-d)} of exact integer-valued FP32 diagonal sums (|A_d| < 2^22)
 template <int S>
 __device__ __forceinline__ long long tc_fold(const float *a) {
-  long long T = 0;
+  int v[S];
 #pragma unroll
-  for (int d = 0; d < S; ++d) {
-    const int v = (int)((unsigned)__float_as_int(a[d] + kRintMagic) - 0x4B400000u);
-    T = T * 256 + v;
+  for (int d = 0; d < S; ++d) v[d] = (int)((unsigned)__float_as_int(a[d] + kRintMagic) - 0x4B400000u);
+  if constexpr (S == 5) {   // v0 2^8 + v1 and v3 2^8 + v4 stay below 2^31
+    return ((long long)(v[0] * 256 + v[1]) << 24) + ((long long)v[2] << 16) + (long long)(v[3] * 256 + v[4]);
+  } else if constexpr (S == 3) {
+    return ((long long)v[0] << 16) + (long long)(v[1] * 256 + v[2]);
+  } else {
+    long long T = 0;
+#pragma unroll
+    for (int d = 0; d < S; ++d) T = T * 256 + v[d];
+    return T;
   }
-  return T;
 }
 
 template <int S>
@@ -539,7 +545,7 @@ __global__ void __launch_bounds__(128) k_oassemble_tc(OArgs a) {
       v[q] = make_float2(0.f, 0.f);
       if (i < nU && t < two) {
         const double *Gs = t < nV ? GA : GB;
-        v[q] = g_pair(Gs[((size_t)pt.iR) * n2 + (size_t)(aoU + i) * a.nao + aoV + (t % nV)]);
+        v[q] = g_pair(Gs[((size_t)pt.iR) * n2 + (size_t)(aoU + i) * a.nao + aoV + (t < nV ? t : t - nV)]);
       }
       m = fmaxf(m, fabsf(v[q].x));
     }
@@ -575,7 +581,7 @@ __global__ void __launch_bounds__(128) k_oassemble_tc(OArgs a) {
       v[q] = make_float2(0.f, 0.f);
       if (live && t < two) {
         const double *Gs = t < nV ? GB : GA;
-        v[q] = g_pair(Gs[(size_t)iR * n2 + (size_t)(aoV + (t % nV)) * a.nao + kp[4]]);
+        v[q] = g_pair(Gs[(size_t)iR * n2 + (size_t)(aoV + (t < nV ? t : t - nV)) * a.nao + kp[4]]);
       }
       m = fmaxf(m, fabsf(v[q].x));
     }
@@ -619,7 +625,8 @@ __global__ void __launch_bounds__(128) k_oassemble_tc(OArgs a) {
         const int t = t0 + q;
         v[q] = make_float2(0.f, 0.f);
         if (i < nU && t < two)
-          v[q] = *reinterpret_cast<const float2 *>((t < nV ? XA : XB) + (size_t)(aoU + i) * ldx + nu * nV + (t % nV));
+          v[q] = *reinterpret_cast<const float2 *>(t < nV ? XA + (size_t)(aoU + i) * ldx + nu * nV + t
+                                                          : XB + (size_t)(aoU + i) * ldx + nu * nV + (t - nV));
         m = fmaxf(m, fabsf(v[q].x));
       }
       m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
@@ -648,7 +655,7 @@ __global__ void __launch_bounds__(128) k_oassemble_tc(OArgs a) {
         const int t = nt0 + q;
         v[q] = make_float2(0.f, 0.f);
         if (nlive && t < two)
-          v[q] = *reinterpret_cast<const float2 *>((t < nV ? Nn : Na) + (size_t)(t % nV) * a.m_all);
+          v[q] = *reinterpret_cast<const float2 *>(t < nV ? Nn + (size_t)t * a.m_all : Na + (size_t)(t - nV) * a.m_all);
         m = fmaxf(m, fabsf(v[q].x));
       }
       m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));

@@ -13,9 +13,26 @@
 #include <vector>
 
 #include "internal.h"
+#include "ozgemm.h"
 
 namespace librpa {
 namespace {
+
+// digit planes of the G build in the tensor-core modes (FP64-accurate products)
+constexpr int kGreenS = 5;
+
+// Y[g][k][n][i] = sqrt(w[g][k][n]) c_in(k) (the weights are >= 0), so that P^g_k = Y^T conj(Y)
+__global__ void k_scale_bands(const double2 *wfc, const double *w, int nk, int nb, int nao, double2 *Y) {
+  const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t per_g = (size_t)nk * nb * nao;
+  if (x >= 2 * per_g) return;
+  const int g = (int)(x / per_g);
+  const size_t kni = x % per_g;
+  const size_t kn = kni / nao;
+  const double sw = sqrt(w[(size_t)g * nk * nb + kn]);
+  const double2 c = wfc[kni];
+  Y[x] = make_double2(sw * c.x, sw * c.y);
+}
 
 // w[g][k][n] for one tau: g = 0 occupied weight f e^{-(mu - e) tau}, g = 1 virtual weight
 // (1 - f) e^{-(e - mu) tau}
@@ -125,7 +142,11 @@ size_t green_work_bytes(const Handle &h) {
   const size_t nk = h.mesh.size(), nR = nk, nb = h.nao, n2 = (size_t)h.nao * h.nao;
   const size_t b_e = nk * nb * 8, b_w = 2 * b_e, b_p = 2 * nk * n2 * 16, b_t = nk * nR * 16;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  return al(b_w) + al(b_p) + al(b_t) + 256;
+  size_t b = al(b_w) + al(b_p) + al(b_t) + 256;
+  if (h.chi0_S >= 0)   // tensor-core modes: Y and the digit planes of both GEMM roles
+    b += al(b_p) + oz::sliced_bytes((int)(2 * nk * 2 * h.nao), (int)(2 * nb), kGreenS) +
+         oz::sliced_bytes((int)(2 * nk * h.nao), (int)(2 * nb), kGreenS) + 256;
+  return b;
 }
 
 double green_build(Handle &h) {
@@ -139,8 +160,21 @@ double green_build(Handle &h) {
                b_t = (size_t)nk * nR * 16;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t o_w = 0, o_p = o_w + al(b_w), o_t = o_p + al(b_p), o_m = o_t + al(b_t);
+  // tensor-core modes: P^g_k = Y^T conj(Y) as one batched digit-plane GEMM per tau (FP64-accurate)
+  const bool tc = h.chi0_S >= 0;
+  const size_t o_y = o_m + 256, o_sa = o_y + al(b_p),
+               o_sb = o_sa + oz::sliced_bytes(2 * nk * 2 * nao, 2 * nb, kGreenS),
+               o_err = o_sb + oz::sliced_bytes(2 * nk * nao, 2 * nb, kGreenS);
   h.ensure(h.work, green_work_bytes(h));
   char *wk = (char *)h.work.p;
+  double2 *d_Y = tc ? (double2 *)(wk + o_y) : nullptr;
+  int *d_err = tc ? (int *)(wk + o_err) : nullptr;
+  oz::Sliced sa, sb;
+  if (tc) {
+    oz::sliced_bind(sa, wk + o_sa, 2 * nk * 2 * nao, 2 * nb, kGreenS);
+    oz::sliced_bind(sb, wk + o_sb, 2 * nk * nao, 2 * nb, kGreenS);
+    LR_CUDA(cudaMemsetAsync(d_err, 0, 4, s));
+  }
   const double2 *d_wfc0 = (const double2 *)h.d_wfc.p;
   const double *d_eig0 = (const double *)h.d_eig.p, *d_occ0 = (const double *)h.d_occ.p;
   double *d_w = (double *)(wk + o_w);
@@ -180,6 +214,26 @@ double green_build(Handle &h) {
     for (int it = 0; it < ntau; ++it) {
       k_weights<<<(nk * nb + 255) / 256, 256, 0, s>>>(d_eig, d_occ, mu, h.tau[it], nk * nb, d_w);
       ++launch_counter();
+      if (tc) {
+        // every band enters with its weight (zero outside the occupied / virtual range)
+        const size_t ny = 2 * (size_t)nk * nb * nao;
+        k_scale_bands<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(d_wfc, d_w, nk, nb, nao, d_Y);
+        ++launch_counter();
+        oz::split_complex(d_Y, nao, oz::OP_T, true, nao, nb, 2 * nk, (long long)nb * nao, sa, s);
+        oz::split_complex(d_Y, nao, oz::OP_C, false, nao, nb, 2 * nk, (long long)nb * nao, sb, s);
+        oz::Out o;
+        o.C = (double *)d_P;
+        o.ldc = nao;
+        o.batch_stride = (long long)n2;
+        o.mode = 1;
+        oz::gemm(sa, sb, 2 * nao, nao, 2 * nk, o, 0, 0, 2, d_err, s, h);
+        const size_t nthr = 2 * n2;
+        k_phase_sum<<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(d_P, d_tw, nk, nR, nao, 1.0 / nk,
+                                                                  d_gs + (size_t)it * nR * n2, g_stride, d_max);
+        ++launch_counter();
+        LR_CUDA(cudaGetLastError());
+        continue;
+      }
       std::vector<ZGemm> batch;
       for (int g = 0; g < 2; ++g)
         for (int k = 0; k < nk; ++k) {
@@ -215,8 +269,11 @@ double green_build(Handle &h) {
     }
   }
   unsigned long long mx[2];
+  int e_host = 0;
   LR_CUDA(cudaMemcpyAsync(mx, d_max, 16, cudaMemcpyDeviceToHost, s));
+  if (tc) LR_CUDA(cudaMemcpyAsync(&e_host, d_err, 4, cudaMemcpyDeviceToHost, s));
   LR_CUDA(cudaStreamSynchronize(s));
+  if (e_host) throw Error{LIBRPA_E_TIMEOUT, "Green's function: a bounded wait in the tensor-core GEMM ran out"};
   green_screen(h);   // after the imaginary-part check's maxima: they describe the unscreened G
   double mre, mim;
   std::memcpy(&mre, &mx[0], 8);

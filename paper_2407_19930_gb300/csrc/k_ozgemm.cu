@@ -75,6 +75,10 @@ struct CplxSrc {
   bool as_a;
   __device__ double2 opget(const double2 *q, int i, int k) const {
     if (op == OP_N) return q[(long long)i * ld + k];
+    if (op == OP_C) {
+      const double2 z = q[(long long)i * ld + k];
+      return make_double2(z.x, -z.y);
+    }
     double2 z = q[(long long)k * ld + i];
     if (op == OP_H) z.y = -z.y;
     return z;

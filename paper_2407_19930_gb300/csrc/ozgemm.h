@@ -46,12 +46,12 @@ void sliced_bind(Sliced &o, void *mem, int rows, int K, int S);
 
 // Row r of a split source is produced by `Src::get(r, k)` for k < K; rows [row0, row0 + rows)
 // of the destination are written (digits for k in [K, kpad) are zero).
-enum Op { OP_N = 0, OP_T = 1, OP_H = 2 };
+enum Op { OP_N = 0, OP_T = 1, OP_H = 2, OP_C = 3 };   // OP_C: complex conjugate, not transposed
 //  real:    X[r][k] = src[r * ld + k] (trans = false) or src[k * ld + r] (trans = true); entries of
 //           `rows` rows each are `batch_stride` doubles apart.
 void split_real(const double *src, long long ld, bool trans, int rows, int K, int batch, long long batch_stride,
                 Sliced &out, cudaStream_t s, int row0 = 0);
-//  complex: op(Z)[i][k] with op in {N, T, H}; Z row-major interleaved (re, im), leading dim ld.
+//  complex: op(Z)[i][k] with op in {N, T, H, C}; Z row-major interleaved (re, im), leading dim ld.
 //   as_a = true  -> stacked real matrix A'[2i + c][2k + c'] = [[Re, -Im], [Im, Re]] of op(Z)[i][k]
 //   as_a = false -> B'^T[j][2k + c'] = component c' of op(Z)[k][j]
 void split_complex(const double2 *src, long long ld, Op op, bool as_a, int n_out, int n_k, int batch,
