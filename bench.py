@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RPA energies/s"
 UNIT = "energies/s"
+WORKLOAD_CUBIC = "cubic cell: 2 atoms, 8 NAO / 24 ABF each, N_aux 48, 2x2x2 k-mesh, %d tau/omega points"
 WORKLOAD = ("graphene 4x4 supercell + H2O-shaped molecule: 35 atoms, n_ao 431, N_aux 2010, "
             "4x4x1 k-mesh, 16 tau/omega points")
 
@@ -379,7 +380,7 @@ def run_gpu(args):
     if dist:
         dist.barrier()
     L.load(build_if_missing=False)
-    inp = syn.config_graphene(kmesh=args.kmesh)
+    inp = syn.config_cubic() if args.workload == "cubic" else syn.config_graphene(kmesh=args.kmesh)
     st = inp.st
     stream = torch.cuda.Stream(device=local)
     o = L.librpa_gpu_default_opts()
@@ -421,6 +422,7 @@ def run_gpu(args):
         clk = clocks.stop()
         # counters of the last step (every step launches the same kernels), read after the timed region
         stats = [L.librpa_gpu_get_stats(h)]
+        grid_used = L.librpa_gpu_get_grid(h)
         launches = stats[-1]["launches"] * args.steps
         t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, "cuda")
         value = job_value(args.steps, ws, t)
@@ -470,7 +472,9 @@ def run_gpu(args):
     ms, fl, nl, srcf = kern[name]
     achieved = fl / (ms * 1e-3) / 1e12 if ms > 0 else None
     tr = TRAFFIC.get(name)
-    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _src_sha(tr["src"], tr["begin"], tr["end"]) else None
+    # the captured traffic is the graphene slab's (its per-launch work is the same at every k-mesh)
+    traffic = tr["bytes_per_launch"] if (tr and args.workload == "graphene" and
+                                         tr["src_sha"] == _src_sha(tr["src"], tr["begin"], tr["end"])) else None
     step_ms = t / args.steps * 1e3 * ws / ws
     chi0_tflops = s["flop_chi0"] / (s["ms_chi0"] * 1e-3) / 1e12
     line = {
@@ -479,7 +483,8 @@ def run_gpu(args):
         "dtype": PRECISIONS[args.precision][1],
         "data": "synthetic (seeded tight-binding KS data, LRI coefficients and Coulomb matrices "
                 "of the paper's graphene/H2O workload shape)",
-        "config": {"workload": WORKLOAD if (args.kmesh, args.ntau) == ((4, 4, 1), 16) else
+        "config": {"workload": (WORKLOAD_CUBIC % args.ntau) if args.workload == "cubic" else
+                   WORKLOAD if (args.kmesh, args.ntau) == ((4, 4, 1), 16) else
                    "profiling variant: graphene slab, %s k-mesh, %d tau" % ("x".join(map(str, st.kmesh)), args.ntau),
                    "atoms": st.natoms, "n_ao": st.nao, "n_aux": st.naux,
                    "kmesh": "x".join(map(str, st.kmesh)), "n_tau": args.ntau, "precision": args.precision,
@@ -522,7 +527,19 @@ def run_gpu(args):
         binp = _batch_inputs(args.batch_sample)
         bout, bclk = batch_measure(L, binp, args.ntau, 1, local, torch)
         line["batch"] = {"workload": _batch_workload(binp, args.ntau), "modes": bout, "clocks": bclk}
-    if ws == 1 and not args.no_cpu:
+    if ws == 1 and not args.no_cpu and args.workload == "cubic":
+        # the oracle's whole energy on the library's grid (a fraction of a second on the host cores)
+        from oracle import build as obuild
+        obuild.build()
+        t_or, ec_or = oracle_full_energy(inp, grid_used)
+        cpu = cpu_model()
+        line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "the whole energy of the workload", "nproc": cpu["nproc"],
+                                "cpu_model": cpu["model"], "ec_ha": ec_or,
+                                "ec_gpu_minus_oracle_mev_per_atom": (ec - ec_or) * MEV_PER_HA / st.natoms}
+        for m, v in modes.items():
+            v["ec_diff_vs_oracle_mev_per_atom"] = abs(v["ec_ha"] - ec_or) * MEV_PER_HA / st.natoms
+    elif ws == 1 and not args.no_cpu:
         from oracle import build as obuild, grid as ogrid
         obuild.build()
         cb = cpu_sample(inp, ogrid.make_grid(args.ntau, *inp.delta_range))
@@ -817,6 +834,8 @@ def main():
     ap.add_argument("--single-thread-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-peaks", action="store_true", help="skip the FP64/TF32 peak probes")
     # smaller variants of the same workload, for profiler captures only (not bench lines)
+    ap.add_argument("--workload", choices=["graphene", "cubic"], default="graphene",
+                    help="graphene: the slab of the headline; cubic: the 2-atom cubic cell (2x2x2 k)")
     ap.add_argument("--kmesh", default="4,4,1", help="k-mesh of the graphene slab (profiling variants)")
     ap.add_argument("--ntau", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")

@@ -36,12 +36,15 @@ __global__ void __launch_bounds__(256) k_tau_to_omega(const double *__restrict__
   }
 }
 
+// chi0(q, i omega_k) for the nsel selected q (qidx: their mesh indices; ph: their phases, [qi][R])
 template <int NR>
 __global__ void __launch_bounds__(256) k_r_to_q(const double *__restrict__ in, double2 *__restrict__ out,
-                                                const double2 *__restrict__ ph, int nR, int nq, int nw,
-                                                size_t n2) {
+                                                const double2 *__restrict__ ph, const int *__restrict__ qidx,
+                                                int nR, int nsel, int nw, size_t n2) {
   __shared__ double2 ps[NR * NR];
-  for (int e = threadIdx.x; e < nq * nR; e += blockDim.x) ps[e] = ph[e];
+  __shared__ int qs[NR];
+  for (int e = threadIdx.x; e < nsel * nR; e += blockDim.x) ps[e] = ph[e];
+  for (int e = threadIdx.x; e < nsel; e += blockDim.x) qs[e] = qidx[e];
   __syncthreads();
   const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
@@ -50,17 +53,27 @@ __global__ void __launch_bounds__(256) k_r_to_q(const double *__restrict__ in, d
 #pragma unroll
   for (int R = 0; R < NR; ++R) y[R] = R < nR ? in[((size_t)k * nR + R) * n2 + x] : 0.0;
 #pragma unroll 1
-  for (int q = 0; q < nq; ++q) {
+  for (int qi = 0; qi < nsel; ++qi) {
     double re = 0.0, im = 0.0;
 #pragma unroll
     for (int R = 0; R < NR; ++R)
       if (R < nR) {
-        const double2 p = ps[q * nR + R];
+        const double2 p = ps[qi * nR + R];
         re = fma(p.x, y[R], re);
         im = fma(p.y, y[R], im);
       }
-    out[((size_t)q * nw + k) * n2 + x] = make_double2(re, im);
+    out[((size_t)qs[qi] * nw + k) * n2 + x] = make_double2(re, im);
   }
+}
+
+// chi0(q) = conj chi0(-q) for the q not computed (chi0(R) is real); pairs[2 i] = q, pairs[2 i + 1] = -q
+__global__ void __launch_bounds__(256) k_conj_fill(double2 *__restrict__ chi, const int *__restrict__ pairs, int nw,
+                                                   size_t per_q) {
+  const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= per_q) return;
+  const int q = pairs[2 * blockIdx.y], p = pairs[2 * blockIdx.y + 1];
+  const double2 z = chi[(size_t)p * per_q + x];
+  chi[(size_t)q * per_q + x] = make_double2(z.x, -z.y);
 }
 
 template <int NT>
@@ -70,10 +83,10 @@ void launch_tw(const double *in, double *out, const double *gamma, int ntau, int
 }
 
 template <int NR>
-void launch_rq(const double *in, double2 *out, const double2 *ph, int nR, int nq, int nw, size_t n2,
-               cudaStream_t s) {
+void launch_rq(const double *in, double2 *out, const double2 *ph, const int *qidx, int nR, int nsel, int nw,
+               size_t n2, cudaStream_t s) {
   dim3 g((unsigned)((n2 + 255) / 256), (unsigned)nw);
-  k_r_to_q<NR><<<g, 256, 0, s>>>(in, out, ph, nR, nq, nw, n2);
+  k_r_to_q<NR><<<g, 256, 0, s>>>(in, out, ph, qidx, nR, nsel, nw, n2);
 }
 
 }  // namespace
@@ -81,7 +94,7 @@ void launch_rq(const double *in, double2 *out, const double2 *ph, int nR, int nq
 size_t freq_work_bytes(const Handle &h) {
   const size_t nR = h.mesh.size(), n2 = (size_t)h.naux * h.naux;
   const size_t b_rw = (size_t)h.ntau * nR * n2 * 8, b_g = (size_t)h.ntau * h.ntau * 8, b_p = nR * nR * 16;
-  return b_rw + 256 + b_g + 256 + b_p;
+  return b_rw + 256 + b_g + 256 + b_p + 256 + 3 * nR * 4;
 }
 
 void freq_transform(Handle &h) {
@@ -97,8 +110,20 @@ void freq_transform(Handle &h) {
   double *rw = (double *)w;
   double *dg = (double *)(w + (b_rw + 255) / 256 * 256);
   double2 *dp = (double2 *)((char *)dg + (b_g + 255) / 256 * 256);
-  std::vector<double2> ph((size_t)nq * nR);
+  int *di = (int *)((char *)dp + (b_p + 255) / 256 * 256);   // [nq] selected q, then [nq][2] pairs
+  // only q <= -q is transformed; the others are conj chi0(-q) (chi0(R) is real)
+  std::vector<int> qsel, pairs;
   for (int q = 0; q < nq; ++q) {
+    const int p = h.mesh.neg(q);
+    if (q <= p)
+      qsel.push_back(q);
+    else
+      pairs.insert(pairs.end(), {q, p});
+  }
+  const int nsel = (int)qsel.size();
+  std::vector<double2> ph((size_t)nsel * nR);
+  for (int qi = 0; qi < nsel; ++qi) {
+    const int q = qsel[qi];
     int a, b, c;
     h.mesh.split(q, a, b, c);
     for (int R = 0; R < nR; ++R) {
@@ -108,11 +133,14 @@ void freq_transform(Handle &h) {
       const long long num = (long long)a * x * h.mesh.n2 * h.mesh.n3 + (long long)b * y * h.mesh.n1 * h.mesh.n3 +
                             (long long)c * z * h.mesh.n1 * h.mesh.n2;
       const double th = 2.0 * M_PI * (double)(num % den) / (double)den;
-      ph[(size_t)q * nR + R] = make_double2(std::cos(th), std::sin(th));
+      ph[(size_t)qi * nR + R] = make_double2(std::cos(th), std::sin(th));
     }
   }
+  std::vector<int> ints(qsel);
+  ints.insert(ints.end(), pairs.begin(), pairs.end());
   LR_CUDA(cudaMemcpyAsync(dg, h.gamma.data(), b_g, cudaMemcpyHostToDevice, s));
-  LR_CUDA(cudaMemcpyAsync(dp, ph.data(), b_p, cudaMemcpyHostToDevice, s));
+  LR_CUDA(cudaMemcpyAsync(dp, ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  LR_CUDA(cudaMemcpyAsync(di, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   const double *in = (const double *)h.d_chi_tau.p;
   if (ntau <= 16)
     launch_tw<16>(in, rw, dg, ntau, nR, n2, s);
@@ -120,13 +148,20 @@ void freq_transform(Handle &h) {
     launch_tw<32>(in, rw, dg, ntau, nR, n2, s);
   else
     launch_tw<64>(in, rw, dg, ntau, nR, n2, s);
+  double2 *out = (double2 *)h.d_chi_qw.p;
   if (nR <= 16)
-    launch_rq<16>(rw, (double2 *)h.d_chi_qw.p, dp, nR, nq, ntau, n2, s);
+    launch_rq<16>(rw, out, dp, di, nR, nsel, ntau, n2, s);
   else if (nR <= 32)
-    launch_rq<32>(rw, (double2 *)h.d_chi_qw.p, dp, nR, nq, ntau, n2, s);
+    launch_rq<32>(rw, out, dp, di, nR, nsel, ntau, n2, s);
   else
-    launch_rq<64>(rw, (double2 *)h.d_chi_qw.p, dp, nR, nq, ntau, n2, s);
+    launch_rq<64>(rw, out, dp, di, nR, nsel, ntau, n2, s);
   launch_counter() += 2;
+  if (!pairs.empty()) {
+    const size_t per_q = (size_t)ntau * n2;
+    dim3 g((unsigned)((per_q + 255) / 256), (unsigned)(pairs.size() / 2));
+    k_conj_fill<<<g, 256, 0, s>>>(out, di + nsel, ntau, per_q);
+    ++launch_counter();
+  }
   LR_CUDA(cudaGetLastError());
 }
 
