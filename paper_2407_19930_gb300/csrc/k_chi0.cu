@@ -220,6 +220,9 @@ struct OArgs {
   long long o_sz_p;
   // under screening: 1 where the CTA's O block is exactly zero ([P][U][V][64-column chunk]), else NULL
   const unsigned char *zero;
+  // 3-plane tensor-core kernel: the row exponents of O's digit planes (rows (p, U, nu); atomicMax
+  // of the largest biased FP64 exponent minus 1022), or NULL
+  int *rexp;
 };
 
 // Arithmetic of the O assembly.  ArD: FP64 (FP64 modes).  ArF: FP32, for the mixed modes whose
@@ -690,6 +693,7 @@ __global__ void __launch_bounds__(128) k_oassemble_tc(OArgs a) {
       }
     tc_term<S>(sLX, sRG, 64 * kTcKP, warp * 16, ks_n, lane, acc);
     double *orow = Ob + (size_t)(a.aux_off[V] + nu) * ldo;
+    int emax = 0;   // largest biased exponent among this lane's stored outputs
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -718,8 +722,17 @@ __global__ void __launch_bounds__(128) k_oassemble_tc(OArgs a) {
           const int ex = (int)((bits >> 52) & 0x7ff) + k;
           o = ex <= 0 ? 0.0 : __longlong_as_double(bits + ((long long)k << 52));
         }
-        if (i < nU && kc < mU) orow[(size_t)i * mU + kc] = o;
+        if (i < nU && kc < mU) {
+          orow[(size_t)i * mU + kc] = o;
+          emax = max(emax, (int)((__double_as_longlong(o) >> 52) & 0x7FF));
+        }
       }
+    if (S < 4 && a.rexp) {   // the row (p, U, nu) of the final contraction's O operand
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+      if (lane == 0 && emax > 0)
+        atomicMax(a.rexp + ((size_t)p * a.natoms + U) * a.naux + a.aux_off[V] + nu, emax - 1022);
+    }
     __syncthreads();   // every warp done with LX and the exponents before the next nu
   }
 }
@@ -1051,8 +1064,11 @@ int oasm_chunks(const Handle &h) {
   return c;
 }
 
-void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw, double *Ow,
-                   const unsigned char *zero = nullptr) {
+// rexp (may be NULL): row exponents of the O operand's digit planes, built by atomicMax (initialised
+// to -1022) in the 3-plane tensor-core kernel only: in the 5-plane kernel the atomics cost more
+// than the exponent pass they save.  Returns true when the kernel that builds them ran.
+bool run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw, double *Ow,
+                   const unsigned char *zero = nullptr, int *rexp = nullptr) {
   Chi0Plan &P = h.plan;
   const int nat = h.natoms;
   int maxn = 0, max_chunks = 0;
@@ -1107,7 +1123,9 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
   oa.o_off = (const long long *)P.t_o_off.p;
   oa.o_sz_p = P.o_sz;
   oa.zero = zero;
+  oa.rexp = nullptr;
   if (ar != 0 && maxn <= 16) {
+    oa.rexp = ar == 1 ? rexp : nullptr;
     // tensor-core modes: digit-plane products on the tensor cores, one launch over every (U, V);
     // 5 planes (~39 bits) for the FP64-accurate mode, 3 (~23 bits, as FP32) for the mixed modes
     dim3 og((unsigned)max_chunks, (unsigned)(np * nat * nat));
@@ -1123,7 +1141,7 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
     }
     ++launch_counter();
     LR_CUDA(cudaGetLastError());
-    return;
+    return oa.rexp != nullptr;
   }
   // one launch per row-block size: the atoms U of each group (listed in the plan's table).  The
   // FP64 arithmetic is bound by the FP64 pipe, where rows beyond n_U cost nothing: one launch over
@@ -1142,6 +1160,7 @@ void run_oassemble(Handle &h, const Point *dpts, int np, double *Nw, double *Xw,
     ++launch_counter();
     LR_CUDA(cudaGetLastError());
   }
+  return false;
 }
 
 // Points of the (R, tau) grid in flat order: point idx = itau * nR + iR.
@@ -1739,7 +1758,9 @@ void tc_gather(Handle &h, TcRound &r) {
 void tc_assemble(Handle &h, TcRound &r, const unsigned char *zero) {
   Chi0Plan &P = h.plan;
   const int nat = h.natoms, nR = h.mesh.size(), naux = h.naux, np = r.np;
-  run_oassemble(h, (const Point *)P.t_pts.p, np, r.Nw, r.Xw, r.Ow, zero);
+  int *rexp = h.chi0_S >= 4 && h.chi0_S <= oz::SMAX ? nullptr : r.sod.expo;   // 3-plane kernel only
+  if (rexp) oz::expo_init(r.sod, np * nat * naux, h.stream);
+  const bool expo_given = run_oassemble(h, (const Point *)P.t_pts.p, np, r.Nw, r.Xw, r.Ow, zero, rexp);
   std::vector<long long> off(np * nat);
   std::vector<int> ke(np * nat);
   for (int q = 0; q < np; ++q)
@@ -1750,7 +1771,7 @@ void tc_assemble(Handle &h, TcRound &r, const unsigned char *zero) {
   h.upload_async(P.t_oe_off, off.data(), off.size() * 8);
   h.upload_async(P.t_oe_k, ke.data(), ke.size() * 4);
   oz::split_ragged(r.Ow, (const long long *)P.t_oe_off.p, (const int *)P.t_oe_k.p, naux, np * nat, P.max_nm, r.sod,
-                   h.stream);
+                   h.stream, expo_given);
   const double spin = spin_factor(h);
   r.ef.clear();
   for (int q = 0; q < np; ++q) {

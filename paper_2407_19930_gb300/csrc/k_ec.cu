@@ -91,23 +91,32 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double2 *const *mats, int n,
     if (bad) info[b] = 1;
   }
   if (inv) {
-    // y = L^{-1}: column j solves L y_j = e_j (y_ij = 0 for i < j); L's diagonal is real
+    // y = L^{-1}: column j solves L y_j = e_j (y_ij = 0 for i < j); L's diagonal is real.  Four
+    // consecutive lanes per column (blockDim.x == 4 NB), each summing every fourth k of a row.
     double2 *y = a + NB * lda;
-    for (int j = threadIdx.x; j < NB; j += blockDim.x)
-      for (int i = 0; i < NB; ++i) {
+    const int j = threadIdx.x >> 2, part = threadIdx.x & 3;
+    for (int i = 0; i < NB; ++i) {
+      double sr = 0.0, si = 0.0;
+      if (j < nb && i < nb && i > j)
+        for (int k = j + part; k < i; k += 4) {
+          const double2 l = a[i * lda + k], z = y[k * lda + j];
+          sr += l.x * z.x - l.y * z.y;
+          si += l.x * z.y + l.y * z.x;
+        }
+      sr += __shfl_xor_sync(0xffffffffu, sr, 1);
+      si += __shfl_xor_sync(0xffffffffu, si, 1);
+      sr += __shfl_xor_sync(0xffffffffu, sr, 2);
+      si += __shfl_xor_sync(0xffffffffu, si, 2);
+      if (part == 0) {
         double2 v = make_double2(0.0, 0.0);
         if (j < nb && i < nb && i >= j) {
-          double sr = i == j ? 1.0 : 0.0, si = 0.0;
-          for (int k = j; k < i; ++k) {
-            const double2 l = a[i * lda + k], z = y[k * lda + j];
-            sr -= l.x * z.x - l.y * z.y;
-            si -= l.x * z.y + l.y * z.x;
-          }
           const double d = a[i * lda + i].x;
-          v = make_double2(sr / d, si / d);
+          v = make_double2(((i == j ? 1.0 : 0.0) - sr) / d, -si / d);
         }
         y[i * lda + j] = v;
       }
+      __syncwarp();
+    }
     __syncthreads();
     double2 *Y = inv + (size_t)b * NB * NB;
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Y[e] = y[(e / NB) * lda + e % NB];

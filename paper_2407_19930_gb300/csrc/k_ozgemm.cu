@@ -211,7 +211,7 @@ __global__ void k_plain_tf32(Src src, int rows, int K, int kpad, int row0, float
 }
 
 template <class Src>
-void split_any(const Src &src, int rows, int K, int row0, Sliced &o, cudaStream_t s) {
+void split_any(const Src &src, int rows, int K, int row0, Sliced &o, cudaStream_t s, bool expo_given = false) {
   if (row0 < 0 || row0 + rows > o.rows || K > o.kpad) throw Error{LIBRPA_E_ARG, "split: rows or K exceed the operand"};
   if (rows <= 0) return;
   const int kpad = o.kpad;
@@ -234,7 +234,10 @@ void split_any(const Src &src, int rows, int K, int row0, Sliced &o, cudaStream_
     return;
   }
   __nv_bfloat16 *dig = (__nv_bfloat16 *)o.digits;
-  k_row_expo<Src><<<(unsigned)(((long long)rows * 32 + 255) / 256), 256, 0, s>>>(src, rows, K, row0, o.expo);
+  if (!expo_given) {
+    k_row_expo<Src><<<(unsigned)(((long long)rows * 32 + 255) / 256), 256, 0, s>>>(src, rows, K, row0, o.expo);
+    ++launch_counter();
+  }
   const dim3 gd((unsigned)rows, (unsigned)((kpad + 1023) / 1024));
   switch (o.S) {
     case 1: k_digits<1, Src><<<gd, 256, 0, s>>>(src, K, kpad, row0, plane, o.expo, dig); break;
@@ -243,7 +246,7 @@ void split_any(const Src &src, int rows, int K, int row0, Sliced &o, cudaStream_
     case 4: k_digits<4, Src><<<gd, 256, 0, s>>>(src, K, kpad, row0, plane, o.expo, dig); break;
     default: k_digits<5, Src><<<gd, 256, 0, s>>>(src, K, kpad, row0, plane, o.expo, dig); break;
   }
-  launch_counter() += 2;
+  ++launch_counter();
   LR_CUDA(cudaGetLastError());
 }
 
@@ -900,9 +903,21 @@ void split_gather(const GatherSrc &src, int rows, int K, Sliced &out, cudaStream
 }
 
 void split_ragged(const double *base, const long long *off, const int *Ke, int rows_per_entry, int n_entries,
-                  int Kmax, Sliced &out, cudaStream_t s) {
+                  int Kmax, Sliced &out, cudaStream_t s, bool expo_given) {
   RaggedSrc r{base, off, Ke, rows_per_entry};
-  split_any(r, rows_per_entry * n_entries, Kmax, 0, out, s);
+  split_any(r, rows_per_entry * n_entries, Kmax, 0, out, s, expo_given);
+}
+
+// out.expo[r] = -1022 (the exponent of an all-zero row) for rows [0, rows)
+__global__ void k_expo_init(int *expo, int rows) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < rows) expo[r] = -1022;
+}
+void expo_init(Sliced &out, int rows, cudaStream_t s) {
+  if (rows <= 0) return;
+  k_expo_init<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(out.expo, rows);
+  ++launch_counter();
+  LR_CUDA(cudaGetLastError());
 }
 
 long long gemm_multi(const std::vector<std::pair<const Sliced *, const Sliced *>> &ops, const std::vector<Entry> &entries,

@@ -73,8 +73,12 @@ struct GatherSrc {
 void split_gather(const GatherSrc &src, int rows, int K, Sliced &out, cudaStream_t s);
 //  ragged entries: row r belongs to entry e = r / rows_per_entry; its K_e columns are
 //  base[off[e] + (r % rows_per_entry) * K_e + k] (zero for k >= K_e); off, K on the device.
+//  expo_given: out.expo already holds each row's exponent (its largest biased FP64 exponent
+//  minus 1022, as the exponent pass would write it), which is then not recomputed.
 void split_ragged(const double *base, const long long *off, const int *Ke, int rows_per_entry, int n_entries,
-                  int Kmax, Sliced &out, cudaStream_t s);
+                  int Kmax, Sliced &out, cudaStream_t s, bool expo_given = false);
+//  out.expo[r] = -1022 (an all-zero row) for r < rows: the start of an exponent built by atomicMax
+void expo_init(Sliced &out, int rows, cudaStream_t s);
 
 // Output of a GEMM entry.
 //  mode 0: real C[m][n] (ldc);

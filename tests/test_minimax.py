@@ -17,7 +17,9 @@ import os
 import numpy as np
 import pytest
 
-from oracle import grid as ogrid, minimax as omm
+from oracle import grid as ogrid
+
+omm = pytest.importorskip("oracle.minimax")   # needs mpmath
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "minimax_grids.json")
 
