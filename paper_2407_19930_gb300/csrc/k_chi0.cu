@@ -1758,7 +1758,9 @@ void tc_gather(Handle &h, TcRound &r) {
 void tc_assemble(Handle &h, TcRound &r, const unsigned char *zero) {
   Chi0Plan &P = h.plan;
   const int nat = h.natoms, nR = h.mesh.size(), naux = h.naux, np = r.np;
-  int *rexp = h.chi0_S >= 4 && h.chi0_S <= oz::SMAX ? nullptr : r.sod.expo;   // 3-plane kernel only
+  // the 3-plane kernel builds the row exponents when O is split into at most 3 digit planes (the
+  // plain BF16 / TF32 operands have none)
+  int *rexp = h.chi0_S >= 1 && h.chi0_S <= 3 ? r.sod.expo : nullptr;
   if (rexp) oz::expo_init(r.sod, np * nat * naux, h.stream);
   const bool expo_given = run_oassemble(h, (const Point *)P.t_pts.p, np, r.Nw, r.Xw, r.Ow, zero, rexp);
   std::vector<long long> off(np * nat);
