@@ -301,7 +301,7 @@ int librpa_gpu_create(librpa_gpu_t *hp, const librpa_gpu_opts *o) {
   {
     // arithmetic per stage (-1 = FP64 pipes, 0 = plain BF16, 1..5 = digit planes, 6 = plain
     // TF32, 7 = 3xTF32): presets, then explicit overrides
-    static const int chi0_preset[6] = {-1, 5, 3, 0, 6, 7}, ec_preset[6] = {-1, 5, 5, 5, 5, 5};
+    static const int chi0_preset[6] = {-1, 5, 3, 0, 6, 7}, ec_preset[6] = {-1, 5, 4, 4, 4, 4};
     h->chi0_S = o->chi0_slices ? o->chi0_slices : chi0_preset[o->precision];
     h->ec_S = o->ec_slices ? o->ec_slices : ec_preset[o->precision];
   }

@@ -163,7 +163,7 @@ TOL_MIXED_MEV_PER_ATOM = 0.1
 
 @pytest.mark.parametrize("name", ["cubic", "mixed", "cubic_3x3x1"])
 def test_split_mode_energy(name):
-    """Mixed mode (chi0 GEMMs on 3 BF16 digit planes, FP32 O assembly; ln det FP64-accurate):
+    """Mixed mode (chi0 GEMMs on 3 BF16 digit planes, 3-plane O assembly; ln det on 4 planes):
     E_c within 0.1 meV/atom of the FP64 oracle."""
     inp = CONFIGS[name]()
     grid = ogrid.make_grid(8, *inp.delta_range)
