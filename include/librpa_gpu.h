@@ -68,7 +68,8 @@ extern "C" {
  * in FP32 (about 21 bits).  In every mode other than LIBRPA_FP64 the O assembly of the chi0
  * contraction also runs on digit planes (5 for LIBRPA_FP64_TC, 3 otherwise), the ln det GEMMs
  * (including the Cholesky panel products and trailing updates) on 5 planes for LIBRPA_FP64_TC and
- * 4 (~31 bits) otherwise, and the G(tau) products C diag(w) C^H on 5 planes.  So LIBRPA_FP64_TC is a ~39-bit mode, not FP64: its results match
+ * 4 (~31 bits) otherwise, and the G(tau) products C diag(w) C^H on 5 planes; outside the two
+ * FP64-accurate modes the tau -> omega and R -> q transforms also compute in FP32.  So LIBRPA_FP64_TC is a ~39-bit mode, not FP64: its results match
  * the FP64 path to chi0(R, tau) 1e-10 normwise and E_c 1e-8 Ha, not bit for bit.  The
  * exponentials of G(tau), the transform weights, the Cholesky factorisations' diagonal blocks
  * and the E_c sum always stay FP64. */
