@@ -44,10 +44,11 @@ NOMINAL_FP64_OVER_BF16 = 1.25 / 2250.0
 
 # precision presets of the library (include/librpa_gpu.h): name -> (LIBRPA_* value, dtype label)
 PRECISIONS = {"fp64": (0, "f64"), "fp64_tc": (1, "f64-accurate: bf16 digit planes (5) on tcgen05"),
-              "split": (2, "mixed: chi0 GEMMs on 3 bf16 digit planes, ln det on 4"),
-              "bf16": (3, "mixed: chi0 GEMMs in plain bf16 (fp32 accumulation), ln det on 4 digit planes"),
-              "tf32": (4, "mixed: chi0 GEMMs in plain tf32 (fp32 accumulation), ln det on 4 digit planes"),
-              "tf32x3": (5, "mixed: chi0 GEMMs as 3xtf32 split products (fp32 accumulation), ln det on 4 digit planes")}
+              "split": (2, "mixed: chi0 GEMMs on 3 bf16 digit planes, ln det on 5"),
+              "bf16": (3, "mixed: chi0 GEMMs in plain bf16 (fp32 accumulation), ln det on 5 digit planes"),
+              "tf32": (4, "mixed: chi0 GEMMs in plain tf32 (fp32 accumulation), ln det on 5 digit planes"),
+              "tf32x3": (5, "mixed: chi0 GEMMs as 3xtf32 split products (fp32 accumulation), ln det on 5 digit planes"),
+              "split_fast": (6, "mixed: chi0 GEMMs on 3 bf16 digit planes, ln det on 4, transforms in fp32")}
 MEV_PER_HA = 27211.386245988
 
 # DRAM traffic per launch of the dominant kernels from one ncu capture (see profiles/), valid only
@@ -852,7 +853,7 @@ def main():
                     help="arrival rates (req/s) of the serving sweep in the headline line")
     ap.add_argument("--rate", type=float, default=20.0, help="request arrival rate (Poisson), per second")
     ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--modes", default="fp64_tc,split,tf32x3,tf32,bf16,fp64@1e-3,fp64_tc@1e-3",
+    ap.add_argument("--modes", default="fp64_tc,split,split_fast,tf32x3,tf32,bf16,fp64@1e-3,fp64_tc@1e-3",
                     help="other precision modes timed after the headline, 'mode@theta' with G screening "
                          "(1 GPU; '' for none)")
     args = ap.parse_args()

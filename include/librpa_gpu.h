@@ -67,18 +67,20 @@ extern "C" {
  * split writes x = hi + lo with hi = tf32(x), lo = tf32(x - hi) and sums hi hi + hi lo + lo hi
  * in FP32 (about 21 bits).  In every mode other than LIBRPA_FP64 the O assembly of the chi0
  * contraction also runs on digit planes (5 for LIBRPA_FP64_TC, 3 otherwise), the ln det GEMMs
- * (including the Cholesky panel products and trailing updates) on 5 planes for LIBRPA_FP64_TC and
- * 4 (~31 bits) otherwise, and the G(tau) products C diag(w) C^H on 5 planes; outside the two
- * FP64-accurate modes the tau -> omega and R -> q transforms also compute in FP32.  So LIBRPA_FP64_TC is a ~39-bit mode, not FP64: its results match
+ * (including the Cholesky panel products and trailing updates) and the G(tau) products
+ * C diag(w) C^H on 5 planes.  LIBRPA_SPLIT_FAST alone leaves that rule: its ln det GEMMs use 4
+ * planes (~31 bits) and its tau -> omega and R -> q transforms compute in FP32 (the transform
+ * weights and phases rounded to FP32), for an E_c still within 0.1 meV/atom.  So LIBRPA_FP64_TC is a ~39-bit mode, not FP64: its results match
  * the FP64 path to chi0(R, tau) 1e-10 normwise and E_c 1e-8 Ha, not bit for bit.  The
  * exponentials of G(tau), the transform weights, the Cholesky factorisations' diagonal blocks
  * and the E_c sum always stay FP64. */
 #define LIBRPA_FP64 0     /* every step in FP64 on the FP64 pipes (DMMA / DFMA) */
 #define LIBRPA_FP64_TC 1  /* chi0, G and ln det GEMMs with 5 digit planes (~39 bits) on the tensor cores */
-#define LIBRPA_SPLIT 2    /* chi0 GEMMs with 3 digit planes (mixed), ln det GEMMs with 4 (~31 bits) */
-#define LIBRPA_BF16 3     /* chi0 GEMMs in plain BF16 (FP32 accumulation), ln det GEMMs with 4 */
-#define LIBRPA_TF32 4     /* chi0 GEMMs in plain TF32 (FP32 accumulation), ln det GEMMs with 4 */
-#define LIBRPA_TF32X3 5   /* chi0 GEMMs as 3xTF32 split products (FP32 accumulation), ln det with 4 */
+#define LIBRPA_SPLIT 2    /* chi0 GEMMs with 3 digit planes (mixed), ln det GEMMs with 5 */
+#define LIBRPA_BF16 3     /* chi0 GEMMs in plain BF16 (FP32 accumulation), ln det GEMMs with 5 */
+#define LIBRPA_TF32 4     /* chi0 GEMMs in plain TF32 (FP32 accumulation), ln det GEMMs with 5 */
+#define LIBRPA_TF32X3 5   /* chi0 GEMMs as 3xTF32 split products (FP32 accumulation), ln det with 5 */
+#define LIBRPA_SPLIT_FAST 6 /* as LIBRPA_SPLIT, ln det GEMMs with 4 planes, transforms in FP32 */
 
 /* Grids the library builds (opts.grid_kind) */
 #define LIBRPA_GRID_MINIMAX 0         /* minimax tau / omega grids (librpa_gpu_build_grid_minimax) */
@@ -99,7 +101,7 @@ typedef struct {
   librpa_gpu_free_fn dev_free;   /* NULL = cudaFree */
   void *alloc_ctx;               /* passed to dev_alloc / dev_free */
   int n_tau;                     /* grid size (tau = omega points) when the library builds the grid */
-  int precision;                 /* LIBRPA_FP64, _FP64_TC, _SPLIT, _BF16, _TF32 or _TF32X3 */
+  int precision;                 /* LIBRPA_FP64, _FP64_TC, _SPLIT, _BF16, _TF32, _TF32X3 or _SPLIT_FAST */
   size_t hbm_budget;             /* bytes the handle may allocate; 0 = no limit */
   int check_level;               /* 0 = none; 1 = check G is real and the pivots finite */
   int chi0_slices;               /* 0 = from precision; 1..5 = digit planes of the chi0 GEMMs */

@@ -105,6 +105,7 @@ struct Handle {
   int chi0_S = -1;  // chi0 GEMMs: -1 = FP64 pipes, 0 = plain BF16, 1..5 = BF16 digit planes, 6 = plain TF32,
                     // 7 = 3xTF32
   int ec_S = -1;    // ln det GEMMs: same encoding
+  bool freq_f32 = false;   // tau -> omega and R -> q transforms in FP32 (LIBRPA_SPLIT_FAST)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::string last_error;

@@ -14,9 +14,9 @@
 namespace librpa {
 namespace {
 
-// Arithmetic of the two maps: double in the FP64 and FP64_TC modes; float in the modes whose
-// chi0(R, tau) carries ~23 bits or fewer, where FP32 rounding is of the size of chi0's own error
-// and the FP64 pipe's flops (~60 ms per energy on the graphene slab) give way to the HBM traffic.
+// Arithmetic of the two maps: double, or float in LIBRPA_SPLIT_FAST, whose chi0(R, tau) carries
+// ~23 bits, so that FP32 rounding is of the size of chi0's own error and the FP64 pipe's flops
+// (~60 ms per energy on the graphene slab) give way to the HBM traffic.
 template <class A>
 struct Cplx;
 template <>
@@ -182,10 +182,8 @@ void freq_transform(Handle &h) {
   }
   std::vector<int> ints(qsel);
   ints.insert(ints.end(), qneg.begin(), qneg.end());
-  // FP32 for plain BF16 (0), 1..3 digit planes, plain TF32 (6) and 3xTF32 (7) chi0 GEMMs
-  const bool f32 = h.chi0_S >= 0 && (h.chi0_S <= 3 || h.chi0_S >= 6);
   char *w = (char *)h.work.p;
-  if (f32)
+  if (h.freq_f32)
     transform_as<float>(h, h.gamma, ph, ints, nsel, w, b_rw, b_g, b_p);
   else
     transform_as<double>(h, h.gamma, ph, ints, nsel, w, b_rw, b_g, b_p);

@@ -32,6 +32,7 @@ LIBRPA_SPLIT = 2
 LIBRPA_BF16 = 3
 LIBRPA_TF32 = 4
 LIBRPA_TF32X3 = 5
+LIBRPA_SPLIT_FAST = 6
 LIBRPA_GRID_MINIMAX = 0
 LIBRPA_GRID_GAUSS_LEGENDRE = 1
 LIBRPA_NOALLOC_SCRATCH_BYTES = 16 << 20

@@ -87,9 +87,11 @@ def test_fp64_tc_full_aux(full):
     assert np.abs(gpu["ec_w"] - ref["ec_w"]).max() < TOL_EC
 
 
-def test_split_full_aux(full):
+@pytest.mark.parametrize("precision", [L.LIBRPA_SPLIT, L.LIBRPA_SPLIT_FAST])
+def test_split_full_aux(full, precision):
     inp, grid, ref = full
-    gpu = _run(inp, grid, L.LIBRPA_SPLIT)
+    gpu = _run(inp, grid, precision)
     err = abs(gpu["ec"] - ref["ec"]) * MEV / inp.st.natoms
-    print("split mode at N_aux 2010 (%s k): E_c error %.2e meV/atom" % ("x".join(map(str, inp.st.kmesh)), err))
+    print("mixed mode %d at N_aux 2010 (%s k): E_c error %.2e meV/atom" % (
+        precision, "x".join(map(str, inp.st.kmesh)), err))
     assert err < 0.1, err

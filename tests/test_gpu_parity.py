@@ -161,14 +161,15 @@ MEV = 27211.386245988
 TOL_MIXED_MEV_PER_ATOM = 0.1
 
 
+@pytest.mark.parametrize("precision", [L.LIBRPA_SPLIT, L.LIBRPA_SPLIT_FAST])
 @pytest.mark.parametrize("name", ["cubic", "mixed", "cubic_3x3x1"])
-def test_split_mode_energy(name):
-    """Mixed mode (chi0 GEMMs on 3 BF16 digit planes, 3-plane O assembly; ln det on 4 planes):
-    E_c within 0.1 meV/atom of the FP64 oracle."""
+def test_split_mode_energy(name, precision):
+    """Mixed modes (chi0 GEMMs on 3 BF16 digit planes, 3-plane O assembly; ln det on 5 planes, or
+    on 4 with the transforms in FP32 for SPLIT_FAST): E_c within 0.1 meV/atom of the FP64 oracle."""
     inp = CONFIGS[name]()
     grid = ogrid.make_grid(8, *inp.delta_range)
     ref = pipeline.rpa_energy(inp, grid)
-    gpu = _run(inp, grid, opts=_opts(L.LIBRPA_SPLIT))
+    gpu = _run(inp, grid, opts=_opts(precision))
     err = abs(gpu["ec"] - ref["ec"]) * MEV / inp.st.natoms
     assert err < TOL_MIXED_MEV_PER_ATOM, err
 
